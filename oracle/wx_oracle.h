@@ -1,0 +1,107 @@
+/*
+ * wx_oracle.h -- plain FP64 CPU oracle of one weather-model time step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code exists to check the GPU path.  Only
+ * the tests, the smoke check and the benchmark's CPU-baseline leg may load
+ * it.  It shares no source, header, table or helper with the CUDA library
+ * and must never be called by the product path.
+ *
+ * What is computed (one step n -> n+1, dynamics first, then column physics):
+ *
+ *   Grid: cells (i,j,k), i in [0,nx), j in [0,ny), k in [0,nz), k = 0 at the
+ *   bottom; horizontal spacing h, layer thickness dz[k]; periodic in i and j
+ *   (the paper's Sec. 3.1 treats the KI/KJ boundaries cyclically), zero flux
+ *   through the bottom and the top (the paper's diffusion listing in the
+ *   appendix drops the missing vertical neighbour, 1-5d instead of 1-6d).
+ *
+ *   Dynamics for phi in {T, q} (paper Eq. 1 diffusion term, explicit Euler,
+ *   Sec. 3.1; plus flux-form first-order upwind advection on a C grid,
+ *   Sec. 2 describes ASUCA's C-grid finite-volume dynamics):
+ *     Dh  = kappa_h/h^2 * (phi_E + phi_W + phi_N + phi_S - 4 phi)
+ *     Dz  = kappa_h/dz_k * (F_{k+1/2} - F_{k-1/2}),
+ *           F_{k+1/2} = (phi_{k+1} - phi_k)/g_{k+1/2},  g = (dz_k+dz_{k+1})/2,
+ *           F_{-1/2} = F_{nz-1/2} = 0
+ *     Adv = -(1/h) * (U_e phi_e - U_w phi_w + V_n phi_n - V_s phi_s),
+ *           face value phi_f taken from the upwind cell: for a face
+ *           between cells L (west/south) and R (east/north) it is phi_L
+ *           when the face velocity is >= 0 and phi_R otherwise
+ *     phi* = phi + dt*(Dh + Dz + Adv)
+ *
+ *   Column physics (one column at a time: the paper's run_physics, Sec. 3.1
+ *   and the appendix listing "Physical processes"):
+ *     implicit vertical diffusion of T*:  (I - dt L_v) T** = T*, solved with
+ *     the Thomas algorithm, kappa_v(i,j,k) = kappa_mult(i,j)*kappa_lev(k),
+ *     interface value = mean of the two adjacent levels;
+ *     radiation: dtau_k = alpha_k dz_k q*_k / q_ref, tau_top(k) = sum of dtau
+ *     above k, tau_bot(k) = tau_top(k) + dtau_k,
+ *     H_k = S0 (exp(-tau_top) - exp(-tau_bot)) / dz_k;
+ *     T^{n+1} = T** + dt H,   q^{n+1} = q*.
+ *
+ * All arrays are C order: 3D fields [nz][ny][nx], 2D fields [ny][nx], face
+ * winds U[j][i] on the east face of cell (i,j), V[j][i] on the north face.
+ */
+#ifndef WX_ORACLE_H
+#define WX_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int nx, ny, nz;
+    double dt, h, kappa_h, S0, q_ref;
+    const double *dz;         /* [nz] layer thickness                      */
+    const double *kappa_lev;  /* [nz] vertical diffusivity profile         */
+    const double *alpha;      /* [nz] absorber coefficient                 */
+    const double *kappa_mult; /* [ny*nx] per-column multiplier, NULL = 1   */
+    int advection;            /* 0: winds ignored                          */
+    int physics;              /* 0: T^{n+1} = T*, no Thomas, no radiation  */
+} wxo_params;
+
+/* Dynamics only: (T, q) at step n -> (Ts, qs) = (T*, q*). */
+void wxo_dynamics(const wxo_params *p, const double *T, const double *q,
+                  const double *U, const double *V, double *Ts, double *qs);
+
+/* Coefficients of the implicit vertical-diffusion system of one column
+ * (sub-diagonal a, diagonal b, super-diagonal c, each [nz]). */
+void wxo_vdiff_coeffs(int nz, double dt, const double *dz,
+                      const double *kappa_lev, double kappa_mult,
+                      double *a, double *b, double *c);
+
+/* Thomas algorithm: solve a_k x_{k-1} + b_k x_k + c_k x_{k+1} = r_k. */
+void wxo_thomas(int nz, const double *a, const double *b, const double *c,
+                const double *r, double *x);
+
+/* Radiative heating H[nz] of one column from its q*[nz]. */
+void wxo_radiation(int nz, const double *qs, const double *alpha,
+                   const double *dz, double S0, double q_ref, double *H);
+
+/* Column physics of ncol independent columns, arrays [ncol][nz]:
+ * Tout = T** + dt H; tend (optional, [ncol][2][nz]) = (H, (T** - T*)/dt). */
+void wxo_physics_columns(int nz, long ncol, double dt, const double *dz,
+                         const double *kappa_lev, const double *kappa_mult,
+                         const double *alpha, double S0, double q_ref,
+                         const double *Ts, const double *qs,
+                         double *Tout, double *tend);
+
+/* One full step (dynamics then physics), out of place. */
+void wxo_step(const wxo_params *p, const double *T, const double *q,
+              const double *U, const double *V, double *Tn, double *qn);
+
+/* n_steps steps with ping-pong buffers; T, q updated in place.  If
+ * mass/energy are non-NULL they receive the sums after every step. */
+void wxo_run(const wxo_params *p, int n_steps, double *T, double *q,
+             const double *U, const double *V, double *mass_q,
+             double *energy_T);
+
+/* h^2 * sum over cells of phi*dz_k, accumulated in order k, j, i. */
+double wxo_column_weighted_sum(const wxo_params *p, const double *phi);
+
+/* Threads the oracle's parallel loops use (1 when built without OpenMP). */
+int wxo_threads(void);
+void wxo_set_threads(int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
