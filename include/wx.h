@@ -1,0 +1,159 @@
+/*
+ * wx.h -- C ABI of the GB300 weather-step library (libwx.so).
+ *
+ * One time step of a structured-grid weather model, the data-parallel hot
+ * path of the paper's reduced weather application (Sec. 3.1) and of its
+ * production model's dynamics + column physics split (Sec. 2 and Sec. 5):
+ *
+ *   dynamics  phi* = phi + dt (kappa_h Lap_h phi + kappa_h Lap_z phi - div(v phi))
+ *             for phi in {T, q}: 7-point finite-volume diffusion (paper Eq. 1,
+ *             explicit Euler), zero flux through bottom and top (the paper's
+ *             appendix diffusion listing uses 1-5d on the end levels),
+ *             periodic in x and y (Sec. 3.1: "cyclic" KI/KJ boundaries), plus
+ *             flux-form first-order upwind advection by C-grid face winds;
+ *   physics   per column (Sec. 3.1: one thread per K column, K sequential,
+ *             Sec. 2.2): implicit vertical diffusion (I - dt L_v) T** = T*
+ *             by the Thomas algorithm, optical depth dtau_k =
+ *             alpha_k dz_k q*_k / q_ref scanned from the top, heating
+ *             H_k = S0 (exp(-tau_top,k) - exp(-tau_bot,k)) / dz_k,
+ *             T^{n+1} = T** + dt H, q^{n+1} = q*.
+ *
+ * Conventions
+ *  - Every call returns a status (WX_OK = 0, negative on error); nothing is
+ *    thrown across the ABI.  wx_last_error() gives a message for the last
+ *    failing call on a context.
+ *  - Host arrays are FP64 and C order: 3D fields [nz][ny][nx], 2D fields
+ *    [ny][nx], per-level arrays [nz].  An FP32 context rounds them once on
+ *    load.
+ *  - The library owns all device memory of a context (fields stay resident
+ *    across steps, the paper's "data region", Sec. 3.2.2 and Sec. 5.1.3);
+ *    arrays passed in are copied and remain owned by the caller.
+ *  - Streams belong to the caller (a cudaStream_t passed as void*, NULL =
+ *    legacy default stream).  wx_step is asynchronous; wx_sync waits and
+ *    reports the device status word.
+ *  - A context is used by one host thread at a time.
+ */
+#ifndef WX_H
+#define WX_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wx_ctx wx_ctx;
+
+/* storage / compute precision of a context */
+enum {
+    WX_F32 = 0,   /* FP32 fields, FP32 arithmetic                               */
+    WX_F64 = 1,   /* FP64 fields, FP64 arithmetic                               */
+    WX_MIXED = 2  /* FP32 fields; FP64 elimination on weakly dominant columns   */
+};
+
+/* status codes */
+enum {
+    WX_OK = 0,
+    WX_EINVAL = -1,      /* bad argument                                       */
+    WX_ENOMEM = -2,      /* device or host allocation failed                   */
+    WX_ECUDA = -3,       /* a CUDA runtime call failed                         */
+    WX_ECFL = -4,        /* parameters/winds violate the positivity bound      */
+    WX_ENONFINITE = -5,  /* a step produced a non-finite value                 */
+    WX_ETIMEOUT = -6,    /* a bounded device wait gave up                      */
+    WX_ESTATE = -7,      /* call out of order (e.g. step before load)          */
+    WX_EUNSUPPORTED = -8 /* size or option outside what this build supports    */
+};
+
+/* wx_params.flags */
+enum {
+    WX_ADVECTION = 1u, /* include the upwind advection term                    */
+    WX_PHYSICS = 2u,   /* run the column physics (Thomas solve + radiation)    */
+    WX_SUMS = 4u       /* record FP64 mass/energy sums after every step        */
+};
+
+typedef struct {
+    double dt;           /* time step (> 0)                                    */
+    double h;            /* horizontal grid spacing (> 0)                      */
+    double kappa_h;      /* diffusivity of the dynamics (>= 0)                 */
+    double S0;           /* top-of-column radiative flux (>= 0)                */
+    double q_ref;        /* optical-depth reference tracer value (> 0)         */
+    double dd_threshold; /* WX_MIXED: columns whose dominance ratio
+                            min_k |b_k|/(|a_k|+|c_k|) is below this run the
+                            elimination in FP64 (<= 0 selects 1.1)             */
+    const double *dz;        /* [nz] layer thickness (> 0), host               */
+    const double *kappa_lev; /* [nz] vertical diffusivity profile (>= 0), host */
+    const double *alpha;     /* [nz] absorber coefficient (>= 0), host         */
+    const double *kappa_mult;/* [ny*nx] per-column multiplier (>= 0) or NULL   */
+    unsigned flags;          /* WX_ADVECTION | WX_PHYSICS | WX_SUMS            */
+} wx_params;
+
+/* Create a context for an nx x ny x nz grid (each >= 1; nz <= 256).
+ * dtype is WX_F32, WX_F64 or WX_MIXED.  Allocates the resident fields.
+ * Errors: WX_EINVAL, WX_EUNSUPPORTED, WX_ENOMEM, WX_ECUDA. */
+int wx_create(int nx, int ny, int nz, int dtype, wx_ctx **out);
+
+/* Copy and validate parameters (positivity of dt, h, q_ref, dz; the
+ * explicit update's coefficients must be non-negative, checked against the
+ * winds at the next wx_step -> WX_ECFL).  Computes the per-level tables on
+ * the device.  May be called again between steps. */
+int wx_set_params(wx_ctx *c, const wx_params *p);
+
+/* Load the state: T, q [nz][ny][nx], face winds U, V [ny][nx] (U on the
+ * east face of cell (i,j), V on its north face).  src_is_device = 0: host
+ * pointers; 1: device pointers (e.g. torch tensors).  FP64 in both cases.
+ * Synchronous.  Resets the sums record. */
+int wx_load_fields(wx_ctx *c, const double *T, const double *q,
+                   const double *U, const double *V, int src_is_device);
+
+/* Advance n_steps >= 0 steps on the caller's stream (asynchronous).  The
+ * fields are updated out of place and the buffers swapped after each step
+ * (paper appendix, time-integration listing).  Errors found on the host
+ * (WX_ESTATE, WX_ECFL) are returned at once; device-side errors surface in
+ * wx_sync. */
+int wx_step(wx_ctx *c, int n_steps, void *cuda_stream);
+
+/* Wait for the context's last stream and return the device status word as
+ * a status (WX_ENONFINITE, WX_ETIMEOUT) or WX_OK.  Clears the word. */
+int wx_sync(wx_ctx *c);
+
+/* Copy the current state to host FP64 arrays T, q [nz][ny][nx] (either may
+ * be NULL).  Synchronous; a checkpoint that wx_load_fields restores. */
+int wx_read_fields(wx_ctx *c, double *T, double *q);
+
+/* Same as wx_read_fields into device FP64 buffers. */
+int wx_read_fields_device(wx_ctx *c, double *T, double *q, void *cuda_stream);
+
+/* Sums recorded with WX_SUMS since the last load: mass_q[s] = h^2 sum q dz,
+ * energy_T[s] = h^2 sum T dz after step s (FP64, deterministic order).
+ * Copies up to max_steps of the most recent entries; *n_out gets the count.
+ * Synchronous. */
+int wx_get_sums(wx_ctx *c, double *mass_q, double *energy_T, int max_steps,
+                int *n_out);
+
+/* Column physics only (the per-column half of the step) on ncol >= 0
+ * independent columns in device memory, in the context's storage type
+ * (float for WX_F32/WX_MIXED, double for WX_F64):
+ *   Tstar, qstar [ncol][nz] in; kappa_mult [ncol] in (NULL = 1);
+ *   Tout [ncol][nz] out = T** + dt H;
+ *   tend [ncol][2][nz] out or NULL: (H_k, (T**_k - T*_k)/dt).
+ * Uses the context's per-level tables (wx_set_params first). Asynchronous. */
+int wx_physics_columns(wx_ctx *c, const void *Tstar, const void *qstar,
+                       const void *kappa_mult, void *Tout, void *tend,
+                       long ncol, void *cuda_stream);
+
+/* Grid and layout facts of a context (any out pointer may be NULL). */
+int wx_info(const wx_ctx *c, int *nx, int *ny, int *nz, int *dtype,
+            long *pitch_cells, long *device_bytes);
+
+/* Number of kernel launches the last wx_step issued. */
+long wx_last_launches(const wx_ctx *c);
+
+/* Free the context and its device memory.  NULL-safe. */
+void wx_destroy(wx_ctx *c);
+
+/* Message of the last failing call on c (or of the last failed wx_create
+ * when c is NULL).  Valid until the next call on c. */
+const char *wx_last_error(const wx_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

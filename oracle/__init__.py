@@ -73,6 +73,9 @@ def lib():
                                           ctypes.c_double, ctypes.c_double,
                                           _D, _D, _D, _D]
         L.wxo_step.argtypes = [P, _D, _D, _D, _D, _D, _D]
+        L.wxo_step_columns.argtypes = [P, _D, _D, _D, _D, ctypes.c_long,
+                                       ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int), _D, _D]
         L.wxo_run.argtypes = [P, ctypes.c_int, _D, _D, _D, _D, _D, _D]
         L.wxo_column_weighted_sum.argtypes = [P, _D]
         L.wxo_column_weighted_sum.restype = ctypes.c_double
@@ -131,6 +134,21 @@ def step(case, T, q, U, V):
     T, q, U, V = map(_f64, (T, q, U, V))
     Tn, qn = np.empty_like(T), np.empty_like(q)
     lib().wxo_step(b.ref(), _ptr(T), _ptr(q), _ptr(U), _ptr(V), _ptr(Tn), _ptr(qn))
+    return Tn, qn
+
+
+def step_columns(case, T, q, U, V, ci, cj):
+    """The step's (T^{n+1}, q^{n+1}) at sampled columns (ci[c], cj[c]),
+    each [ncol][nz]."""
+    b = _Bound(case)
+    T, q, U, V = map(_f64, (T, q, U, V))
+    ci = np.ascontiguousarray(ci, dtype=np.int32)
+    cj = np.ascontiguousarray(cj, dtype=np.int32)
+    n = ci.shape[0]
+    Tn, qn = np.empty((n, case.nz)), np.empty((n, case.nz))
+    IP = ctypes.POINTER(ctypes.c_int)
+    lib().wxo_step_columns(b.ref(), _ptr(T), _ptr(q), _ptr(U), _ptr(V), n,
+                           ci.ctypes.data_as(IP), cj.ctypes.data_as(IP), _ptr(Tn), _ptr(qn))
     return Tn, qn
 
 

@@ -232,6 +232,35 @@ void wxo_step(const wxo_params *p, const double *T, const double *q,
     free(Ts);
 }
 
+void wxo_step_columns(const wxo_params *p, const double *T, const double *q,
+                      const double *U, const double *V, long ncol,
+                      const int *ci, const int *cj, double *Tn, double *qn) {
+    const int nz = p->nz;
+    long col;
+#pragma omp parallel num_threads(wxo_threads())
+    {
+        double *work = (double *)malloc(sizeof(double) * 7 * (size_t)nz);
+        double *cT = work + 5 * nz, *cq = work + 6 * nz;
+#pragma omp for schedule(static)
+        for (col = 0; col < ncol; ++col) {
+            const int i = ci[col], j = cj[col];
+            for (int k = 0; k < nz; ++k) {
+                cT[k] = dyn_cell(p, T, U, V, i, j, k);
+                cq[k] = dyn_cell(p, q, U, V, i, j, k);
+                qn[col * nz + k] = cq[k];
+            }
+            if (p->physics) {
+                const double km = p->kappa_mult ? p->kappa_mult[IDX2(p, i, j)] : 1.0;
+                physics_column(nz, p->dt, p->dz, p->kappa_lev, km, p->alpha, p->S0,
+                               p->q_ref, cT, cq, Tn + col * nz, NULL, NULL, work);
+            } else {
+                for (int k = 0; k < nz; ++k) Tn[col * nz + k] = cT[k];
+            }
+        }
+        free(work);
+    }
+}
+
 double wxo_column_weighted_sum(const wxo_params *p, const double *phi) {
     double s = 0.0;
     for (int k = 0; k < p->nz; ++k)

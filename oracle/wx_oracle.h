@@ -88,6 +88,13 @@ void wxo_physics_columns(int nz, long ncol, double dt, const double *dz,
 void wxo_step(const wxo_params *p, const double *T, const double *q,
               const double *U, const double *V, double *Tn, double *qn);
 
+/* The step's result at ncol sampled columns (i[c], j[c]) only: Tn, qn are
+ * [ncol][nz].  Same arithmetic as wxo_step, for checks at sizes where the
+ * full oracle step is too slow. */
+void wxo_step_columns(const wxo_params *p, const double *T, const double *q,
+                      const double *U, const double *V, long ncol,
+                      const int *ci, const int *cj, double *Tn, double *qn);
+
 /* n_steps steps with ping-pong buffers; T, q updated in place.  If
  * mass/energy are non-NULL they receive the sums after every step. */
 void wxo_run(const wxo_params *p, int n_steps, double *T, double *q,

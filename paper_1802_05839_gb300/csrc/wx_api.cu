@@ -1,0 +1,415 @@
+// wx_api.cu -- the C ABI of libwx.so (declared in include/wx.h): context
+// life cycle, parameter validation, resident-field layout, TMA descriptors,
+// the step loop and the checkpoint / sums read-back.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "wx_internal.cuh"
+
+using namespace wx;
+
+static thread_local std::string g_create_error;
+
+static int fail(wx_ctx *c, int code, const std::string &msg) {
+    if (c)
+        c->err = msg;
+    else
+        g_create_error = msg;
+    return code;
+}
+
+static int cuda_fail(wx_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, WX_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                        \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+#define RC(call)                   \
+    do {                           \
+        int r_ = (call);           \
+        if (r_ != WX_OK) return r_; \
+    } while (0)
+
+// ------------------------------------------------------------ TMA maps
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+namespace wx {
+// Describe a resident field as a 3D tensor of 32-bit words (the bytes are
+// moved untouched): dims {P*words_per_cell, ny+2, nz}; box = 36 cells wide,
+// ty+2 rows, kb planes.
+int encode_tmap(wx_ctx *c, int which, int ty, int kb) {
+    auto enc = tmap_encoder();
+    if (!enc) return fail(c, WX_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const int wpc = c->cell_bytes / 4;
+    cuuint64_t dims[3] = {(cuuint64_t)c->P * wpc, (cuuint64_t)c->R, (cuuint64_t)c->nz};
+    cuuint64_t strides[2] = {(cuuint64_t)c->P * c->cell_bytes, (cuuint64_t)c->P * c->R * c->cell_bytes};
+    cuuint32_t box[3] = {(cuuint32_t)(kBoxX * wpc), (cuuint32_t)(ty + 2), (cuuint32_t)kb};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(&c->tmap[which], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->fld[which], dims, strides, box,
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(c, WX_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")");
+    return WX_OK;
+}
+}  // namespace wx
+
+static int apply_cfg(wx_ctx *c, const StepCfg &g) {
+    c->cfg = g;
+    RC(encode_tmap(c, 0, g.ty, g.kb));
+    RC(encode_tmap(c, 1, g.ty, g.kb));
+    return WX_OK;
+}
+
+// ------------------------------------------------------------ life cycle
+extern "C" int wx_create(int nx, int ny, int nz, int dtype, wx_ctx **out) {
+    if (!out) return fail(nullptr, WX_EINVAL, "wx_create: out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, WX_EINVAL, "wx_create: sizes must be >= 1");
+    if (dtype != WX_F32 && dtype != WX_F64 && dtype != WX_MIXED)
+        return fail(nullptr, WX_EINVAL, "wx_create: unknown dtype");
+    if (nz > 256) return fail(nullptr, WX_EUNSUPPORTED, "wx_create: nz > 256 is not supported");
+    if ((long)nx > (1L << 24) || ny > 65535)
+        return fail(nullptr, WX_EUNSUPPORTED, "wx_create: nx must be < 2^24 and ny <= 65535");
+    wx_ctx *c = new (std::nothrow) wx_ctx();
+    if (!c) return fail(nullptr, WX_ENOMEM, "wx_create: host allocation failed");
+    c->nx = nx;
+    c->ny = ny;
+    c->nz = nz;
+    c->dtype = dtype;
+    c->t_bytes = dtype == WX_F64 ? 8 : 4;
+    c->cell_bytes = 2 * c->t_bytes;
+    c->P = align_up(kGhostX + nx + 1, 16);
+    c->R = ny + 2;
+    c->plane_cells = (size_t)c->P * c->R;
+    c->field_cells = c->plane_cells * nz;
+
+    auto bail = [&](int code) {
+        g_create_error = c->err;
+        wx_destroy(c);
+        return code;
+    };
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        c->err = "wx_create: no CUDA device";
+        return bail(WX_ECUDA);
+    }
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    const size_t fbytes = c->field_cells * c->cell_bytes;
+    const size_t cols = (size_t)nx * ny;
+    const size_t nblk_max = (size_t)((nx + kTileX - 1) / kTileX) * ny;
+    struct {
+        void **p;
+        size_t n;
+    } allocs[] = {{&c->fld[0], fbytes},
+                  {&c->fld[1], fbytes},
+                  {&c->U, cols * c->t_bytes},
+                  {&c->V, cols * c->t_bytes},
+                  {&c->tab, (size_t)nz * kTab * c->t_bytes},
+                  {(void **)&c->d_lev, 3 * (size_t)nz * sizeof(double)},
+                  {(void **)&c->d_status, sizeof(unsigned)},
+                  {(void **)&c->partials, 2 * nblk_max * sizeof(double)},
+                  {(void **)&c->sums_ring, 2 * (size_t)c->sums_cap * sizeof(double)}};
+    for (auto &a : allocs) {
+        cudaError_t e = cudaMalloc(a.p, a.n);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->err = std::string("wx_create: device allocation failed: ") + cudaGetErrorString(e);
+            return bail(WX_ENOMEM);
+        }
+    }
+    c->partials_cap = nblk_max;
+    if (cudaMemset(c->fld[0], 0, fbytes) != cudaSuccess || cudaMemset(c->fld[1], 0, fbytes) != cudaSuccess ||
+        cudaMemset(c->d_status, 0, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(c->U, 0, cols * c->t_bytes) != cudaSuccess ||
+        cudaMemset(c->V, 0, cols * c->t_bytes) != cudaSuccess) {
+        c->err = "wx_create: cudaMemset failed";
+        return bail(WX_ECUDA);
+    }
+    int rc = apply_cfg(c, default_cfg(c));
+    if (rc != WX_OK) return bail(rc);
+    *out = c;
+    return WX_OK;
+}
+
+extern "C" void wx_destroy(wx_ctx *c) {
+    if (!c) return;
+    void *ptrs[] = {c->fld[0], c->fld[1], c->U,        c->V,         c->kmult,     c->tab,
+                    c->d_lev,  c->staging, c->d_status, c->partials, c->sums_ring, c->flag_list,
+                    c->flag_fac, c->flag_mask, c->flag_rhs};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete c;
+}
+
+extern "C" const char *wx_last_error(const wx_ctx *c) {
+    return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+extern "C" int wx_info(const wx_ctx *c, int *nx, int *ny, int *nz, int *dtype, long *pitch, long *bytes) {
+    if (!c) return WX_EINVAL;
+    if (nx) *nx = c->nx;
+    if (ny) *ny = c->ny;
+    if (nz) *nz = c->nz;
+    if (dtype) *dtype = c->dtype;
+    if (pitch) *pitch = c->P;
+    if (bytes) *bytes = (long)(2 * c->field_cells * c->cell_bytes);
+    return WX_OK;
+}
+
+extern "C" long wx_last_launches(const wx_ctx *c) { return c ? c->last_launches : -1; }
+
+// ------------------------------------------------------------ parameters
+static bool finite_pos(double x) { return std::isfinite(x) && x > 0; }
+static bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0; }
+
+extern "C" int wx_set_params(wx_ctx *c, const wx_params *p) {
+    if (!c) return WX_EINVAL;
+    if (!p) return fail(c, WX_EINVAL, "wx_set_params: params is NULL");
+    if (!finite_pos(p->dt) || !finite_pos(p->h) || !finite_pos(p->q_ref))
+        return fail(c, WX_EINVAL, "wx_set_params: dt, h and q_ref must be finite and > 0");
+    if (!finite_nonneg(p->kappa_h) || !finite_nonneg(p->S0))
+        return fail(c, WX_EINVAL, "wx_set_params: kappa_h and S0 must be finite and >= 0");
+    if (!p->dz || !p->kappa_lev || !p->alpha)
+        return fail(c, WX_EINVAL, "wx_set_params: dz, kappa_lev and alpha are required");
+    if (p->flags & ~(unsigned)(WX_ADVECTION | WX_PHYSICS | WX_SUMS))
+        return fail(c, WX_EINVAL, "wx_set_params: unknown flag bits");
+    const int nz = c->nz;
+    for (int k = 0; k < nz; ++k) {
+        if (!finite_pos(p->dz[k])) return fail(c, WX_EINVAL, "wx_set_params: dz must be finite and > 0");
+        if (!finite_nonneg(p->kappa_lev[k]) || !finite_nonneg(p->alpha[k]))
+            return fail(c, WX_EINVAL, "wx_set_params: kappa_lev and alpha must be finite and >= 0");
+    }
+    const size_t cols = (size_t)c->nx * c->ny;
+    if (p->kappa_mult)
+        for (size_t e = 0; e < cols; ++e)
+            if (!finite_nonneg(p->kappa_mult[e]))
+                return fail(c, WX_EINVAL, "wx_set_params: kappa_mult must be finite and >= 0");
+
+    c->dt = p->dt;
+    c->h = p->h;
+    c->kappa_h = p->kappa_h;
+    c->S0 = p->S0;
+    c->q_ref = p->q_ref;
+    c->dd_threshold = p->dd_threshold > 0 ? p->dd_threshold : 1.1;
+    c->flags = p->flags;
+    c->dz.assign(p->dz, p->dz + nz);
+    c->kappa_lev.assign(p->kappa_lev, p->kappa_lev + nz);
+    c->alpha.assign(p->alpha, p->alpha + nz);
+    if (p->kappa_mult)
+        c->kmult_h.assign(p->kappa_mult, p->kappa_mult + cols);
+    else
+        c->kmult_h.clear();
+
+    std::vector<double> lev(3 * (size_t)nz);
+    std::copy(c->dz.begin(), c->dz.end(), lev.begin());
+    std::copy(c->kappa_lev.begin(), c->kappa_lev.end(), lev.begin() + nz);
+    std::copy(c->alpha.begin(), c->alpha.end(), lev.begin() + 2 * nz);
+    CK(cudaMemcpy(c->d_lev, lev.data(), lev.size() * sizeof(double), cudaMemcpyHostToDevice), "upload levels");
+    RC(launch_tables(c, 0));
+    if (p->kappa_mult) {
+        if (!c->kmult) CK(cudaMalloc(&c->kmult, cols * c->t_bytes), "alloc kappa_mult");
+        double *tmp = nullptr;
+        CK(cudaMalloc(&tmp, cols * sizeof(double)), "alloc kappa_mult staging");
+        cudaError_t e = cudaMemcpy(tmp, p->kappa_mult, cols * sizeof(double), cudaMemcpyHostToDevice);
+        int rc = (e == cudaSuccess) ? launch_convert(c, tmp, c->kmult, cols, 0) : cuda_fail(c, e, "upload kappa_mult");
+        cudaDeviceSynchronize();
+        cudaFree(tmp);
+        if (rc != WX_OK) return rc;
+    } else if (c->kmult) {
+        cudaFree(c->kmult);
+        c->kmult = nullptr;
+    }
+    CK(cudaDeviceSynchronize(), "wx_set_params");
+    c->params_set = true;
+    c->cfl_ok = false;
+    return WX_OK;
+}
+
+// Positivity of the explicit update: every coefficient of phi* as a linear
+// combination of old values must be >= 0 (this is what keeps the first-order
+// upwind + diffusion scheme monotone).  Checked on the host from the FP64
+// parameters and winds.
+static int check_cfl(wx_ctx *c) {
+    if (c->cfl_ok) return WX_OK;
+    const int nx = c->nx, ny = c->ny, nz = c->nz;
+    const double dh = c->dt * c->kappa_h / (c->h * c->h), dth = c->dt / c->h;
+    double wmax = 0;
+    for (int k = 0; k < nz; ++k) {
+        double w = 0;
+        if (k < nz - 1) w += c->dt * c->kappa_h / (c->dz[k] * 0.5 * (c->dz[k] + c->dz[k + 1]));
+        if (k > 0) w += c->dt * c->kappa_h / (c->dz[k] * 0.5 * (c->dz[k - 1] + c->dz[k]));
+        wmax = std::max(wmax, w);
+    }
+    double omax = 0;
+    if (c->flags & WX_ADVECTION) {
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const double ue = c->U_h[(size_t)j * nx + i];
+                const double uw = c->U_h[(size_t)j * nx + (i == 0 ? nx - 1 : i - 1)];
+                const double vn = c->V_h[(size_t)j * nx + i];
+                const double vs = c->V_h[(size_t)(j == 0 ? ny - 1 : j - 1) * nx + i];
+                if (!std::isfinite(ue) || !std::isfinite(vn))
+                    return fail(c, WX_EINVAL, "winds must be finite");
+                const double o = std::max(ue, 0.0) - std::min(uw, 0.0) + std::max(vn, 0.0) - std::min(vs, 0.0);
+                omax = std::max(omax, o);
+            }
+    }
+    const double worst = 4 * dh + dth * omax + wmax;
+    if (worst > 1.0 + 1e-12) {
+        char buf[256];
+        snprintf(buf, sizeof buf,
+                 "positivity bound violated: 4*dt*kappa/h^2 + dt/h*max outflow + max vertical weight = %.6g > 1",
+                 worst);
+        return fail(c, WX_ECFL, buf);
+    }
+    c->cfl_ok = true;
+    return WX_OK;
+}
+
+// ------------------------------------------------------------ state I/O
+static int ensure_staging(wx_ctx *c) {
+    if (c->staging) return WX_OK;
+    const size_t n = 2 * (size_t)c->nx * c->ny * c->nz;
+    cudaError_t e = cudaMalloc(&c->staging, n * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->staging = nullptr;
+        return fail(c, WX_ENOMEM, "staging allocation failed");
+    }
+    return WX_OK;
+}
+
+extern "C" int wx_load_fields(wx_ctx *c, const double *T, const double *q, const double *U, const double *V,
+                              int src_is_device) {
+    if (!c) return WX_EINVAL;
+    if (!T || !q || !U || !V) return fail(c, WX_EINVAL, "wx_load_fields: NULL array");
+    const size_t n = (size_t)c->nx * c->ny * c->nz, cols = (size_t)c->nx * c->ny;
+    const double *dT = T, *dq = q, *dU = U, *dV = V;
+    c->U_h.resize(cols);
+    c->V_h.resize(cols);
+    if (!src_is_device) {
+        RC(ensure_staging(c));
+        double *sT = c->staging, *sq = c->staging + n;
+        CK(cudaMemcpy(sT, T, n * sizeof(double), cudaMemcpyHostToDevice), "upload T");
+        CK(cudaMemcpy(sq, q, n * sizeof(double), cudaMemcpyHostToDevice), "upload q");
+        dT = sT;
+        dq = sq;
+        std::memcpy(c->U_h.data(), U, cols * sizeof(double));
+        std::memcpy(c->V_h.data(), V, cols * sizeof(double));
+    } else {
+        CK(cudaMemcpy(c->U_h.data(), U, cols * sizeof(double), cudaMemcpyDeviceToHost), "winds to host");
+        CK(cudaMemcpy(c->V_h.data(), V, cols * sizeof(double), cudaMemcpyDeviceToHost), "winds to host");
+    }
+    c->cur = 0;
+    RC(launch_pack(c, dT, dq, c->fld[0], 0));
+    if (!src_is_device) {
+        // winds through the (now free) staging area
+        double *sU = c->staging, *sV = c->staging + cols;
+        CK(cudaDeviceSynchronize(), "pack");
+        CK(cudaMemcpy(sU, U, cols * sizeof(double), cudaMemcpyHostToDevice), "upload U");
+        CK(cudaMemcpy(sV, V, cols * sizeof(double), cudaMemcpyHostToDevice), "upload V");
+        dU = sU;
+        dV = sV;
+    }
+    RC(launch_convert(c, dU, c->U, cols, 0));
+    RC(launch_convert(c, dV, c->V, cols, 0));
+    CK(cudaDeviceSynchronize(), "wx_load_fields");
+    c->sums_count = 0;
+    c->fields_loaded = true;
+    c->cfl_ok = false;
+    return WX_OK;
+}
+
+extern "C" int wx_read_fields_device(wx_ctx *c, double *T, double *q, void *stream) {
+    if (!c) return WX_EINVAL;
+    if (!c->fields_loaded) return fail(c, WX_ESTATE, "wx_read_fields: no fields loaded");
+    return launch_unpack(c, c->fld[c->cur], T, q, (cudaStream_t)stream);
+}
+
+extern "C" int wx_read_fields(wx_ctx *c, double *T, double *q) {
+    if (!c) return WX_EINVAL;
+    if (!c->fields_loaded) return fail(c, WX_ESTATE, "wx_read_fields: no fields loaded");
+    const size_t n = (size_t)c->nx * c->ny * c->nz;
+    RC(ensure_staging(c));
+    CK(cudaDeviceSynchronize(), "wx_read_fields");
+    RC(launch_unpack(c, c->fld[c->cur], T ? c->staging : nullptr, q ? c->staging + n : nullptr, 0));
+    CK(cudaDeviceSynchronize(), "unpack");
+    if (T) CK(cudaMemcpy(T, c->staging, n * sizeof(double), cudaMemcpyDeviceToHost), "download T");
+    if (q) CK(cudaMemcpy(q, c->staging + n, n * sizeof(double), cudaMemcpyDeviceToHost), "download q");
+    return WX_OK;
+}
+
+// ------------------------------------------------------------ stepping
+extern "C" int wx_step(wx_ctx *c, int n_steps, void *stream) {
+    if (!c) return WX_EINVAL;
+    if (n_steps < 0) return fail(c, WX_EINVAL, "wx_step: n_steps < 0");
+    if (!c->params_set || !c->fields_loaded) return fail(c, WX_ESTATE, "wx_step: set params and load fields first");
+    RC(check_cfl(c));
+    cudaStream_t s = (cudaStream_t)stream;
+    long launches = 0;
+    for (int n = 0; n < n_steps; ++n) RC(launch_step(c, s, &launches));
+    c->last_launches = launches;
+    c->last_stream = s;
+    return WX_OK;
+}
+
+extern "C" int wx_sync(wx_ctx *c) {
+    if (!c) return WX_EINVAL;
+    CK(cudaStreamSynchronize(c->last_stream), "wx_sync");
+    unsigned st = 0;
+    CK(cudaMemcpy(&st, c->d_status, sizeof st, cudaMemcpyDeviceToHost), "read status");
+    if (st) CK(cudaMemset(c->d_status, 0, sizeof(unsigned)), "clear status");
+    if (st & ST_TIMEOUT) return fail(c, WX_ETIMEOUT, "a bounded device wait timed out");
+    if (st & ST_NONFINITE) return fail(c, WX_ENONFINITE, "a step produced a non-finite value");
+    if (st) return fail(c, WX_ECUDA, "device reported an invalid argument");
+    return WX_OK;
+}
+
+extern "C" int wx_get_sums(wx_ctx *c, double *mass_q, double *energy_T, int max_steps, int *n_out) {
+    if (!c) return WX_EINVAL;
+    if (max_steps < 0) return fail(c, WX_EINVAL, "wx_get_sums: max_steps < 0");
+    CK(cudaDeviceSynchronize(), "wx_get_sums");
+    const long avail = std::min<long>(c->sums_count, c->sums_cap);
+    const long n = std::min<long>(avail, max_steps);
+    std::vector<double> ring(2 * (size_t)c->sums_cap);
+    if (n > 0)
+        CK(cudaMemcpy(ring.data(), c->sums_ring, ring.size() * sizeof(double), cudaMemcpyDeviceToHost),
+           "download sums");
+    for (long e = 0; e < n; ++e) {
+        const long step = c->sums_count - n + e;
+        const long slot = step % c->sums_cap;
+        if (mass_q) mass_q[e] = ring[2 * slot];
+        if (energy_T) energy_T[e] = ring[2 * slot + 1];
+    }
+    if (n_out) *n_out = (int)n;
+    return WX_OK;
+}
+
+extern "C" int wx_physics_columns(wx_ctx *c, const void *Ts, const void *qs, const void *km, void *Tout,
+                                  void *tend, long ncol, void *stream) {
+    if (!c) return WX_EINVAL;
+    if (ncol < 0) return fail(c, WX_EINVAL, "wx_physics_columns: ncol < 0");
+    if (ncol > 0 && (!Ts || !qs || !Tout)) return fail(c, WX_EINVAL, "wx_physics_columns: NULL array");
+    if (!c->params_set) return fail(c, WX_ESTATE, "wx_physics_columns: set params first");
+    int rc = launch_columns(c, Ts, qs, km, Tout, tend, ncol, (cudaStream_t)stream);
+    c->last_stream = (cudaStream_t)stream;
+    return rc;
+}

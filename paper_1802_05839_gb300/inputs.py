@@ -52,13 +52,31 @@ def _key(seed: int, stream: int) -> np.uint64:
     return _mix64(base)[0]
 
 
+def _uniform_block(k, start: int, n: int, out: np.ndarray) -> None:
+    z = np.arange(start + 1, start + n + 1, dtype=np.uint64)
+    t = np.empty_like(z)
+    with np.errstate(over="ignore"):
+        np.multiply(z, _GOLDEN, out=z)
+        np.add(z, k, out=z)
+        for sh, mul in ((30, _M1), (27, _M2)):
+            np.right_shift(z, np.uint64(sh), out=t)
+            np.bitwise_xor(z, t, out=z)
+            np.multiply(z, mul, out=z)
+        np.right_shift(z, np.uint64(31), out=t)
+        np.bitwise_xor(z, t, out=z)
+        np.right_shift(z, np.uint64(11), out=z)
+    np.multiply(z, 1.0 / 9007199254740992.0, out=out)
+
+
 def uniform(seed: int, stream: int, n: int, start: int = 0) -> np.ndarray:
     """n doubles in [0, 1) (53-bit), values start..start+n-1 of the stream."""
     k = _key(seed, stream)
-    idx = np.arange(start + 1, start + n + 1, dtype=np.uint64)
-    with np.errstate(over="ignore"):
-        z = k + idx * _GOLDEN
-    return (_mix64(z) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+    out = np.empty(n, dtype=np.float64)
+    blk = 1 << 20
+    for b0 in range(0, n, blk):
+        m = min(blk, n - b0)
+        _uniform_block(k, start + b0, m, out[b0:b0 + m])
+    return out
 
 
 def normal(seed: int, stream: int, n: int) -> np.ndarray:
@@ -125,12 +143,12 @@ def temperature(nx: int, ny: int, nz: int, seed: int) -> np.ndarray:
     ii = np.arange(nx)[None, :] / nx
     jj = np.arange(ny)[:, None] / ny
     kk = (np.arange(nz) + 0.5) / nz
-    T = np.full((nz, ny, nx), 280.0)
-    for m in range(8):
-        plane = A[m] * np.cos(2 * np.pi * (a[m] * ii + b[m] * jj) + ph[m])
-        vert = np.cos(np.pi * c[m] * kk)
-        T += vert[:, None, None] * plane[None, :, :]
-    return T
+    planes = np.stack([A[m] * np.cos(2 * np.pi * (a[m] * ii + b[m] * jj) + ph[m])
+                       for m in range(8)]).reshape(8, ny * nx)
+    vert = np.stack([np.cos(np.pi * c[m] * kk) for m in range(8)], axis=1)  # [nz][8]
+    T = vert @ planes
+    T += 280.0
+    return T.reshape(nz, ny, nx)
 
 
 def tracer(nx: int, ny: int, nz: int, seed: int) -> np.ndarray:
@@ -163,7 +181,8 @@ def winds(nx: int, ny: int, h: float, seed: int, umax: float = 10.0):
         return U, V
 
     U, V = diff(psi)
-    scale = umax / max(np.abs(U).max(), np.abs(V).max())
+    peak = max(np.abs(U).max(), np.abs(V).max())
+    scale = umax / peak if peak > 0 else 0.0  # a 1x1 periodic grid has no wind
     return diff(psi * scale)
 
 

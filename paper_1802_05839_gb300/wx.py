@@ -1,0 +1,188 @@
+"""Thin ctypes binding of libwx.so (include/wx.h).
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels.  Loading fails loudly when the library has not been
+built (``python -m paper_1802_05839_gb300.build``); there is no fallback.
+Functions keep the C names; ``Context`` wraps one ``wx_ctx*``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libwx.so")
+
+WX_F32, WX_F64, WX_MIXED = 0, 1, 2
+WX_ADVECTION, WX_PHYSICS, WX_SUMS = 1, 2, 4
+STATUS = {0: "WX_OK", -1: "WX_EINVAL", -2: "WX_ENOMEM", -3: "WX_ECUDA", -4: "WX_ECFL",
+          -5: "WX_ENONFINITE", -6: "WX_ETIMEOUT", -7: "WX_ESTATE", -8: "WX_EUNSUPPORTED"}
+DTYPES = {"f32": WX_F32, "f64": WX_F64, "mixed": WX_MIXED}
+
+_D = ctypes.POINTER(ctypes.c_double)
+_VP = ctypes.c_void_p
+
+
+class wx_params(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("h", ctypes.c_double), ("kappa_h", ctypes.c_double),
+                ("S0", ctypes.c_double), ("q_ref", ctypes.c_double),
+                ("dd_threshold", ctypes.c_double),
+                ("dz", _D), ("kappa_lev", _D), ("alpha", _D), ("kappa_mult", _D),
+                ("flags", ctypes.c_uint)]
+
+
+class WxError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+# (name, restype, argtypes) of every entry point declared in include/wx.h
+SIGNATURES = [
+    ("wx_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.POINTER(_VP)]),
+    ("wx_set_params", ctypes.c_int, [_VP, ctypes.POINTER(wx_params)]),
+    ("wx_load_fields", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int]),
+    ("wx_step", ctypes.c_int, [_VP, ctypes.c_int, _VP]),
+    ("wx_sync", ctypes.c_int, [_VP]),
+    ("wx_read_fields", ctypes.c_int, [_VP, _VP, _VP]),
+    ("wx_read_fields_device", ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    ("wx_get_sums", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    ("wx_physics_columns", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_long, _VP]),
+    ("wx_info", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                               ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long)]),
+    ("wx_last_launches", ctypes.c_long, [_VP]),
+    ("wx_destroy", None, [_VP]),
+    ("wx_last_error", ctypes.c_char_p, [_VP]),
+]
+
+
+def lib():
+    """Load libwx.so (raises if it is missing: there is no CPU fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -m paper_1802_05839_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code, ctx=None):
+    if code != 0:
+        msg = lib().wx_last_error(ctx)
+        raise WxError(code, msg.decode() if msg else "")
+
+
+def _dptr(a):
+    """Device pointer of a torch tensor, or host pointer of a numpy array."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+class Context:
+    """One wx_ctx*: resident fields of an nx x ny x nz grid."""
+
+    def __init__(self, nx, ny, nz, dtype="f32"):
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.dtype = dtype
+        p = _VP()
+        _check(lib().wx_create(self.nx, self.ny, self.nz, DTYPES[dtype], ctypes.byref(p)))
+        self.ptr = p
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            lib().wx_destroy(self.ptr)
+            self.ptr = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- parameters ----------------------------------------------------
+    def set_params(self, case, flags=None, dd_threshold=0.0):
+        if flags is None:
+            flags = (WX_ADVECTION if case.advection else 0) | (WX_PHYSICS if case.physics else 0)
+        arr = lambda a: None if a is None else np.ascontiguousarray(a, np.float64).reshape(-1)
+        keep = [arr(case.dz), arr(case.kappa_lev), arr(case.alpha), arr(case.kappa_mult)]
+        ptr = lambda a: None if a is None else a.ctypes.data_as(_D)
+        p = wx_params(case.dt, case.h, case.kappa_h, case.S0, case.q_ref, dd_threshold,
+                      ptr(keep[0]), ptr(keep[1]), ptr(keep[2]), ptr(keep[3]), flags)
+        self._keep = keep
+        _check(lib().wx_set_params(self.ptr, ctypes.byref(p)), self.ptr)
+
+    # -- state ---------------------------------------------------------
+    def load_fields(self, T, q, U, V):
+        """numpy FP64 (host) or torch FP64 CUDA tensors (device)."""
+        dev = hasattr(T, "data_ptr")
+        if not dev:
+            T, q, U, V = (np.ascontiguousarray(a, np.float64) for a in (T, q, U, V))
+        _check(lib().wx_load_fields(self.ptr, _dptr(T), _dptr(q), _dptr(U), _dptr(V), int(dev)),
+               self.ptr)
+
+    def read_fields(self):
+        n = (self.nz, self.ny, self.nx)
+        T, q = np.empty(n), np.empty(n)
+        _check(lib().wx_read_fields(self.ptr, _dptr(T), _dptr(q)), self.ptr)
+        return T, q
+
+    def read_fields_into(self, T, q, stream=None):
+        """Device FP64 outputs (torch tensors), asynchronous on `stream`."""
+        _check(lib().wx_read_fields_device(self.ptr, _dptr(T), _dptr(q), _stream_ptr(stream)),
+               self.ptr)
+
+    def step(self, n_steps=1, stream=None):
+        _check(lib().wx_step(self.ptr, int(n_steps), _stream_ptr(stream)), self.ptr)
+
+    def sync(self):
+        _check(lib().wx_sync(self.ptr), self.ptr)
+
+    def sums(self, max_steps=4096):
+        m, e = np.empty(max_steps), np.empty(max_steps)
+        n = ctypes.c_int(0)
+        _check(lib().wx_get_sums(self.ptr, _dptr(m), _dptr(e), max_steps, ctypes.byref(n)), self.ptr)
+        return m[:n.value], e[:n.value]
+
+    def physics_columns(self, Ts, qs, kappa_mult, Tout, tend=None, stream=None):
+        """Device arrays (torch tensors) of the context's storage type."""
+        ncol = Ts.shape[0]
+        _check(lib().wx_physics_columns(self.ptr, _dptr(Ts), _dptr(qs), _dptr(kappa_mult),
+                                        _dptr(Tout), _dptr(tend), ncol, _stream_ptr(stream)),
+               self.ptr)
+
+    def info(self):
+        v = [ctypes.c_int() for _ in range(4)]
+        pitch, nbytes = ctypes.c_long(), ctypes.c_long()
+        _check(lib().wx_info(self.ptr, *[ctypes.byref(x) for x in v], ctypes.byref(pitch),
+                             ctypes.byref(nbytes)))
+        return dict(nx=v[0].value, ny=v[1].value, nz=v[2].value, dtype=v[3].value,
+                    pitch=pitch.value, device_bytes=nbytes.value)
+
+    def last_launches(self):
+        return int(lib().wx_last_launches(self.ptr))

@@ -1,0 +1,61 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point include/*.h declares, and the binding names them all."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1802_05839_gb300 import wx
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(wx\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(wx.LIB_PATH):
+        from paper_1802_05839_gb300 import build
+        build.build()
+    return wx.lib()
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for n in ("wx_create", "wx_set_params", "wx_load_fields", "wx_step", "wx_physics_columns",
+              "wx_destroy", "wx_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for n in sorted(declared_functions()):
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+
+
+def test_binding_covers_every_declared_symbol():
+    bound = {n for n, _, _ in wx.SIGNATURES}
+    missing = declared_functions() - bound
+    assert not missing, missing
+
+
+def test_create_fails_cleanly_without_gpu_or_with_bad_args(lib):
+    p = ctypes.c_void_p()
+    assert lib.wx_create(0, 4, 4, 0, ctypes.byref(p)) == -1
+    assert b"sizes" in lib.wx_last_error(None)
+    assert lib.wx_create(4, 4, 4, 7, ctypes.byref(p)) == -1
+    assert lib.wx_create(4, 4, 300, 0, ctypes.byref(p)) == -8
+    assert lib.wx_create(4, 4, 4, 0, None) == -1
+    lib.wx_destroy(None)  # NULL-safe
+    assert lib.wx_step(None, 1, None) == -1
+    assert lib.wx_sync(None) == -1

@@ -291,3 +291,15 @@ def test_near_singular_columns_have_low_dominance():
         a, b, cc = oracle.vdiff_coeffs(c.nz, c.dt, c.dz, c.kappa_lev, s)
         ratios.append(np.min(np.abs(b) / (np.abs(a) + np.abs(cc))))
     assert ratios[0] > 1.1 and ratios[1] < 1.1
+
+
+def test_step_columns_equals_full_step():
+    """The sampled-column form of the step is the full step restricted to
+    those columns (bitwise: same arithmetic, same order)."""
+    c = _generated(13, 11, 9, S0=1.0, near_singular=True)
+    Tn, qn = oracle.step(c, c.T, c.q, c.U, c.V)
+    ci = np.array([0, 12, 5, 0, 12])
+    cj = np.array([0, 10, 4, 10, 0])
+    Ts, qs = oracle.step_columns(c, c.T, c.q, c.U, c.V, ci, cj)
+    assert np.array_equal(Ts, Tn[:, cj, ci].T)
+    assert np.array_equal(qs, qn[:, cj, ci].T)
