@@ -146,6 +146,31 @@ int wx_info(const wx_ctx *c, int *nx, int *ny, int *nz, int *dtype,
 /* Number of kernel launches the last wx_step issued. */
 long wx_last_launches(const wx_ctx *c);
 
+/* FP64 sums of caller-owned fields without any device allocation.  The
+ * paper has no counterpart: this exists for callers that cannot allocate
+ * device memory (inside a CUDA-graph capture, under an allocator that owns
+ * every device byte, or in a latency-bound loop).
+ *   T, q     device arrays [nz][ny][nx], float (dtype WX_F32) or double
+ *            (WX_F64);
+ *   dz       device array [nz] of double;
+ *   out      device array of 2 doubles: out[0] = h^2 sum q dz_k,
+ *            out[1] = h^2 sum T dz_k (deterministic order).
+ * Per-tile partial sums go to one fixed __device__ array inside the library
+ * (1 MiB, held by each GPU that loads it until the process exits), so grids
+ * needing more than 65536 tiles of 32x4 columns are rejected with
+ * WX_EUNSUPPORTED.  Nothing has to be cleared between calls, but calls
+ * sharing that array must not overlap on the GPU (they would race).  The
+ * first call on a device looks up the array's address with that device
+ * current; make it before any stream capture.  Asynchronous on the stream.
+ * Errors: WX_EINVAL, WX_EUNSUPPORTED, WX_ECUDA; message in
+ * wx_sums_noalloc_error(). */
+int wx_sums_noalloc(const void *T, const void *q, int dtype, int nx, int ny,
+                    int nz, const double *dz, double h, double *out,
+                    void *cuda_stream);
+
+/* Message of the last failing wx_sums_noalloc call on this host thread. */
+const char *wx_sums_noalloc_error(void);
+
 /* Free the context and its device memory.  NULL-safe. */
 void wx_destroy(wx_ctx *c);
 

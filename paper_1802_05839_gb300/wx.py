@@ -57,6 +57,9 @@ SIGNATURES = [
                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long)]),
     ("wx_last_launches", ctypes.c_long, [_VP]),
+    ("wx_sums_noalloc", ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, _VP, ctypes.c_double, _VP, _VP]),
+    ("wx_sums_noalloc_error", ctypes.c_char_p, []),
     ("wx_destroy", None, [_VP]),
     ("wx_last_error", ctypes.c_char_p, [_VP]),
 ]
@@ -186,3 +189,17 @@ class Context:
 
     def last_launches(self):
         return int(lib().wx_last_launches(self.ptr))
+
+
+def wx_sums_noalloc(T, q, dz, h, out, stream=None):
+    """FP64 (mass_q, energy_T) sums of device fields T, q [nz][ny][nx] (torch
+    float32 or float64 CUDA tensors) into the device tensor out[2], with no
+    device allocation (see include/wx.h)."""
+    import torch
+    nz, ny, nx = T.shape
+    dtype = WX_F32 if T.dtype == torch.float32 else WX_F64
+    code = lib().wx_sums_noalloc(_dptr(T), _dptr(q), dtype, nx, ny, nz, _dptr(dz), float(h),
+                                 _dptr(out), _stream_ptr(stream))
+    if code != 0:
+        raise WxError(code, lib().wx_sums_noalloc_error().decode())
+
