@@ -143,6 +143,17 @@ int wx_physics_columns(wx_ctx *c, const void *Tstar, const void *qstar,
 int wx_info(const wx_ctx *c, int *nx, int *ny, int *nz, int *dtype,
             long *pitch_cells, long *device_bytes);
 
+/* Launch configuration of the step kernel (the autotuner's knobs): tile
+ * rows ty (1, 2, 4 or 8; a tile is 64 x ty columns), TMA ring stages
+ * (2..16, two k-planes each), resident CTAs per SM (>= 1) and the L2
+ * prefetch distance in stages (0..64).  Rejected with WX_EUNSUPPORTED when
+ * the shared-memory plan does not fit.  wx_get_step_config reads the
+ * current one (chosen by a built-in heuristic until set). */
+int wx_set_step_config(wx_ctx *c, int ty, int stages, int ctas_per_sm,
+                       int prefetch);
+int wx_get_step_config(const wx_ctx *c, int *ty, int *stages,
+                       int *ctas_per_sm, int *prefetch, int *smem_bytes);
+
 /* Number of kernel launches the last wx_step issued. */
 long wx_last_launches(const wx_ctx *c);
 

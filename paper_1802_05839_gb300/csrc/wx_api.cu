@@ -53,19 +53,21 @@ static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
 }
 
 namespace wx {
-// Describe a resident field as a 3D tensor of 32-bit words (the bytes are
-// moved untouched): dims {P*words_per_cell, ny+2, nz}; box = 36 cells wide,
-// ty+2 rows, kb planes.
+// Describe a resident state as a 4D tensor of T elements {x: P, y: ny+2,
+// field: 2, z: nz} (planar T and q planes per level); box = 72 x (ty+2) x 2
+// fields x kb planes, x start a multiple of 4 elements (16-byte aligned).
 int encode_tmap(wx_ctx *c, int which, int ty, int kb) {
     auto enc = tmap_encoder();
     if (!enc) return fail(c, WX_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
-    const int wpc = c->cell_bytes / 4;
-    cuuint64_t dims[3] = {(cuuint64_t)c->P * wpc, (cuuint64_t)c->R, (cuuint64_t)c->nz};
-    cuuint64_t strides[2] = {(cuuint64_t)c->P * c->cell_bytes, (cuuint64_t)c->P * c->R * c->cell_bytes};
-    cuuint32_t box[3] = {(cuuint32_t)(kBoxX * wpc), (cuuint32_t)(ty + 2), (cuuint32_t)kb};
-    cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = enc(&c->tmap[which], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->fld[which], dims, strides, box,
-                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+    const cuuint64_t t = (cuuint64_t)c->t_bytes;
+    cuuint64_t dims[4] = {(cuuint64_t)c->P, (cuuint64_t)c->R, 2, (cuuint64_t)c->nz};
+    cuuint64_t strides[3] = {(cuuint64_t)c->P * t, (cuuint64_t)c->P * c->R * t, 2 * (cuuint64_t)c->P * c->R * t};
+    cuuint32_t box[4] = {(cuuint32_t)kBoxX, (cuuint32_t)(ty + 2), 2, (cuuint32_t)kb};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUtensorMapDataType dt =
+        c->t_bytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    CUresult r = enc(&c->tmap[which], dt, 4, c->fld[which], dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(c, WX_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")");
     return WX_OK;
@@ -122,7 +124,7 @@ extern "C" int wx_create(int nx, int ny, int nz, int dtype, wx_ctx **out) {
                   {&c->fld[1], fbytes},
                   {&c->U, cols * c->t_bytes},
                   {&c->V, cols * c->t_bytes},
-                  {&c->tab, (size_t)nz * kTab * c->t_bytes},
+                  {&c->tab, (size_t)nz * kTabRec * 4 * c->t_bytes},
                   {(void **)&c->d_lev, 3 * (size_t)nz * sizeof(double)},
                   {(void **)&c->d_status, sizeof(unsigned)},
                   {(void **)&c->partials, 2 * nblk_max * sizeof(double)},
@@ -175,6 +177,33 @@ extern "C" int wx_info(const wx_ctx *c, int *nx, int *ny, int *nz, int *dtype, l
 }
 
 extern "C" long wx_last_launches(const wx_ctx *c) { return c ? c->last_launches : -1; }
+
+extern "C" int wx_set_step_config(wx_ctx *c, int ty, int stages, int ctas_per_sm, int prefetch) {
+    if (!c) return WX_EINVAL;
+    if (!(ty == 1 || ty == 2 || ty == 4 || ty == 8) || stages < 2 || stages > 16 || ctas_per_sm < 1 ||
+        prefetch < 0 || prefetch > 64)
+        return fail(c, WX_EINVAL, "wx_set_step_config: ty in {1,2,4,8}, stages 2..16, ctas >= 1, prefetch 0..64");
+    StepCfg g;
+    g.ty = ty;
+    g.stages = stages;
+    g.kb = 2;
+    g.ctas_per_sm = ctas_per_sm;
+    g.prefetch = prefetch;
+    if (!cfg_fits(c, g, nullptr)) return fail(c, WX_EUNSUPPORTED, "wx_set_step_config: shared memory does not fit");
+    RC(apply_cfg(c, g));
+    c->cfg_forced = true;
+    return WX_OK;
+}
+
+extern "C" int wx_get_step_config(const wx_ctx *c, int *ty, int *stages, int *ctas, int *prefetch, int *smem) {
+    if (!c) return WX_EINVAL;
+    if (ty) *ty = c->cfg.ty;
+    if (stages) *stages = c->cfg.stages;
+    if (ctas) *ctas = c->cfg.ctas_per_sm;
+    if (prefetch) *prefetch = c->cfg.prefetch;
+    if (smem) cfg_fits(c, c->cfg, smem);
+    return WX_OK;
+}
 
 // ------------------------------------------------------------ parameters
 static bool finite_pos(double x) { return std::isfinite(x) && x > 0; }
@@ -238,6 +267,8 @@ extern "C" int wx_set_params(wx_ctx *c, const wx_params *p) {
         c->kmult = nullptr;
     }
     CK(cudaDeviceSynchronize(), "wx_set_params");
+    // the kernel variant (and its shared-memory plan) depends on kappa_mult
+    if (!c->cfg_forced || !cfg_fits(c, c->cfg, nullptr)) RC(apply_cfg(c, default_cfg(c)));
     c->params_set = true;
     c->cfl_ok = false;
     return WX_OK;

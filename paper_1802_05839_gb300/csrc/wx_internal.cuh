@@ -14,19 +14,32 @@
 namespace wx {
 
 // ---------------------------------------------------------------- layout
-// Resident fields are stored as interleaved (T, q) cells, x fastest:
-//   cell[k][jp][ip],  jp = j + 1 in [0, ny+2),  ip = i + kGhostX in [0, P).
-// Row jp = 0 and jp = ny+1 and columns ip = kGhostX-1 and ip = kGhostX+nx
-// are the periodic ghost ring (copies of the opposite interior edge).  The
-// interior starts kGhostX cells into each row so that a warp's 32-cell row
-// segment starts on a 128-byte boundary in FP32.
+// Resident fields are stored plane by plane, x fastest:
+//   fld[((k*2 + f)*R + jp)*P + ip],  f = 0 (T) or 1 (q),
+//   jp = j + 1 in [0, R = ny+2),  ip = i + kGhostX in [0, P).
+// Rows jp = 0 and jp = ny+1 and columns ip = kGhostX-1 and ip = kGhostX+nx
+// form the periodic ghost ring (copies of the opposite interior edge).  The
+// interior starts kGhostX cells into each row so that a warp's 64-column row
+// segment starts on a 64-byte boundary in FP32.
 constexpr int kGhostX = 16;
-constexpr int kTileX = 32;       // columns per tile in x (one warp)
-constexpr int kBoxX = 36;        // TMA box width in cells: 32 + halo, even start
-constexpr int kTab = 8;          // per-level table entries
+constexpr int kTileX = 64;     // columns per tile in x (one warp, 2 per lane)
+constexpr int kBoxX = 72;      // TMA box width: 64 + halo, start a multiple of 4
+constexpr int kBoxX0 = 4;      // interior column 0 of a tile sits at box x = 4
+constexpr int kTabRec = 5;     // 4-value records per level in the table
 
-// per-level table entries (one row of kTab values per level k)
-enum { TAB_WU = 0, TAB_WD, TAB_AHAT, TAB_CHAT, TAB_WTAU, TAB_WH, TAB_DZ, TAB_PAD };
+// Per-level table: kTabRec record arrays of nz records, record-major:
+//  A[k] = {wU, wU, wD, wD}          explicit vertical weights, paired for f32x2
+//  B[k] = {-(wU+wD), -(wU+wD), wt2, wt2}  centre correction; optical depth per
+//                                   unit q in log2 units, alpha dz log2(e)/q_ref
+//  C[k] = {wH, wH, -c_k, -c_k}      dt S0/dz_k; minus the super-diagonal of the
+//                                   kappa_mult = 1 column
+//  D[k] = {1/m_k, 1/m_k, e_k, e_k}  that column's top-down elimination:
+//                                   m_k = b_k - c_k e_{k+1}, e_k = a_k/m_k
+//  E[k] = {ahat_k, chat_k, dz_k, 0} sub/super-diagonal per unit kappa_mult
+// with wU = dt kappa_h/(dz_k g_{k+1/2}) (0 at the top), wD likewise below.
+enum { REC_A = 0, REC_B = 1, REC_C = 2, REC_D = 3, REC_E = 4 };
+
+template <typename T> struct alignas(4 * sizeof(T)) Q4 { T x, y, z, w; };
 
 // device status word bits
 enum : unsigned { ST_NONFINITE = 1u, ST_TIMEOUT = 2u, ST_BADARG = 4u };
@@ -36,21 +49,22 @@ template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };
 
 template <typename T> struct StepArgs {
-    typename Vec2<T>::type *out;  // new state (interleaved cells)
+    T *out;                       // new state (planar fields)
     const T *U, *V;               // face winds [ny][nx]
     const T *kmult;               // [ny][nx] or nullptr
-    const T *tab;                 // [nz][kTab]
+    const Q4<T> *tab;             // [kTabRec][nz]
     unsigned *status;
-    double *partials;             // [gridDim.x*gridDim.y][2] (sums)
+    double *partials;             // [tiles][2] (sums)
     int nx, ny, nz, P, R;
     T dth, dh;                    // dt/h, dt*kappa_h/h^2
     int advection;
 };
 
-// A step-kernel configuration: rows per tile, pipeline stages and planes
-// per stage.  Chosen per grid by the launcher (or by the autotuner).
+// A step-kernel configuration: rows per tile, TMA ring stages (2 planes
+// each), resident CTAs per SM and L2 prefetch distance in stages.  Chosen by
+// a heuristic at create time or set by the autotuner.
 struct StepCfg {
-    int ty = 4, stages = 6, kb = 2;
+    int ty = 2, stages = 4, kb = 2, ctas_per_sm = 4, prefetch = 8;
 };
 
 struct SmemPlan {
@@ -59,16 +73,21 @@ struct SmemPlan {
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline SmemPlan plan_smem(int nz, int ty, int stages, int kb, int cell_bytes,
-                                              int t_bytes, int narr) {
+// Shared-memory plan of the step kernel: per-level table, TMA ring of
+// `stages` slots (kb planes x 2 fields x (ty+2) rows x kBoxX), per-thread
+// column state (F_k of the lane's two columns, plus their e_k for per-column
+// kappa), then full/empty mbarriers.
+__host__ __device__ inline SmemPlan plan_smem(int nz, int ty, int stages, int kb, int t_bytes,
+                                              bool per_col) {
     SmemPlan p;
-    const int nt = kTileX * ty;
+    const int nt = 32 * ty;
     p.tab_off = 0;
-    p.ring_off = align_up(nz * kTab * t_bytes, 128);
-    p.stage_bytes = align_up(kb * (ty + 2) * kBoxX * cell_bytes, 128);
+    p.ring_off = align_up(kTabRec * nz * 4 * t_bytes, 128);
+    p.stage_bytes = align_up(kb * 2 * (ty + 2) * kBoxX * t_bytes, 128);
     p.state_off = align_up(p.ring_off + stages * p.stage_bytes, 128);
-    p.bar_off = align_up(p.state_off + narr * nz * nt * t_bytes, 16);
-    p.total = p.bar_off + stages * 8 + 16;
+    const int state = nz * nt * 2 * t_bytes * (per_col ? 2 : 1);
+    p.bar_off = align_up(p.state_off + state, 16);
+    p.total = p.bar_off + 2 * stages * 8 + 16;
     return p;
 }
 
@@ -78,7 +97,7 @@ __host__ __device__ inline SmemPlan plan_smem(int nz, int ty, int stages, int kb
 struct wx_ctx {
     int nx = 0, ny = 0, nz = 0, dtype = 0;
     int P = 0, R = 0;            // row pitch (cells) and rows per plane
-    size_t plane_cells = 0, field_cells = 0;
+    size_t plane_cells = 0, field_cells = 0;  // one (k, f) plane; whole array
     int cell_bytes = 0, t_bytes = 0;
     int device = 0, num_sms = 0;
 
@@ -104,9 +123,9 @@ struct wx_ctx {
 
     // WX_MIXED: columns whose elimination runs in FP64
     int *flag_list = nullptr;    // [n_flag] column index j*nx+i
-    double *flag_fac = nullptr;  // [nz][n_flag][2] FP64 elimination factors
+    double *flag_fac = nullptr;  // FP64 elimination factors of flagged columns
     unsigned char *flag_mask = nullptr;  // [ny*nx]
-    float *flag_rhs = nullptr;   // [nz][n_flag] T* of flagged columns
+    float *flag_rhs = nullptr;   // side buffer of flagged columns
     long n_flag = 0;
 
     wx::StepCfg cfg;

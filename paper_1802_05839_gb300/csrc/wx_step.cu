@@ -1,30 +1,30 @@
 // wx_step.cu -- the fused weather-step kernel and its helpers.
 //
-// One CTA owns a 32 x TY tile of columns and walks it bottom to top once
-// (pass 1) and top to bottom once (pass 2):
+// One step n -> n+1 for every column (i, j), in two sweeps over k:
 //
-//   pass 1, level k = 0 .. nz-1
-//     TMA stages k-slabs of the (T, q) cell array, tile plus a one-cell halo,
-//     into a ring of shared-memory stages (mbarrier completion).  Each thread
-//     forms phi* for its column at level k from the 5-point horizontal
-//     neighbourhood in shared memory and the vertical neighbours it carries in
-//     registers (dynamics, paper Eq. 1 + upwind advection), then runs the
-//     Thomas forward elimination of the implicit vertical diffusion for T*
-//     (the K dependency the paper keeps sequential, Sec. 2.2) and parks c'_k,
-//     d'_k and q*_k in shared memory.
-//   pass 2, level k = nz-1 .. 0
-//     back substitution x_k = d'_k - c'_k x_{k+1}, the optical-depth scan from
-//     the top and the heating H_k, then one 8-byte (16-byte in FP64) store of
-//     the new (T, q) cell, plus ghost-ring copies from edge tiles.
+//   pass 1, top -> bottom (k = nz-1 .. 0)
+//     dynamics: phi* = cC phi + cE phi_E + cW phi_W + cN phi_N + cS phi_S
+//                      + wU_k (phi_{k+1} - phi_k) - wD_k (phi_k - phi_{k-1})
+//       for phi in {T, q} (paper Eq. 1 diffusion, explicit Euler, zero flux
+//       at the column ends, periodic x/y; first-order upwind advection by
+//       C-grid face winds folded into cE..cS, U+ = max(U,0), U- = min(U,0):
+//         cE = dh - dth Ue-,  cW = dh + dth Uw+,  cN = dh - dth Vn-,
+//         cS = dh + dth Vs+,  cC = 1 - 4 dh - dth (Ue+ - Uw- + Vn+ - Vs-));
+//     q^{n+1} = q* is stored at once;
+//     radiation: tau accumulates from the top, H_k = S0 (2^-tau2_top -
+//       2^-tau2_bot) / dz_k with tau carried in log2 units;
+//     implicit vertical diffusion (I - dt L_v) x = T*: the Thomas elimination
+//       run from the top, f_k = (T*_k - c_k f_{k+1}) / m_k, m_k = b_k -
+//       c_k e_{k+1}, e_k = a_k / m_k (the K recurrence the paper keeps
+//       sequential, Sec. 2.2);
+//     the heating is folded into the back substitution: with T^{n+1}_k =
+//       x_k + dt H_k and x_k = f_k - e_k x_{k-1},
+//         T^{n+1}_k = F_k - e_k T^{n+1}_{k-1},  F_k = f_k + h_k + e_k h_{k-1},
+//       h = dt H, so one value F_k per level is parked in shared memory.
+//   pass 2, bottom -> top: T^{n+1}_k = F_k - e_k T^{n+1}_{k-1}, stored.
 //
-// Each field crosses HBM once per step in each direction.  The horizontal
-// operator is rewritten as per-column coefficients
-//   phi* = cC phi + cE phi_E + cW phi_W + cN phi_N + cS phi_S
-//          + wU_k (phi_{k+1} - phi_k) - wD_k (phi_k - phi_{k-1}),
-// with the upwind choice folded into cE..cS (U+ = max(U,0), U- = min(U,0)):
-//   cE = dh - dth Ue-,  cW = dh + dth Uw+,  cN = dh - dth Vn-,  cS = dh + dth Vs+,
-//   cC = 1 - 4 dh - dth (Ue+ - Uw- + Vn+ - Vs-),
-// the same linear map as the flux form, evaluated in a different order.
+// Each field crosses HBM once per step in each direction.
+#include <algorithm>
 #include <cstdio>
 
 #include "ptx.cuh"
@@ -32,36 +32,66 @@
 
 namespace wx {
 
-template <typename T> __device__ __forceinline__ T exp_neg(T x);
-template <> __device__ __forceinline__ float exp_neg<float>(float x) { return __expf(-x); }
-template <> __device__ __forceinline__ double exp_neg<double>(double x) { return exp(-x); }
+// ------------------------------------------------------------ arithmetic
+// Paired arithmetic on the lane's two columns: one packed f32x2 instruction
+// in FP32 (sm_100+ FFMA2/FADD2/FMUL2), two scalar ones in FP64.
+template <typename T> struct Pk;
+template <> struct Pk<float> {
+    using V = float2;
+    static __device__ __forceinline__ V fma(V a, V b, V c) { return __ffma2_rn(a, b, c); }
+    static __device__ __forceinline__ V mul(V a, V b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ V add(V a, V b) { return __fadd2_rn(a, b); }
+    static __device__ __forceinline__ V dup(float x) { return make_float2(x, x); }
+};
+template <> struct Pk<double> {
+    using V = double2;
+    static __device__ __forceinline__ V fma(V a, V b, V c) {
+        return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y));
+    }
+    static __device__ __forceinline__ V mul(V a, V b) { return make_double2(a.x * b.x, a.y * b.y); }
+    static __device__ __forceinline__ V add(V a, V b) { return make_double2(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ V dup(double x) { return make_double2(x, x); }
+};
+
+// 2^-x: the optical depth is carried in log2 units, so exp(-tau) = 2^-tau2.
+template <typename T> __device__ __forceinline__ T exp2_neg(T x);
+template <> __device__ __forceinline__ float exp2_neg<float>(float x) { return exp2f(-x); }
+template <> __device__ __forceinline__ double exp2_neg<double>(double x) { return exp2(-x); }
 
 template <typename T> __device__ __forceinline__ T recip(T m);
 template <> __device__ __forceinline__ float recip<float>(float m) { return __frcp_rn(m); }
 template <> __device__ __forceinline__ double recip<double>(double m) { return 1.0 / m; }
 
-template <typename T> __device__ __forceinline__ bool finite(T x) { return isfinite(x); }
-
-// Column sum of phi*dz in the storage precision, compensated in FP32 so the
-// FP64 total that follows is not limited by a 58-term FP32 sum.
-template <typename T> struct ColSum;
-template <> struct ColSum<float> {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float v, float w) {
-        const float p = v * w;
-        const float pe = fmaf(v, w, -p);  // exact product error
-        const float s1 = s + p;           // TwoSum(s, p)
-        const float bp = s1 - s;
-        const float e = (s - (s1 - bp)) + (p - bp);
-        c += e + pe;
+// Column sums of phi*dz for the lane's two columns, compensated in FP32
+// (exact product error + TwoSum) so the FP64 total is not limited by a
+// 58-term FP32 sum; plain FMA accumulation in FP64.
+template <typename T> struct ColSum2;
+template <> struct ColSum2<float> {
+    float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+    __device__ __forceinline__ void add(float2 v, float w) {
+        const float2 w2 = make_float2(w, w), m1 = make_float2(-1.f, -1.f);
+        const float2 p = __fmul2_rn(v, w2);
+        const float2 pe = __ffma2_rn(v, w2, __fmul2_rn(p, m1));
+        const float2 s1 = __fadd2_rn(s, p);
+        const float2 bp = __ffma2_rn(s, m1, s1);  // s1 - s
+        const float2 sa = __ffma2_rn(bp, m1, s1); // s1 - bp
+        const float2 e = __fadd2_rn(__ffma2_rn(sa, m1, s), __ffma2_rn(bp, m1, p));
+        c = __fadd2_rn(c, __fadd2_rn(e, pe));
         s = s1;
     }
-    __device__ __forceinline__ double total() const { return (double)s + (double)c; }
+    __device__ __forceinline__ double total(bool va, bool vb) const {
+        return (va ? (double)s.x + (double)c.x : 0.0) + (vb ? (double)s.y + (double)c.y : 0.0);
+    }
 };
-template <> struct ColSum<double> {
-    double s = 0.0;
-    __device__ __forceinline__ void add(double v, double w) { s = fma(v, w, s); }
-    __device__ __forceinline__ double total() const { return s; }
+template <> struct ColSum2<double> {
+    double2 s = make_double2(0.0, 0.0);
+    __device__ __forceinline__ void add(double2 v, double w) {
+        s.x = ::fma(v.x, w, s.x);
+        s.y = ::fma(v.y, w, s.y);
+    }
+    __device__ __forceinline__ double total(bool va, bool vb) const {
+        return (va ? s.x : 0.0) + (vb ? s.y : 0.0);
+    }
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -70,220 +100,370 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-template <typename T, int TY, int KB, bool PHYS, bool SUMS>
-__global__ void __launch_bounds__(32 * TY) step_kernel(const __grid_constant__ CUtensorMap tin,
-                                                       const StepArgs<T> a, const int S) {
-    using C2 = typename Vec2<T>::type;
-    constexpr int NT = 32 * TY;
-    constexpr int PC = (TY + 2) * kBoxX;  // cells per staged plane
-    extern __shared__ __align__(128) unsigned char smem[];
-
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const int i = blockIdx.x * kTileX + tx, j = blockIdx.y * TY + ty;
-    const bool valid = (i < nx) && (j < ny);
-
-    const SmemPlan pl = plan_smem(nz, TY, S, KB, (int)sizeof(C2), (int)sizeof(T), PHYS ? 3 : 2);
-    T *tab = reinterpret_cast<T *>(smem + pl.tab_off);
-    C2 *ring = reinterpret_cast<C2 *>(smem + pl.ring_off);
-    T *st_dp = reinterpret_cast<T *>(smem + pl.state_off);
-    T *st_qs = st_dp + nz * NT;
-    T *st_cp = st_qs + nz * NT;
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + pl.bar_off);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(full + S);
-
-    const int n_stages = (nz + KB - 1) / KB;
-    const int SC = pl.stage_bytes / (int)sizeof(C2);  // cells per stage slot
-    constexpr int wpc = (int)(sizeof(C2) / 4);  // 32-bit words per cell
-    const int x0 = (kGhostX - 2 + (int)blockIdx.x * kTileX) * wpc;
-    const int y0 = (int)blockIdx.y * TY;
-    const uint32_t stage_tx = (uint32_t)(KB * PC * sizeof(C2));
-
-    if (tid == 0) {
-        prefetch_tmap(&tin);
-        for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
-        *abort_flag = 0;
-        fence_mbar_init();
-        const int first = n_stages < S ? n_stages : S;
-        for (int s = 0; s < first; ++s) {
-            mbar_arrive_expect_tx(&full[s], stage_tx);
-            tma_load_3d(ring + s * SC, &tin, &full[s], x0, y0, s * KB);
-        }
-    }
-    for (int e = tid; e < nz * kTab; e += NT) tab[e] = a.tab[e];
-
-    // per-column coefficients of the horizontal operator
-    const int ic = valid ? i : 0, jc = valid ? j : 0;
-    T ue = 0, uw = 0, vn = 0, vs = 0;
-    if (a.advection) {
-        ue = a.U[(size_t)jc * nx + ic];
-        uw = a.U[(size_t)jc * nx + (ic == 0 ? nx - 1 : ic - 1)];
-        vn = a.V[(size_t)jc * nx + ic];
-        vs = a.V[(size_t)(jc == 0 ? ny - 1 : jc - 1) * nx + ic];
-    }
-    const T zero = T(0);
-    const T cE = a.dh - a.dth * fmin(ue, zero);
-    const T cW = a.dh + a.dth * fmax(uw, zero);
-    const T cN = a.dh - a.dth * fmin(vn, zero);
-    const T cS = a.dh + a.dth * fmax(vs, zero);
-    const T cC = T(1) - T(4) * a.dh -
-                 a.dth * (fmax(ue, zero) - fmin(uw, zero) + fmax(vn, zero) - fmin(vs, zero));
-    const T km = a.kmult ? a.kmult[(size_t)jc * nx + ic] : T(1);
-
-    __syncthreads();  // barriers initialised, table staged
-
-    bool ok = mbar_wait_bounded(&full[0], 0);
-    const int ctr = (ty + 1) * kBoxX + tx + 2;
-    C2 cur = ring[ctr];
-    C2 prev = cur;
-    T cp_prev = 0, dp_prev = 0;
-
-    // plane k lives in stage k/KB, slot (k/KB) % S, sub-plane k % KB
-    int sub = 0, slot = 0, gst = 0;       // plane k
-    int sub1 = 1 % KB, slot1 = (KB == 1) ? 1 % S : 0;
-    uint32_t par1 = (KB == 1 && S == 1) ? 1u : 0u;
-    for (int k = 0; k < nz; ++k) {
-        const C2 *pk = ring + slot * SC + sub * PC;
-        C2 nxt = cur;
-        if (k + 1 < nz) {
-            if (sub1 == 0) ok &= mbar_wait_bounded(&full[slot1], par1);
-            nxt = ring[slot1 * SC + sub1 * PC + ctr];
-        }
-        const C2 e = pk[ctr + 1], w = pk[ctr - 1], n = pk[ctr + kBoxX], s = pk[ctr - kBoxX];
-        const T wU = tab[k * kTab + TAB_WU], wD = tab[k * kTab + TAB_WD];
-
-        const T ts = cC * cur.x + cE * e.x + cW * w.x + cN * n.x + cS * s.x + wU * (nxt.x - cur.x) -
-                     wD * (cur.x - prev.x);
-        const T qs = cC * cur.y + cE * e.y + cW * w.y + cN * n.y + cS * s.y + wU * (nxt.y - cur.y) -
-                     wD * (cur.y - prev.y);
-        if (PHYS) {
-            const T ak = km * tab[k * kTab + TAB_AHAT];
-            const T ck = km * tab[k * kTab + TAB_CHAT];
-            const T bk = T(1) - ak - ck;
-            const T m = bk - ak * cp_prev;
-            const T inv = recip(m);
-            const T cp = ck * inv;
-            const T dp = (ts - ak * dp_prev) * inv;
-            st_cp[k * NT + tid] = cp;
-            st_dp[k * NT + tid] = dp;
-            cp_prev = cp;
-            dp_prev = dp;
-        } else {
-            st_dp[k * NT + tid] = ts;
-        }
-        st_qs[k * NT + tid] = qs;
-        prev = cur;
-        cur = nxt;
-
-        // advance plane k+1 cursor
-        if (++sub1 == KB) {
-            sub1 = 0;
-            if (++slot1 == S) { slot1 = 0; par1 ^= 1u; }
-        }
-        // plane k's stage done: refill its slot with stage gst + S
-        if (++sub == KB) {
-            sub = 0;
-            if (!ok) *abort_flag = 1;
-            __syncthreads();
-            if (*abort_flag) {
-                if (tid == 0) {
-                    atomicOr(a.status, ST_TIMEOUT);
-                    // bounded wait for the last fill of every slot, so no copy
-                    // is still landing in shared memory when the CTA exits
-                    const int issued = (gst + S < n_stages) ? gst + S : n_stages;
-                    for (int s2 = 0; s2 < S && s2 < issued; ++s2) {
-                        const int fills = (issued - 1 - s2) / S;
-                        (void)mbar_wait_bounded(&full[s2], (uint32_t)(fills & 1));
-                    }
-                }
-                return;
-            }
-            if (tid == 0 && (gst + S) < n_stages) {
-                mbar_arrive_expect_tx(&full[slot], stage_tx);
-                tma_load_3d(ring + slot * SC, &tin, &full[slot], x0, y0, (gst + S) * KB);
-            }
-            ++gst;
-            if (++slot == S) slot = 0;
-        }
-    }
-    if (!ok && tid == 0) atomicOr(a.status, ST_TIMEOUT);
-
-    // pass 2: back substitution, radiation scan from the top, store
-    const size_t plane = (size_t)a.R * a.P;
-    const int ip = i + kGhostX, jp = j + 1;
-    C2 *out = a.out;
-    T x = 0, tau = 0, Etop = 1;
-    T chk = 0;
-    ColSum<T> sumT, sumQ;
-    for (int k = nz - 1; k >= 0; --k) {
-        const T dp = st_dp[k * NT + tid];
-        const T qs = st_qs[k * NT + tid];
-        T tn;
-        if (PHYS) {
-            x = dp - st_cp[k * NT + tid] * x;
-            const T taub = tau + tab[k * kTab + TAB_WTAU] * qs;
-            const T Eb = exp_neg(taub);
-            tn = x + tab[k * kTab + TAB_WH] * (Etop - Eb);
-            Etop = Eb;
-            tau = taub;
-        } else {
-            tn = dp;
-        }
-        if (valid) {
-            C2 v;
-            v.x = tn;
-            v.y = qs;
-            C2 *row = out + (size_t)k * plane + (size_t)jp * a.P;
-            row[ip] = v;
-            if (i == 0) row[kGhostX + nx] = v;
-            if (i == nx - 1) row[kGhostX - 1] = v;
-            if (j == 0) out[(size_t)k * plane + (size_t)(ny + 1) * a.P + ip] = v;
-            if (j == ny - 1) out[(size_t)k * plane + ip] = v;
-            if (SUMS) {
-                const T dzk = tab[k * kTab + TAB_DZ];
-                sumT.add(tn, dzk);
-                sumQ.add(qs, dzk);
-            } else {
-                chk += tn + qs;
-            }
-        }
-    }
-
-    double mT = 0.0, mQ = 0.0;
-    if (valid) {
-        if (SUMS) {
-            mT = sumT.total();
-            mQ = sumQ.total();
-            if (!isfinite(mT) || !isfinite(mQ)) atomicOr(a.status, ST_NONFINITE);
-        } else if (!finite(chk)) {
-            atomicOr(a.status, ST_NONFINITE);
-        }
-    }
-    if (SUMS) {
-        // deterministic CTA reduction: warp tree, then warps in order
-        mT = warp_sum(mT);
-        mQ = warp_sum(mQ);
-        __syncthreads();  // ring no longer read by anyone
-        double *red = reinterpret_cast<double *>(ring);
-        if (tx == 0) {
-            red[2 * ty] = mQ;
-            red[2 * ty + 1] = mT;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            double q = 0.0, t = 0.0;
-            for (int w = 0; w < TY; ++w) {
-                q += red[2 * w];
-                t += red[2 * w + 1];
-            }
-            const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-            a.partials[2 * b] = q;
-            a.partials[2 * b + 1] = t;
-        }
-    }
+__device__ __forceinline__ void consumer_sync(int nthreads) {
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
-// Fixed-order FP64 reduction of the per-CTA partials into one ring entry.
+// ------------------------------------------------------------ step kernel
+// Persistent CTAs walk tiles of 64 x TY columns (t = blockIdx.x, +gridDim.x,
+// ...).  Block = TY consumer warps (lane tx owns columns 2tx, 2tx+1 of a tile
+// row) + one producer warp.  The producer streams each tile's k-slabs from
+// the top down (stage = KB planes x {T, q} x (TY+2) rows x 72 columns, tile
+// plus a one-cell halo) through a ring of S shared-memory slots with TMA
+// (full barrier: bytes landed; empty barrier: every consumer warp is done),
+// and pulls slabs PF stages ahead into L2, so the next tile's loads overlap
+// the current tile's stores.  KMODE 0: kappa_mult = 1 everywhere (the
+// elimination coefficients come from the table); KMODE 1: per-column
+// kappa_mult, eliminated on the fly.
+template <typename T, int TY, int KMODE, bool PHYS, bool SUMS>
+__global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_constant__ CUtensorMap tin,
+                                                             const StepArgs<T> a, const int S, const int PF) {
+    using PK = Pk<T>;
+    using V = typename PK::V;
+    using R4 = Q4<T>;
+    constexpr int KB = 2;                 // planes per stage
+    constexpr int NT = 32 * TY;           // consumer threads
+    constexpr int PL = (TY + 2) * kBoxX;  // elements per staged (plane, field)
+    extern __shared__ __align__(128) unsigned char smem[];
+
+    const int tx = threadIdx.x, wy = threadIdx.y;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int gx = (nx + kTileX - 1) / kTileX, gy = (ny + TY - 1) / TY;
+    const int ntiles = gx * gy;
+    const int n_st = (nz + KB - 1) / KB;  // stages per tile
+    const SmemPlan pl = plan_smem(nz, TY, S, KB, (int)sizeof(T), KMODE == 1);
+    R4 *tab = reinterpret_cast<R4 *>(smem + pl.tab_off);
+    T *ring = reinterpret_cast<T *>(smem + pl.ring_off);
+    V *stF = reinterpret_cast<V *>(smem + pl.state_off);  // [nz][NT] F of the 2 columns
+    V *stE = stF + nz * NT;                                // [nz][NT] e   (KMODE 1)
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + pl.bar_off);
+    uint64_t *empty = full + S;
+    const int SC = pl.stage_bytes / (int)sizeof(T);
+
+    const int tid_all = tx + 32 * wy;
+    if (tid_all == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], TY);
+        }
+        fence_mbar_init();
+    }
+    for (int e = tid_all; e < kTabRec * nz; e += 32 * (TY + 1)) tab[e] = a.tab[e];
+    __syncthreads();
+
+    // ---------------- producer warp: stage g of tile n covers planes
+    // z0 = nz - (s+1)*KB .. z0+KB-1 (s = g mod n_st), top of the column first
+    if (wy == TY) {
+        if (tx == 0 && (int)blockIdx.x < ntiles) {
+            prefetch_tmap(&tin);
+            const int my_tiles = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+            const long total = (long)my_tiles * n_st;
+            const uint32_t tx_bytes = (uint32_t)(KB * 2 * PL * sizeof(T));
+            auto coords = [&](long g) -> int3 {
+                const int n = (int)(g / n_st), s = (int)(g - (long)n * n_st);
+                const int t = (int)blockIdx.x + n * (int)gridDim.x;
+                const int bx = t % gx, by = t / gx;
+                // x start is a multiple of 4 elements: 16-byte aligned in FP32 and FP64
+                return make_int3(kGhostX - kBoxX0 + bx * kTileX, by * TY, nz - (s + 1) * KB);
+            };
+            for (long g = 0; g < PF && g < total; ++g) {
+                const int3 c3 = coords(g);
+                tma_prefetch_l2_4d(&tin, c3.x, c3.y, 0, c3.z);
+            }
+            int slot = 0, fill = 0;
+            long issued = 0;
+            bool ok = true;
+            for (long g = 0; g < total; ++g) {
+                if (g + PF < total) {
+                    const int3 c3 = coords(g + PF);
+                    tma_prefetch_l2_4d(&tin, c3.x, c3.y, 0, c3.z);
+                }
+                if (g >= S && !mbar_wait_bounded(&empty[slot], (uint32_t)((fill - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                const int3 c3 = coords(g);
+                mbar_arrive_expect_tx(&full[slot], tx_bytes);
+                tma_load_4d(ring + slot * SC, &tin, &full[slot], c3.x, c3.y, 0, c3.z);
+                ++issued;
+                if (++slot == S) {
+                    slot = 0;
+                    ++fill;
+                }
+            }
+            if (!ok) atomicOr(a.status, ST_TIMEOUT);
+            // keep this thread until its last copy into every slot has landed
+            for (int s = 0; s < S && s < issued; ++s)
+                (void)mbar_wait_bounded(&full[s], (uint32_t)(((issued - 1 - s) / S) & 1));
+        }
+        return;
+    }
+
+    // ---------------- consumers: two adjacent columns per lane
+    const int tid = tx + 32 * wy;
+    const R4 *tA = tab + REC_A * nz, *tB = tab + REC_B * nz, *tC = tab + REC_C * nz, *tD = tab + REC_D * nz,
+             *tE = tab + REC_E * nz;
+    const int ctr = (wy + 1) * kBoxX + kBoxX0 + 2 * tx;  // column pair in a staged plane (8-byte aligned)
+    const size_t lev = (size_t)2 * a.R * a.P;              // elements between levels
+    const size_t fld = (size_t)a.R * a.P;                  // T plane -> q plane
+    const T zero = T(0);
+    int slot = 0;
+    uint32_t par = 0;
+    bool ok = true;
+
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int bx = t % gx, by = t / gx;
+        const int i0 = bx * kTileX + 2 * tx, j = by * TY + wy;
+        const bool va = (i0 < nx) && (j < ny), vb = (i0 + 1 < nx) && (j < ny);
+        const bool edge = bx == 0 || bx == gx - 1 || by == 0 || by == gy - 1;
+
+        // per-column coefficients of the horizontal operator, paired (a, b)
+        V cC, cE, cW, cN, cS, km;
+        {
+            T c5[2][5], k1[2];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const bool v = c ? vb : va;
+                const int ic = v ? i0 + c : 0, jc = v ? j : 0;
+                T ue = 0, uw = 0, vn = 0, vs = 0;
+                if (a.advection) {
+                    ue = a.U[(size_t)jc * nx + ic];
+                    uw = a.U[(size_t)jc * nx + (ic == 0 ? nx - 1 : ic - 1)];
+                    vn = a.V[(size_t)jc * nx + ic];
+                    vs = a.V[(size_t)(jc == 0 ? ny - 1 : jc - 1) * nx + ic];
+                }
+                c5[c][1] = a.dh - a.dth * fmin(ue, zero);
+                c5[c][2] = a.dh + a.dth * fmax(uw, zero);
+                c5[c][3] = a.dh - a.dth * fmin(vn, zero);
+                c5[c][4] = a.dh + a.dth * fmax(vs, zero);
+                c5[c][0] = T(1) - T(4) * a.dh -
+                           a.dth * (fmax(ue, zero) - fmin(uw, zero) + fmax(vn, zero) - fmin(vs, zero));
+                k1[c] = (KMODE == 1 && a.kmult) ? a.kmult[(size_t)jc * nx + ic] : T(1);
+            }
+            cC = V{c5[0][0], c5[1][0]};
+            cE = V{c5[0][1], c5[1][1]};
+            cW = V{c5[0][2], c5[1][2]};
+            cN = V{c5[0][3], c5[1][3]};
+            cS = V{c5[0][4], c5[1][4]};
+            km = V{k1[0], k1[1]};
+        }
+
+        // ------------- pass 1 (top down)
+        if (ok) ok = mbar_wait_bounded(&full[slot], par);
+        // plane (sub-plane s, field f) of the slot: ring + slot*SC + (s*2 + f)*PL
+        const T *p0 = ring + slot * SC + ((KB - 1) * 2) * PL;  // top plane of the tile
+        V curT = *reinterpret_cast<const V *>(p0 + ctr);
+        V curQ = *reinterpret_cast<const V *>(p0 + PL + ctr);
+        V prvT = curT, prvQ = curQ;
+        V tau = PK::dup(T(0)), Et = PK::dup(T(1));
+        V f_up = PK::dup(T(0)), h_up = PK::dup(T(0)), e_up = PK::dup(T(0));  // level k+1
+        V chk = PK::dup(T(0));
+        ColSum2<T> sumQ, sumT;
+        T *qcol = a.out + fld + (size_t)(j + 1) * a.P + (i0 + kGhostX);  // q plane, level 0
+
+        // one level: plane pk (T) / pk + PL (q), centre of level k-1 in nT/nQ
+        auto level = [&](int k, const T *pk, V nT, V nQ) {
+            const R4 A = tA[k], B = tB[k], C = tC[k];
+            const V b2 = V{B.x, B.y}, wu = V{A.x, A.y}, wd = V{A.z, A.w};
+            const V cCk = PK::add(cC, b2);
+            // T*
+            V r = PK::mul(cCk, curT);
+            r = PK::fma(cE, V{curT.y, pk[ctr + 2]}, r);
+            r = PK::fma(cW, V{pk[ctr - 1], curT.x}, r);
+            r = PK::fma(cN, *reinterpret_cast<const V *>(pk + ctr + kBoxX), r);
+            r = PK::fma(cS, *reinterpret_cast<const V *>(pk + ctr - kBoxX), r);
+            r = PK::fma(wu, prvT, r);
+            const V Ts = PK::fma(wd, nT, r);
+            // q*
+            const T *pq = pk + PL;
+            V rq = PK::mul(cCk, curQ);
+            rq = PK::fma(cE, V{curQ.y, pq[ctr + 2]}, rq);
+            rq = PK::fma(cW, V{pq[ctr - 1], curQ.x}, rq);
+            rq = PK::fma(cN, *reinterpret_cast<const V *>(pq + ctr + kBoxX), rq);
+            rq = PK::fma(cS, *reinterpret_cast<const V *>(pq + ctr - kBoxX), rq);
+            rq = PK::fma(wu, prvQ, rq);
+            const V Qs = PK::fma(wd, nQ, rq);
+            prvT = curT;
+            prvQ = curQ;
+            curT = nT;
+            curQ = nQ;
+
+            // q^{n+1} = q*
+            if (!edge) {
+                *reinterpret_cast<V *>(qcol + k * lev) = Qs;
+            } else {
+                T *row = a.out + k * lev + fld + (size_t)(j + 1) * a.P;
+                if (va) row[i0 + kGhostX] = Qs.x;
+                if (vb) row[i0 + 1 + kGhostX] = Qs.y;
+                if (va && i0 == 0) row[kGhostX + nx] = Qs.x;
+                if (vb && i0 + 1 == nx - 1) row[kGhostX - 1] = Qs.y;
+                if (va && i0 == nx - 1) row[kGhostX - 1] = Qs.x;
+                if (j == 0) {  // bottom row -> top ghost row
+                    T *g = a.out + k * lev + fld + (size_t)(ny + 1) * a.P;
+                    if (va) g[i0 + kGhostX] = Qs.x;
+                    if (vb) g[i0 + 1 + kGhostX] = Qs.y;
+                }
+                if (j == ny - 1) {  // top row -> bottom ghost row
+                    T *g = a.out + k * lev + fld;
+                    if (va) g[i0 + kGhostX] = Qs.x;
+                    if (vb) g[i0 + 1 + kGhostX] = Qs.y;
+                }
+            }
+            if (SUMS)
+                sumQ.add(V{va ? Qs.x : T(0), vb ? Qs.y : T(0)}, tE[k].z);
+            else
+                chk = PK::add(chk, Qs);
+
+            if (PHYS) {
+                // radiation from the top: h = dt H_k
+                const V tb = PK::fma(V{B.z, B.w}, Qs, tau);
+                const V Eb = V{exp2_neg(tb.x), exp2_neg(tb.y)};
+                const V hk = PK::mul(V{C.x, C.y}, PK::add(Et, PK::mul(Eb, PK::dup(T(-1)))));
+                Et = Eb;
+                tau = tb;
+                // elimination from the top
+                V fk, ek;
+                if (KMODE == 0) {
+                    const R4 D = tD[k];
+                    fk = PK::mul(PK::fma(V{C.z, C.w}, f_up, Ts), V{D.x, D.y});
+                    ek = V{D.z, D.w};
+                } else {
+                    const R4 E = tE[k];
+                    const V ak = PK::mul(km, PK::dup(E.x));
+                    const V nck = PK::mul(km, PK::dup(-E.y));  // -c_k
+                    // m = (1 - a - c) - c e_{k+1}
+                    const V m = PK::fma(nck, e_up, PK::add(PK::add(PK::dup(T(1)), PK::mul(ak, PK::dup(T(-1)))), nck));
+                    const V inv = V{recip(m.x), recip(m.y)};
+                    fk = PK::mul(PK::fma(nck, f_up, Ts), inv);
+                    ek = PK::mul(ak, inv);
+                    stE[k * NT + tid] = ek;
+                }
+                // F_{k+1} = f_{k+1} + h_{k+1} + e_{k+1} h_k  (complete now)
+                if (k + 1 < nz) stF[(k + 1) * NT + tid] = PK::fma(e_up, hk, PK::add(f_up, h_up));
+                f_up = fk;
+                h_up = hk;
+                e_up = ek;
+            } else {
+                stF[k * NT + tid] = Ts;
+            }
+        };
+
+        for (int g = 0; g < n_st; ++g) {
+            const int z0 = nz - (g + 1) * KB;  // lowest plane of this stage (may be < 0)
+            const T *pa = ring + slot * SC;    // sub-plane 0 = level z0, sub-plane 1 = z0+1
+            const int nslot = (slot + 1 == S) ? 0 : slot + 1;
+            const uint32_t npar = (nslot == 0) ? (par ^ 1u) : par;
+            // levels z0+1 (upper) then z0 (lower); the one below z0 is the top
+            // sub-plane of the next stage
+            const int ku = z0 + 1, kl = z0;
+            const T *pu = pa + 2 * PL, *plw = pa;
+            if (ku >= 0) {
+                V nT = curT, nQ = curQ;
+                if (kl >= 0) {
+                    nT = *reinterpret_cast<const V *>(plw + ctr);
+                    nQ = *reinterpret_cast<const V *>(plw + PL + ctr);
+                }
+                level(ku, pu, nT, nQ);
+            }
+            if (kl >= 0) {
+                V nT = curT, nQ = curQ;
+                if (kl >= 1) {
+                    if (ok) ok = mbar_wait_bounded(&full[nslot], npar);
+                    const T *pn = ring + nslot * SC + 2 * PL;  // next stage, upper sub-plane
+                    nT = *reinterpret_cast<const V *>(pn + ctr);
+                    nQ = *reinterpret_cast<const V *>(pn + PL + ctr);
+                }
+                level(kl, plw, nT, nQ);
+            }
+            __syncwarp();
+            if (tx == 0) mbar_arrive(&empty[slot]);
+            slot = nslot;
+            par = npar;
+        }
+        if (PHYS) stF[tid] = PK::add(f_up, h_up);  // F_0 = f_0 + h_0
+
+        // ------------- pass 2 (bottom up): T^{n+1}_k = F_k - e_k T^{n+1}_{k-1}
+        T *tcol = a.out + (size_t)(j + 1) * a.P + (i0 + kGhostX);  // T plane, level 0
+        V Tprev = PK::dup(T(0));
+        if (!edge) {
+#pragma unroll 4
+            for (int k = 0; k < nz; ++k) {
+                V tn = stF[k * NT + tid];
+                if (PHYS) {
+                    const V ek = (KMODE == 0) ? V{tD[k].z, tD[k].w} : stE[k * NT + tid];
+                    tn = PK::fma(PK::mul(ek, PK::dup(T(-1))), Tprev, tn);
+                    Tprev = tn;
+                }
+                *reinterpret_cast<V *>(tcol + k * lev) = tn;
+                if (SUMS)
+                    sumT.add(tn, tE[k].z);
+                else
+                    chk = PK::add(chk, tn);
+            }
+        } else {
+            for (int k = 0; k < nz; ++k) {
+                V tn = stF[k * NT + tid];
+                if (PHYS) {
+                    const V ek = (KMODE == 0) ? V{tD[k].z, tD[k].w} : stE[k * NT + tid];
+                    tn = PK::fma(PK::mul(ek, PK::dup(T(-1))), Tprev, tn);
+                    Tprev = tn;
+                }
+                T *row = a.out + k * lev + (size_t)(j + 1) * a.P;
+                if (va) row[i0 + kGhostX] = tn.x;
+                if (vb) row[i0 + 1 + kGhostX] = tn.y;
+                if (va && i0 == 0) row[kGhostX + nx] = tn.x;
+                if (vb && i0 + 1 == nx - 1) row[kGhostX - 1] = tn.y;
+                if (va && i0 == nx - 1) row[kGhostX - 1] = tn.x;
+                if (j == 0) {
+                    T *g = a.out + k * lev + (size_t)(ny + 1) * a.P;
+                    if (va) g[i0 + kGhostX] = tn.x;
+                    if (vb) g[i0 + 1 + kGhostX] = tn.y;
+                }
+                if (j == ny - 1) {
+                    T *g = a.out + k * lev;
+                    if (va) g[i0 + kGhostX] = tn.x;
+                    if (vb) g[i0 + 1 + kGhostX] = tn.y;
+                }
+                if (SUMS)
+                    sumT.add(V{va ? tn.x : T(0), vb ? tn.y : T(0)}, tE[k].z);
+                else
+                    chk = PK::add(chk, V{va ? tn.x : T(0), vb ? tn.y : T(0)});
+            }
+        }
+
+        if (SUMS) {
+            double mT = sumT.total(va, vb), mQ = sumQ.total(va, vb);
+            if ((va || vb) && (!isfinite(mT) || !isfinite(mQ))) atomicOr(a.status, ST_NONFINITE);
+            // deterministic per-tile reduction: warp tree, then warps in order
+            __shared__ double red[2 * 8];
+            mT = warp_sum(mT);
+            mQ = warp_sum(mQ);
+            if (tx == 0) {
+                red[2 * wy] = mQ;
+                red[2 * wy + 1] = mT;
+            }
+            consumer_sync(NT);
+            if (tid == 0) {
+                double q = 0.0, tt = 0.0;
+                for (int w = 0; w < TY; ++w) {
+                    q += red[2 * w];
+                    tt += red[2 * w + 1];
+                }
+                a.partials[2 * (size_t)t] = q;
+                a.partials[2 * (size_t)t + 1] = tt;
+            }
+            consumer_sync(NT);
+        } else {
+            // lanes outside the grid in edge tiles computed from padding: skipped
+            const bool bad = edge ? ((va && !isfinite(chk.x)) || (vb && !isfinite(chk.y)))
+                                  : (!isfinite(chk.x) || !isfinite(chk.y));
+            if (bad) atomicOr(a.status, ST_NONFINITE);
+        }
+    }
+    if (!ok && tx == 0) atomicOr(a.status, ST_TIMEOUT);
+}
+
+// Fixed-order FP64 reduction of the per-tile partials into one ring entry.
 __global__ void __launch_bounds__(1024) sums_finalize(const double *__restrict__ part, long nblk, double h2,
                                                       double *__restrict__ dst) {
     __shared__ double sq[1024], st[1024];
@@ -308,70 +488,72 @@ __global__ void __launch_bounds__(1024) sums_finalize(const double *__restrict__
     }
 }
 
-// Per-level tables from FP64 dz, kappa_lev, alpha (one thread per level).
+// Per-level table from FP64 dz, kappa_lev, alpha.  One thread: the
+// kappa_mult = 1 column's elimination from the top is a recurrence in k.
 template <typename T>
 __global__ void tables_kernel(const double *lev, int nz, double dt, double kappa_h, double S0, double q_ref,
-                              T *tab) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nz) return;
+                              Q4<T> *tab) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
     const double *dz = lev, *kl = lev + nz, *al = lev + 2 * nz;
-    double wU = 0, wD = 0, ah = 0, ch = 0;
-    if (k < nz - 1) {
-        const double g = 0.5 * (dz[k] + dz[k + 1]);
-        wU = dt * kappa_h / (dz[k] * g);
-        ch = -dt * (0.5 * (kl[k] + kl[k + 1])) / (dz[k] * g);
+    const double log2e = 1.4426950408889634074;
+    double e_up = 0.0;
+    for (int k = nz - 1; k >= 0; --k) {
+        double wU = 0, wD = 0, ah = 0, ch = 0;
+        if (k < nz - 1) {
+            const double g = 0.5 * (dz[k] + dz[k + 1]);
+            wU = dt * kappa_h / (dz[k] * g);
+            ch = -dt * (0.5 * (kl[k] + kl[k + 1])) / (dz[k] * g);
+        }
+        if (k > 0) {
+            const double g = 0.5 * (dz[k - 1] + dz[k]);
+            wD = dt * kappa_h / (dz[k] * g);
+            ah = -dt * (0.5 * (kl[k - 1] + kl[k])) / (dz[k] * g);
+        }
+        const double m = (1.0 - ah - ch) - ch * e_up;  // kappa_mult = 1 pivot, from the top
+        const double e = ah / m;
+        e_up = e;
+        tab[REC_A * nz + k] = Q4<T>{(T)wU, (T)wU, (T)wD, (T)wD};
+        const double wt2 = al[k] * dz[k] * log2e / q_ref;
+        tab[REC_B * nz + k] = Q4<T>{(T)(-(wU + wD)), (T)(-(wU + wD)), (T)wt2, (T)wt2};
+        const double wH = dt * S0 / dz[k];
+        tab[REC_C * nz + k] = Q4<T>{(T)wH, (T)wH, (T)(-ch), (T)(-ch)};
+        tab[REC_D * nz + k] = Q4<T>{(T)(1.0 / m), (T)(1.0 / m), (T)e, (T)e};
+        tab[REC_E * nz + k] = Q4<T>{(T)ah, (T)ch, (T)dz[k], (T)0};
     }
-    if (k > 0) {
-        const double g = 0.5 * (dz[k - 1] + dz[k]);
-        wD = dt * kappa_h / (dz[k] * g);
-        ah = -dt * (0.5 * (kl[k - 1] + kl[k])) / (dz[k] * g);
-    }
-    T *r = tab + k * kTab;
-    r[TAB_WU] = (T)wU;
-    r[TAB_WD] = (T)wD;
-    r[TAB_AHAT] = (T)ah;
-    r[TAB_CHAT] = (T)ch;
-    r[TAB_WTAU] = (T)(al[k] * dz[k] / q_ref);
-    r[TAB_WH] = (T)(dt * S0 / dz[k]);
-    r[TAB_DZ] = (T)dz[k];
-    r[TAB_PAD] = (T)0;
 }
 
-// FP64 [nz][ny][nx] (T, q) -> padded interleaved cells with the ghost ring.
+// FP64 [nz][ny][nx] (T, q) -> planar padded fields with the ghost ring.
 template <typename T>
-__global__ void pack_kernel(const double *__restrict__ Tsrc, const double *__restrict__ qsrc,
-                            typename Vec2<T>::type *__restrict__ dst, int nx, int ny, int nz, int P, int R) {
-    using C2 = typename Vec2<T>::type;
-    const size_t n = (size_t)P * R * nz;
+__global__ void pack_kernel(const double *__restrict__ Tsrc, const double *__restrict__ qsrc, T *__restrict__ dst,
+                            int nx, int ny, int nz, int P, int R) {
+    const size_t n = (size_t)P * R * 2 * nz;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
         const int ip = (int)(e % P);
         const int jp = (int)((e / P) % R);
-        const int k = (int)(e / ((size_t)P * R));
-        C2 v;
-        v.x = 0;
-        v.y = 0;
+        const int f = (int)((e / ((size_t)P * R)) % 2);
+        const int k = (int)(e / ((size_t)P * R * 2));
+        T v = 0;
         if (ip >= kGhostX - 1 && ip <= kGhostX + nx) {
             const int i = (ip - kGhostX + nx) % nx;
             const int j = (jp - 1 + ny) % ny;
             const size_t s = ((size_t)k * ny + j) * nx + i;
-            v.x = (T)Tsrc[s];
-            v.y = (T)qsrc[s];
+            v = (T)(f == 0 ? Tsrc[s] : qsrc[s]);
         }
         dst[e] = v;
     }
 }
 
 template <typename T>
-__global__ void unpack_kernel(const typename Vec2<T>::type *__restrict__ src, double *__restrict__ Tdst,
-                              double *__restrict__ qdst, int nx, int ny, int nz, int P, int R) {
+__global__ void unpack_kernel(const T *__restrict__ src, double *__restrict__ Tdst, double *__restrict__ qdst,
+                              int nx, int ny, int nz, int P, int R) {
     const size_t n = (size_t)nx * ny * nz;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(e % nx);
         const int j = (int)((e / nx) % ny);
         const int k = (int)(e / ((size_t)nx * ny));
-        const auto v = src[((size_t)k * R + j + 1) * P + i + kGhostX];
-        if (Tdst) Tdst[e] = (double)v.x;
-        if (qdst) qdst[e] = (double)v.y;
+        const size_t base = ((size_t)(2 * k) * R + j + 1) * P + i + kGhostX;
+        if (Tdst) Tdst[e] = (double)src[base];
+        if (qdst) qdst[e] = (double)src[base + (size_t)R * P];
     }
 }
 
@@ -380,17 +562,19 @@ template <typename T> __global__ void convert_kernel(const double *__restrict__ 
         d[e] = (T)s[e];
 }
 
-// Column physics only, one thread per column, columns [ncol][nz].
+// Column physics only, one thread per column, columns [ncol][nz]: the
+// forward Thomas sweep of the implicit vertical diffusion and the
+// optical-depth scan from the top (same definitions as the step).
 template <typename T>
 __global__ void __launch_bounds__(128) columns_kernel(const T *__restrict__ Ts, const T *__restrict__ qs,
-                                                      const T *__restrict__ km, const T *__restrict__ gtab,
+                                                      const T *__restrict__ km, const Q4<T> *__restrict__ gtab,
                                                       T *__restrict__ Tout, T *__restrict__ tend, long ncol,
                                                       int nz, T dt) {
     extern __shared__ __align__(16) unsigned char smem[];
-    T *tab = reinterpret_cast<T *>(smem);
-    T *cpa = tab + nz * kTab;
+    Q4<T> *tab = reinterpret_cast<Q4<T> *>(smem);
+    T *cpa = reinterpret_cast<T *>(tab + kTabRec * nz);
     T *dpa = cpa + nz * blockDim.x;
-    for (int e = threadIdx.x; e < nz * kTab; e += blockDim.x) tab[e] = gtab[e];
+    for (int e = threadIdx.x; e < kTabRec * nz; e += blockDim.x) tab[e] = gtab[e];
     __syncthreads();
     const long col = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= ncol) return;
@@ -398,11 +582,11 @@ __global__ void __launch_bounds__(128) columns_kernel(const T *__restrict__ Ts, 
     const T *tc = Ts + col * nz;
     const T *qc = qs + col * nz;
     const T s = km ? km[col] : T(1);
+    const Q4<T> *tB = tab + REC_B * nz, *tC = tab + REC_C * nz, *tE = tab + REC_E * nz;
     T cpp = 0, dpp = 0;
     for (int k = 0; k < nz; ++k) {
-        const T ak = s * tab[k * kTab + TAB_AHAT];
-        const T ck = s * tab[k * kTab + TAB_CHAT];
-        const T m = (T(1) - ak - ck) - ak * cpp;
+        const T ak = s * tE[k].x, ck = s * tE[k].y;
+        const T m = ((T(1) - ak) - ck) - ak * cpp;
         const T inv = recip(m);
         cpp = ck * inv;
         dpp = (tc[k] - ak * dpp) * inv;
@@ -412,9 +596,9 @@ __global__ void __launch_bounds__(128) columns_kernel(const T *__restrict__ Ts, 
     T x = 0, tau = 0, Etop = 1;
     for (int k = nz - 1; k >= 0; --k) {
         x = dpa[k * nt + t] - cpa[k * nt + t] * x;
-        const T taub = tau + tab[k * kTab + TAB_WTAU] * qc[k];
-        const T Eb = exp_neg(taub);
-        const T heat = tab[k * kTab + TAB_WH] * (Etop - Eb);  // dt * H_k
+        const T taub = tau + tB[k].z * qc[k];
+        const T Eb = exp2_neg(taub);
+        const T heat = tC[k].x * (Etop - Eb);  // dt * H_k
         Tout[col * nz + k] = x + heat;
         if (tend) {
             tend[col * 2 * nz + k] = heat / dt;
@@ -432,9 +616,9 @@ static int cuda_fail(wx_ctx *c, cudaError_t e, const char *what) {
     return WX_ECUDA;
 }
 
-#define WX_CK(call, what)                                   \
-    do {                                                    \
-        cudaError_t e_ = (call);                            \
+#define WX_CK(call, what)                                     \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
         if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
     } while (0)
 
@@ -445,21 +629,21 @@ static int grid_for(size_t n) {
 
 int launch_tables(wx_ctx *c, cudaStream_t s) {
     if (c->t_bytes == 4)
-        tables_kernel<float><<<(c->nz + 127) / 128, 128, 0, s>>>(c->d_lev, c->nz, c->dt, c->kappa_h, c->S0,
-                                                                 c->q_ref, (float *)c->tab);
+        tables_kernel<float><<<1, 32, 0, s>>>(c->d_lev, c->nz, c->dt, c->kappa_h, c->S0, c->q_ref,
+                                              (Q4<float> *)c->tab);
     else
-        tables_kernel<double><<<(c->nz + 127) / 128, 128, 0, s>>>(c->d_lev, c->nz, c->dt, c->kappa_h, c->S0,
-                                                                  c->q_ref, (double *)c->tab);
+        tables_kernel<double><<<1, 32, 0, s>>>(c->d_lev, c->nz, c->dt, c->kappa_h, c->S0, c->q_ref,
+                                               (Q4<double> *)c->tab);
     WX_CK(cudaGetLastError(), "tables kernel");
     return WX_OK;
 }
 
 int launch_pack(wx_ctx *c, const double *T, const double *q, void *dst, cudaStream_t s) {
-    const size_t n = c->field_cells;
+    const size_t n = 2 * c->field_cells;
     if (c->t_bytes == 4)
-        pack_kernel<float><<<grid_for(n), 256, 0, s>>>(T, q, (float2 *)dst, c->nx, c->ny, c->nz, c->P, c->R);
+        pack_kernel<float><<<grid_for(n), 256, 0, s>>>(T, q, (float *)dst, c->nx, c->ny, c->nz, c->P, c->R);
     else
-        pack_kernel<double><<<grid_for(n), 256, 0, s>>>(T, q, (double2 *)dst, c->nx, c->ny, c->nz, c->P, c->R);
+        pack_kernel<double><<<grid_for(n), 256, 0, s>>>(T, q, (double *)dst, c->nx, c->ny, c->nz, c->P, c->R);
     WX_CK(cudaGetLastError(), "pack kernel");
     return WX_OK;
 }
@@ -467,11 +651,11 @@ int launch_pack(wx_ctx *c, const double *T, const double *q, void *dst, cudaStre
 int launch_unpack(wx_ctx *c, const void *src, double *T, double *q, cudaStream_t s) {
     const size_t n = (size_t)c->nx * c->ny * c->nz;
     if (c->t_bytes == 4)
-        unpack_kernel<float><<<grid_for(n), 256, 0, s>>>((const float2 *)src, T, q, c->nx, c->ny, c->nz, c->P,
+        unpack_kernel<float><<<grid_for(n), 256, 0, s>>>((const float *)src, T, q, c->nx, c->ny, c->nz, c->P,
                                                          c->R);
     else
-        unpack_kernel<double><<<grid_for(n), 256, 0, s>>>((const double2 *)src, T, q, c->nx, c->ny, c->nz,
-                                                          c->P, c->R);
+        unpack_kernel<double><<<grid_for(n), 256, 0, s>>>((const double *)src, T, q, c->nx, c->ny, c->nz, c->P,
+                                                          c->R);
     WX_CK(cudaGetLastError(), "unpack kernel");
     return WX_OK;
 }
@@ -489,7 +673,7 @@ int launch_columns(wx_ctx *c, const void *Ts, const void *qs, const void *km, vo
                    cudaStream_t s) {
     if (ncol <= 0) return WX_OK;
     const int nt = 128;
-    const size_t smem = (size_t)c->nz * kTab * c->t_bytes + 2 * (size_t)c->nz * nt * c->t_bytes;
+    const size_t smem = (size_t)c->nz * kTabRec * 4 * c->t_bytes + 2 * (size_t)c->nz * nt * c->t_bytes;
     if (smem > 227 * 1024) {
         c->err = "wx_physics_columns: nz too large for the column kernel";
         return WX_EUNSUPPORTED;
@@ -499,13 +683,13 @@ int launch_columns(wx_ctx *c, const void *Ts, const void *qs, const void *km, vo
         auto k = columns_kernel<float>;
         WX_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "smem attr");
         k<<<(unsigned)blocks, nt, smem, s>>>((const float *)Ts, (const float *)qs, (const float *)km,
-                                             (const float *)c->tab, (float *)Tout, (float *)tend, ncol, c->nz,
+                                             (const Q4<float> *)c->tab, (float *)Tout, (float *)tend, ncol, c->nz,
                                              (float)c->dt);
     } else {
         auto k = columns_kernel<double>;
         WX_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "smem attr");
         k<<<(unsigned)blocks, nt, smem, s>>>((const double *)Ts, (const double *)qs, (const double *)km,
-                                             (const double *)c->tab, (double *)Tout, (double *)tend, ncol,
+                                             (const Q4<double> *)c->tab, (double *)Tout, (double *)tend, ncol,
                                              c->nz, c->dt);
     }
     WX_CK(cudaGetLastError(), "columns kernel");
@@ -514,46 +698,58 @@ int launch_columns(wx_ctx *c, const void *Ts, const void *qs, const void *km, vo
 
 constexpr int kKB = 2;  // planes per TMA stage
 
+static bool per_col(const wx_ctx *c) { return c->kmult != nullptr; }
+
 bool cfg_fits(const wx_ctx *c, const StepCfg &cfg, int *smem_bytes) {
-    const int narr = 3;
-    const SmemPlan p = plan_smem(c->nz, cfg.ty, cfg.stages, kKB, c->cell_bytes, c->t_bytes, narr);
+    const SmemPlan p = plan_smem(c->nz, cfg.ty, cfg.stages, kKB, c->t_bytes, per_col(c));
     if (smem_bytes) *smem_bytes = p.total;
-    return cfg.stages >= 2 && p.total <= 227 * 1024;
+    // the per-SM budget: ctas_per_sm CTAs plus 1 KB runtime reserve each
+    return cfg.stages >= 3 && cfg.ctas_per_sm >= 1 && p.total <= 227 * 1024 &&
+           cfg.ctas_per_sm * (p.total + 1024) <= 228 * 1024;
 }
 
 StepCfg default_cfg(const wx_ctx *c) {
-    // Prefer two CTAs per SM (<= 113 KB each) with 4 rows in FP32 / 2 in
-    // FP64, and as many TMA stages as fit (up to 8); fall back to fewer rows.
-    const int pref[3] = {c->t_bytes == 4 ? 4 : 2, c->t_bytes == 4 ? 2 : 1, 1};
-    for (int budget : {113 * 1024, 227 * 1024}) {
-        for (int ty : pref) {
-            for (int st = 8; st >= 3; --st) {
-                StepCfg g;
-                g.ty = ty;
-                g.stages = st;
-                g.kb = kKB;
-                int bytes = 0;
-                if (cfg_fits(c, g, &bytes) && bytes <= budget) return g;
+    // Most resident consumer warps per SM first (capped at 16), then taller
+    // tiles (less halo), then the deeper TMA ring (3..8 stages of 2 planes);
+    // the L2 prefetch runs 8 stages ahead.
+    StepCfg best;
+    best.ty = 1;
+    best.stages = 3;
+    best.ctas_per_sm = 1;
+    int best_warps = -1, best_st = 0;
+    for (int ty : {1, 2, 4, 8}) {
+        for (int st = 8; st >= 3; --st) {
+            StepCfg g;
+            g.ty = ty;
+            g.stages = st;
+            g.kb = kKB;
+            int bytes = 0;
+            g.ctas_per_sm = 1;
+            if (!cfg_fits(c, g, &bytes)) continue;
+            g.ctas_per_sm = std::min(228 * 1024 / (bytes + 1024), 2048 / (32 * (ty + 1)));
+            const int warps = std::min(g.ctas_per_sm * ty, 16);
+            if (warps > best_warps || (warps == best_warps && (ty > best.ty || (ty == best.ty && st > best_st)))) {
+                best = g;
+                best_warps = warps;
+                best_st = st;
             }
         }
     }
-    StepCfg g;
-    g.ty = 1;
-    g.stages = 2;
-    return g;
+    best.prefetch = 8;
+    return best;
 }
 
-template <typename T, int TY, bool PHYS, bool SUMS>
+template <typename T, int TY, int KMODE, bool PHYS, bool SUMS>
 static int launch_step_t(wx_ctx *c, cudaStream_t s, const CUtensorMap &tm, void *out) {
-    auto kern = step_kernel<T, TY, kKB, PHYS, SUMS>;
-    const SmemPlan pl = plan_smem(c->nz, TY, c->cfg.stages, kKB, c->cell_bytes, c->t_bytes, PHYS ? 3 : 2);
+    auto kern = step_kernel<T, TY, KMODE, PHYS, SUMS>;
+    const SmemPlan pl = plan_smem(c->nz, TY, c->cfg.stages, kKB, c->t_bytes, KMODE == 1);
     WX_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.total), "smem attr");
     StepArgs<T> a;
-    a.out = reinterpret_cast<typename Vec2<T>::type *>(out);
+    a.out = reinterpret_cast<T *>(out);
     a.U = (const T *)c->U;
     a.V = (const T *)c->V;
     a.kmult = (const T *)c->kmult;
-    a.tab = (const T *)c->tab;
+    a.tab = (const Q4<T> *)c->tab;
     a.status = c->d_status;
     a.partials = c->partials;
     a.nx = c->nx;
@@ -564,43 +760,50 @@ static int launch_step_t(wx_ctx *c, cudaStream_t s, const CUtensorMap &tm, void 
     a.dth = (T)(c->dt / c->h);
     a.dh = (T)(c->dt * c->kappa_h / (c->h * c->h));
     a.advection = (c->flags & WX_ADVECTION) ? 1 : 0;
-    dim3 grid((c->nx + kTileX - 1) / kTileX, (c->ny + TY - 1) / TY);
-    dim3 block(32, TY);
-    kern<<<grid, block, pl.total, s>>>(tm, a, c->cfg.stages);
+    const long ntiles = (long)((c->nx + kTileX - 1) / kTileX) * ((c->ny + TY - 1) / TY);
+    const long resident = (long)c->num_sms * c->cfg.ctas_per_sm;
+    dim3 grid((unsigned)std::max(1L, std::min(ntiles, resident)));
+    dim3 block(32, TY + 1);
+    kern<<<grid, block, pl.total, s>>>(tm, a, c->cfg.stages, c->cfg.prefetch);
     WX_CK(cudaGetLastError(), "step kernel");
     return WX_OK;
 }
 
-template <typename T, bool PHYS, bool SUMS>
+template <typename T, int KMODE, bool PHYS, bool SUMS>
 static int dispatch_ty(wx_ctx *c, cudaStream_t s, const CUtensorMap &tm, void *out) {
     switch (c->cfg.ty) {
-        case 1: return launch_step_t<T, 1, PHYS, SUMS>(c, s, tm, out);
-        case 2: return launch_step_t<T, 2, PHYS, SUMS>(c, s, tm, out);
-        case 4: return launch_step_t<T, 4, PHYS, SUMS>(c, s, tm, out);
-        case 8: return launch_step_t<T, 8, PHYS, SUMS>(c, s, tm, out);
+        case 1: return launch_step_t<T, 1, KMODE, PHYS, SUMS>(c, s, tm, out);
+        case 2: return launch_step_t<T, 2, KMODE, PHYS, SUMS>(c, s, tm, out);
+        case 4: return launch_step_t<T, 4, KMODE, PHYS, SUMS>(c, s, tm, out);
+        case 8: return launch_step_t<T, 8, KMODE, PHYS, SUMS>(c, s, tm, out);
         default: c->err = "unsupported tile rows"; return WX_EUNSUPPORTED;
     }
 }
 
-template <typename T>
+template <typename T, int KMODE>
 static int dispatch_flags(wx_ctx *c, cudaStream_t s, const CUtensorMap &tm, void *out) {
     const bool phys = c->flags & WX_PHYSICS, sums = c->flags & WX_SUMS;
-    if (phys && sums) return dispatch_ty<T, true, true>(c, s, tm, out);
-    if (phys) return dispatch_ty<T, true, false>(c, s, tm, out);
-    if (sums) return dispatch_ty<T, false, true>(c, s, tm, out);
-    return dispatch_ty<T, false, false>(c, s, tm, out);
+    if (phys && sums) return dispatch_ty<T, KMODE, true, true>(c, s, tm, out);
+    if (phys) return dispatch_ty<T, KMODE, true, false>(c, s, tm, out);
+    if (sums) return dispatch_ty<T, KMODE, false, true>(c, s, tm, out);
+    return dispatch_ty<T, KMODE, false, false>(c, s, tm, out);
+}
+
+template <typename T>
+static int dispatch_kmode(wx_ctx *c, cudaStream_t s, const CUtensorMap &tm, void *out) {
+    return per_col(c) ? dispatch_flags<T, 1>(c, s, tm, out) : dispatch_flags<T, 0>(c, s, tm, out);
 }
 
 int launch_step(wx_ctx *c, cudaStream_t s, long *launches) {
     const int src = c->cur, dst = 1 - c->cur;
-    int rc = (c->t_bytes == 4) ? dispatch_flags<float>(c, s, c->tmap[src], c->fld[dst])
-                               : dispatch_flags<double>(c, s, c->tmap[src], c->fld[dst]);
+    int rc = (c->t_bytes == 4) ? dispatch_kmode<float>(c, s, c->tmap[src], c->fld[dst])
+                               : dispatch_kmode<double>(c, s, c->tmap[src], c->fld[dst]);
     if (rc != WX_OK) return rc;
     ++*launches;
     if (c->flags & WX_SUMS) {
-        const long nblk = (long)((c->nx + kTileX - 1) / kTileX) * ((c->ny + c->cfg.ty - 1) / c->cfg.ty);
+        const long ntiles = (long)((c->nx + kTileX - 1) / kTileX) * ((c->ny + c->cfg.ty - 1) / c->cfg.ty);
         double *dst_sum = c->sums_ring + 2 * (c->sums_count % c->sums_cap);
-        sums_finalize<<<1, 1024, 0, s>>>(c->partials, nblk, c->h * c->h, dst_sum);
+        sums_finalize<<<1, 1024, 0, s>>>(c->partials, ntiles, c->h * c->h, dst_sum);
         WX_CK(cudaGetLastError(), "sums kernel");
         ++*launches;
         ++c->sums_count;
