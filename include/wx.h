@@ -144,14 +144,15 @@ int wx_info(const wx_ctx *c, int *nx, int *ny, int *nz, int *dtype,
             long *pitch_cells, long *device_bytes);
 
 /* Launch configuration of the step kernel (the autotuner's knobs): tile
- * rows ty (1, 2, 4 or 8; a tile is 64 x ty columns), TMA ring stages
- * (2..16, two k-planes each), resident CTAs per SM (>= 1) and the L2
- * prefetch distance in stages (0..64).  Rejected with WX_EUNSUPPORTED when
- * the shared-memory plan does not fit.  wx_get_step_config reads the
- * current one (chosen by a built-in heuristic until set). */
-int wx_set_step_config(wx_ctx *c, int ty, int stages, int ctas_per_sm,
+ * rows ty (1, 2, 4 or 8; a tile is 64 x ty columns), k-planes per TMA box
+ * kb (2 or 4), ring slots stages (3..16), resident CTAs per SM (>= 1) and
+ * an L2 bulk-prefetch distance in stages (0..64; 0 = off).  Rejected with
+ * WX_EUNSUPPORTED when the shared-memory plan does not fit (ty = 1 with
+ * kb = 4 is not built).  wx_get_step_config reads the current one (chosen
+ * by a built-in heuristic until set). */
+int wx_set_step_config(wx_ctx *c, int ty, int kb, int stages, int ctas_per_sm,
                        int prefetch);
-int wx_get_step_config(const wx_ctx *c, int *ty, int *stages,
+int wx_get_step_config(const wx_ctx *c, int *ty, int *kb, int *stages,
                        int *ctas_per_sm, int *prefetch, int *smem_bytes);
 
 /* Number of kernel launches the last wx_step issued. */

@@ -178,15 +178,17 @@ extern "C" int wx_info(const wx_ctx *c, int *nx, int *ny, int *nz, int *dtype, l
 
 extern "C" long wx_last_launches(const wx_ctx *c) { return c ? c->last_launches : -1; }
 
-extern "C" int wx_set_step_config(wx_ctx *c, int ty, int stages, int ctas_per_sm, int prefetch) {
+extern "C" int wx_set_step_config(wx_ctx *c, int ty, int kb, int stages, int ctas_per_sm, int prefetch) {
     if (!c) return WX_EINVAL;
-    if (!(ty == 1 || ty == 2 || ty == 4 || ty == 8) || stages < 2 || stages > 16 || ctas_per_sm < 1 ||
-        prefetch < 0 || prefetch > 64)
-        return fail(c, WX_EINVAL, "wx_set_step_config: ty in {1,2,4,8}, stages 2..16, ctas >= 1, prefetch 0..64");
+    if (!(ty == 1 || ty == 2 || ty == 4 || ty == 8) || !(kb == 2 || kb == 4) || stages < 3 || stages > 16 ||
+        ctas_per_sm < 1 || prefetch < 0 || prefetch > 64)
+        return fail(c, WX_EINVAL,
+                    "wx_set_step_config: ty in {1,2,4,8}, kb in {2,4}, stages 3..16, ctas >= 1, prefetch 0..64");
+    if (ty == 1 && kb == 4) return fail(c, WX_EUNSUPPORTED, "wx_set_step_config: ty = 1 with kb = 4 is not built");
     StepCfg g;
     g.ty = ty;
     g.stages = stages;
-    g.kb = 2;
+    g.kb = kb;
     g.ctas_per_sm = ctas_per_sm;
     g.prefetch = prefetch;
     if (!cfg_fits(c, g, nullptr)) return fail(c, WX_EUNSUPPORTED, "wx_set_step_config: shared memory does not fit");
@@ -195,9 +197,11 @@ extern "C" int wx_set_step_config(wx_ctx *c, int ty, int stages, int ctas_per_sm
     return WX_OK;
 }
 
-extern "C" int wx_get_step_config(const wx_ctx *c, int *ty, int *stages, int *ctas, int *prefetch, int *smem) {
+extern "C" int wx_get_step_config(const wx_ctx *c, int *ty, int *kb, int *stages, int *ctas, int *prefetch,
+                                  int *smem) {
     if (!c) return WX_EINVAL;
     if (ty) *ty = c->cfg.ty;
+    if (kb) *kb = c->cfg.kb;
     if (stages) *stages = c->cfg.stages;
     if (ctas) *ctas = c->cfg.ctas_per_sm;
     if (prefetch) *prefetch = c->cfg.prefetch;

@@ -25,7 +25,7 @@ constexpr int kGhostX = 16;
 constexpr int kTileX = 64;     // columns per tile in x (one warp, 2 per lane)
 constexpr int kBoxX = 72;      // TMA box width: 64 + halo, start a multiple of 4
 constexpr int kBoxX0 = 4;      // interior column 0 of a tile sits at box x = 4
-constexpr int kTabRec = 5;     // 4-value records per level in the table
+constexpr int kTabRec = 6;     // 4-value records per level in the table
 
 // Per-level table: kTabRec record arrays of nz records, record-major:
 //  A[k] = {wU, wU, wD, wD}          explicit vertical weights, paired for f32x2
@@ -36,8 +36,9 @@ constexpr int kTabRec = 5;     // 4-value records per level in the table
 //  D[k] = {1/m_k, 1/m_k, e_k, e_k}  that column's top-down elimination:
 //                                   m_k = b_k - c_k e_{k+1}, e_k = a_k/m_k
 //  E[k] = {ahat_k, chat_k, dz_k, 0} sub/super-diagonal per unit kappa_mult
+//  F[k] = {-e_k, -e_k, dz_k, dz_k}  back substitution and sums
 // with wU = dt kappa_h/(dz_k g_{k+1/2}) (0 at the top), wD likewise below.
-enum { REC_A = 0, REC_B = 1, REC_C = 2, REC_D = 3, REC_E = 4 };
+enum { REC_A = 0, REC_B = 1, REC_C = 2, REC_D = 3, REC_E = 4, REC_F = 5 };
 
 template <typename T> struct alignas(4 * sizeof(T)) Q4 { T x, y, z, w; };
 

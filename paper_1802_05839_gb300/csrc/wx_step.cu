@@ -26,6 +26,7 @@
 // Each field crosses HBM once per step in each direction.
 #include <algorithm>
 #include <cstdio>
+#include <type_traits>
 
 #include "ptx.cuh"
 #include "wx_internal.cuh"
@@ -55,7 +56,11 @@ template <> struct Pk<double> {
 
 // 2^-x: the optical depth is carried in log2 units, so exp(-tau) = 2^-tau2.
 template <typename T> __device__ __forceinline__ T exp2_neg(T x);
-template <> __device__ __forceinline__ float exp2_neg<float>(float x) { return exp2f(-x); }
+template <> __device__ __forceinline__ float exp2_neg<float>(float x) {
+    float y;  // hardware base-2 exponential (MUFU), flush-to-zero of tiny results
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-x));
+    return y;
+}
 template <> __device__ __forceinline__ double exp2_neg<double>(double x) { return exp2(-x); }
 
 template <typename T> __device__ __forceinline__ T recip(T m);
@@ -115,13 +120,12 @@ __device__ __forceinline__ void consumer_sync(int nthreads) {
 // the current tile's stores.  KMODE 0: kappa_mult = 1 everywhere (the
 // elimination coefficients come from the table); KMODE 1: per-column
 // kappa_mult, eliminated on the fly.
-template <typename T, int TY, int KMODE, bool PHYS, bool SUMS>
+template <typename T, int TY, int KB, int KMODE, bool PHYS, bool SUMS>
 __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_constant__ CUtensorMap tin,
                                                              const StepArgs<T> a, const int S, const int PF) {
     using PK = Pk<T>;
     using V = typename PK::V;
     using R4 = Q4<T>;
-    constexpr int KB = 2;                 // planes per stage
     constexpr int NT = 32 * TY;           // consumer threads
     constexpr int PL = (TY + 2) * kBoxX;  // elements per staged (plane, field)
     extern __shared__ __align__(128) unsigned char smem[];
@@ -202,14 +206,36 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
     // ---------------- consumers: two adjacent columns per lane
     const int tid = tx + 32 * wy;
     const R4 *tA = tab + REC_A * nz, *tB = tab + REC_B * nz, *tC = tab + REC_C * nz, *tD = tab + REC_D * nz,
-             *tE = tab + REC_E * nz;
+             *tE = tab + REC_E * nz, *tF = tab + REC_F * nz;
     const int ctr = (wy + 1) * kBoxX + kBoxX0 + 2 * tx;  // column pair in a staged plane (8-byte aligned)
     const size_t lev = (size_t)2 * a.R * a.P;              // elements between levels
     const size_t fld = (size_t)a.R * a.P;                  // T plane -> q plane
     const T zero = T(0);
+    const V m1 = PK::dup(T(-1));
     int slot = 0;
     uint32_t par = 0;
     bool ok = true;
+
+    // face winds of a tile's two columns (a, b): Ue, Uw, Vn, Vs each
+    struct Winds {
+        T v[8];
+    };
+    auto load_winds = [&](int t) -> Winds {
+        Winds w;
+        const int bx = t % gx, by = t / gx;
+        const int i0 = bx * kTileX + 2 * tx, j = by * TY + wy;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const bool v = (i0 + c < nx) && (j < ny) && a.advection;
+            const int ic = v ? i0 + c : 0, jc = v ? j : 0;
+            w.v[4 * c + 0] = v ? a.U[(size_t)jc * nx + ic] : T(0);
+            w.v[4 * c + 1] = v ? a.U[(size_t)jc * nx + (ic == 0 ? nx - 1 : ic - 1)] : T(0);
+            w.v[4 * c + 2] = v ? a.V[(size_t)jc * nx + ic] : T(0);
+            w.v[4 * c + 3] = v ? a.V[(size_t)(jc == 0 ? ny - 1 : jc - 1) * nx + ic] : T(0);
+        }
+        return w;
+    };
+    Winds wnext = load_winds(blockIdx.x < ntiles ? (int)blockIdx.x : 0);
 
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int bx = t % gx, by = t / gx;
@@ -218,27 +244,22 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
         const bool edge = bx == 0 || bx == gx - 1 || by == 0 || by == gy - 1;
 
         // per-column coefficients of the horizontal operator, paired (a, b)
+        const Winds wc = wnext;
+        if (t + (int)gridDim.x < ntiles) wnext = load_winds(t + gridDim.x);  // in flight during the tile
         V cC, cE, cW, cN, cS, km;
         {
             T c5[2][5], k1[2];
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
-                const bool v = c ? vb : va;
-                const int ic = v ? i0 + c : 0, jc = v ? j : 0;
-                T ue = 0, uw = 0, vn = 0, vs = 0;
-                if (a.advection) {
-                    ue = a.U[(size_t)jc * nx + ic];
-                    uw = a.U[(size_t)jc * nx + (ic == 0 ? nx - 1 : ic - 1)];
-                    vn = a.V[(size_t)jc * nx + ic];
-                    vs = a.V[(size_t)(jc == 0 ? ny - 1 : jc - 1) * nx + ic];
-                }
+                const T ue = wc.v[4 * c], uw = wc.v[4 * c + 1], vn = wc.v[4 * c + 2], vs = wc.v[4 * c + 3];
                 c5[c][1] = a.dh - a.dth * fmin(ue, zero);
                 c5[c][2] = a.dh + a.dth * fmax(uw, zero);
                 c5[c][3] = a.dh - a.dth * fmin(vn, zero);
                 c5[c][4] = a.dh + a.dth * fmax(vs, zero);
                 c5[c][0] = T(1) - T(4) * a.dh -
                            a.dth * (fmax(ue, zero) - fmin(uw, zero) + fmax(vn, zero) - fmin(vs, zero));
-                k1[c] = (KMODE == 1 && a.kmult) ? a.kmult[(size_t)jc * nx + ic] : T(1);
+                const bool v = c ? vb : va;
+                k1[c] = (KMODE == 1 && a.kmult && v) ? a.kmult[(size_t)j * nx + i0 + c] : T(1);
             }
             cC = V{c5[0][0], c5[1][0]};
             cE = V{c5[0][1], c5[1][1]};
@@ -259,38 +280,39 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
         V f_up = PK::dup(T(0)), h_up = PK::dup(T(0)), e_up = PK::dup(T(0));  // level k+1
         V chk = PK::dup(T(0));
         ColSum2<T> sumQ, sumT;
-        T *qcol = a.out + fld + (size_t)(j + 1) * a.P + (i0 + kGhostX);  // q plane, level 0
+        T *qp = a.out + fld + (size_t)(j + 1) * a.P + (i0 + kGhostX) + (size_t)(nz - 1) * lev;  // q, top
+        V *Fp = stF + (nz - 1) * NT + tid;                                                     // F, top
 
-        // one level: plane pk (T) / pk + PL (q), centre of level k-1 in nT/nQ
-        auto level = [&](int k, const T *pk, V nT, V nQ) {
-            const R4 A = tA[k], B = tB[k], C = tC[k];
-            const V b2 = V{B.x, B.y}, wu = V{A.x, A.y}, wd = V{A.z, A.w};
-            const V cCk = PK::add(cC, b2);
-            // T*
-            V r = PK::mul(cCk, curT);
-            r = PK::fma(cE, V{curT.y, pk[ctr + 2]}, r);
-            r = PK::fma(cW, V{pk[ctr - 1], curT.x}, r);
-            r = PK::fma(cN, *reinterpret_cast<const V *>(pk + ctr + kBoxX), r);
-            r = PK::fma(cS, *reinterpret_cast<const V *>(pk + ctr - kBoxX), r);
-            r = PK::fma(wu, prvT, r);
-            const V Ts = PK::fma(wd, nT, r);
-            // q*
-            const T *pq = pk + PL;
-            V rq = PK::mul(cCk, curQ);
-            rq = PK::fma(cE, V{curQ.y, pq[ctr + 2]}, rq);
-            rq = PK::fma(cW, V{pq[ctr - 1], curQ.x}, rq);
-            rq = PK::fma(cN, *reinterpret_cast<const V *>(pq + ctr + kBoxX), rq);
-            rq = PK::fma(cS, *reinterpret_cast<const V *>(pq + ctr - kBoxX), rq);
-            rq = PK::fma(wu, prvQ, rq);
-            const V Qs = PK::fma(wd, nQ, rq);
+        // phi* for one field at level k: two short FMA chains, summed
+        auto stencil = [&](const T *pf, V cur, V prv, V nxt, V cCk, V wu, V wd) -> V {
+            const V n = *reinterpret_cast<const V *>(pf + ctr + kBoxX);
+            const V s = *reinterpret_cast<const V *>(pf + ctr - kBoxX);
+            const T e = pf[ctr + 2], w = pf[ctr - 1];
+            V c1 = PK::fma(cN, n, PK::mul(cCk, cur));
+            c1.x = ::fma(cE.x, cur.y, c1.x);
+            c1.y = ::fma(cE.y, e, c1.y);
+            V c2 = PK::fma(wd, nxt, PK::fma(wu, prv, PK::mul(cS, s)));
+            c2.x = ::fma(cW.x, w, c2.x);
+            c2.y = ::fma(cW.y, cur.x, c2.y);
+            return PK::add(c1, c2);
+        };
+
+        // one level; EDGE selects the masked store path with ghost copies
+        auto level = [&](auto edge_tag, int k, const T *pk, V nT, V nQ) {
+            constexpr bool EDGE = decltype(edge_tag)::value;
+            const R4 A = tA[k], B = tB[k];
+            const V wu = V{A.x, A.y}, wd = V{A.z, A.w};
+            const V cCk = PK::add(cC, V{B.x, B.y});
+            const V Ts = stencil(pk, curT, prvT, nT, cCk, wu, wd);
+            const V Qs = stencil(pk + PL, curQ, prvQ, nQ, cCk, wu, wd);
             prvT = curT;
             prvQ = curQ;
             curT = nT;
             curQ = nQ;
 
             // q^{n+1} = q*
-            if (!edge) {
-                *reinterpret_cast<V *>(qcol + k * lev) = Qs;
+            if (!EDGE) {
+                *reinterpret_cast<V *>(qp) = Qs;
             } else {
                 T *row = a.out + k * lev + fld + (size_t)(j + 1) * a.P;
                 if (va) row[i0 + kGhostX] = Qs.x;
@@ -309,16 +331,19 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
                     if (vb) g[i0 + 1 + kGhostX] = Qs.y;
                 }
             }
+            qp -= lev;
+            const V Qm = EDGE ? V{va ? Qs.x : T(0), vb ? Qs.y : T(0)} : Qs;
             if (SUMS)
-                sumQ.add(V{va ? Qs.x : T(0), vb ? Qs.y : T(0)}, tE[k].z);
+                sumQ.add(Qm, tF[k].z);
             else
-                chk = PK::add(chk, Qs);
+                chk = PK::add(chk, Qm);
 
             if (PHYS) {
-                // radiation from the top: h = dt H_k
+                const R4 C = tC[k];
+                // radiation from the top: h = dt H_k = wH (E_top - E_bot)
                 const V tb = PK::fma(V{B.z, B.w}, Qs, tau);
                 const V Eb = V{exp2_neg(tb.x), exp2_neg(tb.y)};
-                const V hk = PK::mul(V{C.x, C.y}, PK::add(Et, PK::mul(Eb, PK::dup(T(-1)))));
+                const V hk = PK::mul(V{C.x, C.y}, PK::fma(Eb, m1, Et));
                 Et = Eb;
                 tau = tb;
                 // elimination from the top
@@ -332,80 +357,88 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
                     const V ak = PK::mul(km, PK::dup(E.x));
                     const V nck = PK::mul(km, PK::dup(-E.y));  // -c_k
                     // m = (1 - a - c) - c e_{k+1}
-                    const V m = PK::fma(nck, e_up, PK::add(PK::add(PK::dup(T(1)), PK::mul(ak, PK::dup(T(-1)))), nck));
+                    const V m = PK::fma(nck, e_up, PK::add(PK::fma(ak, m1, PK::dup(T(1))), nck));
                     const V inv = V{recip(m.x), recip(m.y)};
                     fk = PK::mul(PK::fma(nck, f_up, Ts), inv);
                     ek = PK::mul(ak, inv);
-                    stE[k * NT + tid] = ek;
+                    stE[k * NT + tid] = PK::mul(ek, m1);
                 }
                 // F_{k+1} = f_{k+1} + h_{k+1} + e_{k+1} h_k  (complete now)
-                if (k + 1 < nz) stF[(k + 1) * NT + tid] = PK::fma(e_up, hk, PK::add(f_up, h_up));
+                if (k + 1 < nz) Fp[NT] = PK::fma(e_up, hk, PK::add(f_up, h_up));
                 f_up = fk;
                 h_up = hk;
                 e_up = ek;
             } else {
-                stF[k * NT + tid] = Ts;
+                *Fp = Ts;
             }
+            Fp -= NT;
         };
 
-        for (int g = 0; g < n_st; ++g) {
-            const int z0 = nz - (g + 1) * KB;  // lowest plane of this stage (may be < 0)
-            const T *pa = ring + slot * SC;    // sub-plane 0 = level z0, sub-plane 1 = z0+1
-            const int nslot = (slot + 1 == S) ? 0 : slot + 1;
-            const uint32_t npar = (nslot == 0) ? (par ^ 1u) : par;
-            // levels z0+1 (upper) then z0 (lower); the one below z0 is the top
-            // sub-plane of the next stage
-            const int ku = z0 + 1, kl = z0;
-            const T *pu = pa + 2 * PL, *plw = pa;
-            if (ku >= 0) {
-                V nT = curT, nQ = curQ;
-                if (kl >= 0) {
-                    nT = *reinterpret_cast<const V *>(plw + ctr);
-                    nQ = *reinterpret_cast<const V *>(plw + PL + ctr);
+        // stage g holds levels z0 .. z0+KB-1 (sub-planes 0..KB-1), z0 =
+        // nz - KB(g+1); the level below z0 is the top sub-plane of stage g+1
+        auto run_pass1 = [&](auto edge_tag) {
+            for (int g = 0; g < n_st; ++g) {
+                const T *pa = ring + slot * SC;
+                const int nslot = (slot + 1 == S) ? 0 : slot + 1;
+                const uint32_t npar = (nslot == 0) ? (par ^ 1u) : par;
+                const int z0 = nz - (g + 1) * KB;
+#pragma unroll
+                for (int s = KB - 1; s >= 0; --s) {
+                    const int k = z0 + s;
+                    if (k < 0) continue;  // below the column (last stage only)
+                    V nT = curT, nQ = curQ;
+                    if (s > 0) {
+                        if (k >= 1) {
+                            nT = *reinterpret_cast<const V *>(pa + (s - 1) * 2 * PL + ctr);
+                            nQ = *reinterpret_cast<const V *>(pa + (s - 1) * 2 * PL + PL + ctr);
+                        }
+                    } else if (k >= 1) {
+                        if (ok) ok = mbar_wait_bounded(&full[nslot], npar);
+                        const T *pn = ring + nslot * SC + (KB - 1) * 2 * PL;
+                        nT = *reinterpret_cast<const V *>(pn + ctr);
+                        nQ = *reinterpret_cast<const V *>(pn + PL + ctr);
+                    }
+                    level(edge_tag, k, pa + s * 2 * PL, nT, nQ);
                 }
-                level(ku, pu, nT, nQ);
+                __syncwarp();
+                if (tx == 0) mbar_arrive(&empty[slot]);
+                slot = nslot;
+                par = npar;
             }
-            if (kl >= 0) {
-                V nT = curT, nQ = curQ;
-                if (kl >= 1) {
-                    if (ok) ok = mbar_wait_bounded(&full[nslot], npar);
-                    const T *pn = ring + nslot * SC + 2 * PL;  // next stage, upper sub-plane
-                    nT = *reinterpret_cast<const V *>(pn + ctr);
-                    nQ = *reinterpret_cast<const V *>(pn + PL + ctr);
-                }
-                level(kl, plw, nT, nQ);
-            }
-            __syncwarp();
-            if (tx == 0) mbar_arrive(&empty[slot]);
-            slot = nslot;
-            par = npar;
-        }
+        };
+        if (edge)
+            run_pass1(std::true_type{});
+        else
+            run_pass1(std::false_type{});
         if (PHYS) stF[tid] = PK::add(f_up, h_up);  // F_0 = f_0 + h_0
 
         // ------------- pass 2 (bottom up): T^{n+1}_k = F_k - e_k T^{n+1}_{k-1}
-        T *tcol = a.out + (size_t)(j + 1) * a.P + (i0 + kGhostX);  // T plane, level 0
         V Tprev = PK::dup(T(0));
         if (!edge) {
+            T *tp = a.out + (size_t)(j + 1) * a.P + (i0 + kGhostX);  // T plane, level 0
 #pragma unroll 4
             for (int k = 0; k < nz; ++k) {
+                const R4 Fr = tF[k];
                 V tn = stF[k * NT + tid];
                 if (PHYS) {
-                    const V ek = (KMODE == 0) ? V{tD[k].z, tD[k].w} : stE[k * NT + tid];
-                    tn = PK::fma(PK::mul(ek, PK::dup(T(-1))), Tprev, tn);
+                    const V ne = (KMODE == 0) ? V{Fr.x, Fr.y} : stE[k * NT + tid];
+                    tn = PK::fma(ne, Tprev, tn);
                     Tprev = tn;
                 }
-                *reinterpret_cast<V *>(tcol + k * lev) = tn;
+                *reinterpret_cast<V *>(tp) = tn;
+                tp += lev;
                 if (SUMS)
-                    sumT.add(tn, tE[k].z);
+                    sumT.add(tn, Fr.z);
                 else
                     chk = PK::add(chk, tn);
             }
         } else {
             for (int k = 0; k < nz; ++k) {
+                const R4 Fr = tF[k];
                 V tn = stF[k * NT + tid];
                 if (PHYS) {
-                    const V ek = (KMODE == 0) ? V{tD[k].z, tD[k].w} : stE[k * NT + tid];
-                    tn = PK::fma(PK::mul(ek, PK::dup(T(-1))), Tprev, tn);
+                    const V ne = (KMODE == 0) ? V{Fr.x, Fr.y} : stE[k * NT + tid];
+                    tn = PK::fma(ne, Tprev, tn);
                     Tprev = tn;
                 }
                 T *row = a.out + k * lev + (size_t)(j + 1) * a.P;
@@ -424,10 +457,11 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
                     if (va) g[i0 + kGhostX] = tn.x;
                     if (vb) g[i0 + 1 + kGhostX] = tn.y;
                 }
+                const V tm = V{va ? tn.x : T(0), vb ? tn.y : T(0)};
                 if (SUMS)
-                    sumT.add(V{va ? tn.x : T(0), vb ? tn.y : T(0)}, tE[k].z);
+                    sumT.add(tm, Fr.z);
                 else
-                    chk = PK::add(chk, V{va ? tn.x : T(0), vb ? tn.y : T(0)});
+                    chk = PK::add(chk, tm);
             }
         }
 
@@ -453,11 +487,8 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
                 a.partials[2 * (size_t)t + 1] = tt;
             }
             consumer_sync(NT);
-        } else {
-            // lanes outside the grid in edge tiles computed from padding: skipped
-            const bool bad = edge ? ((va && !isfinite(chk.x)) || (vb && !isfinite(chk.y)))
-                                  : (!isfinite(chk.x) || !isfinite(chk.y));
-            if (bad) atomicOr(a.status, ST_NONFINITE);
+        } else if (!isfinite(chk.x) || !isfinite(chk.y)) {
+            atomicOr(a.status, ST_NONFINITE);  // edge tiles tallied only their valid columns
         }
     }
     if (!ok && tx == 0) atomicOr(a.status, ST_TIMEOUT);
@@ -519,6 +550,7 @@ __global__ void tables_kernel(const double *lev, int nz, double dt, double kappa
         tab[REC_C * nz + k] = Q4<T>{(T)wH, (T)wH, (T)(-ch), (T)(-ch)};
         tab[REC_D * nz + k] = Q4<T>{(T)(1.0 / m), (T)(1.0 / m), (T)e, (T)e};
         tab[REC_E * nz + k] = Q4<T>{(T)ah, (T)ch, (T)dz[k], (T)0};
+        tab[REC_F * nz + k] = Q4<T>{(T)(-e), (T)(-e), (T)dz[k], (T)dz[k]};
     }
 }
 
@@ -570,7 +602,7 @@ __global__ void __launch_bounds__(128) columns_kernel(const T *__restrict__ Ts, 
                                                       const T *__restrict__ km, const Q4<T> *__restrict__ gtab,
                                                       T *__restrict__ Tout, T *__restrict__ tend, long ncol,
                                                       int nz, T dt) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     Q4<T> *tab = reinterpret_cast<Q4<T> *>(smem);
     T *cpa = reinterpret_cast<T *>(tab + kTabRec * nz);
     T *dpa = cpa + nz * blockDim.x;
@@ -696,53 +728,56 @@ int launch_columns(wx_ctx *c, const void *Ts, const void *qs, const void *km, vo
     return WX_OK;
 }
 
-constexpr int kKB = 2;  // planes per TMA stage
 
 static bool per_col(const wx_ctx *c) { return c->kmult != nullptr; }
 
 bool cfg_fits(const wx_ctx *c, const StepCfg &cfg, int *smem_bytes) {
-    const SmemPlan p = plan_smem(c->nz, cfg.ty, cfg.stages, kKB, c->t_bytes, per_col(c));
+    const SmemPlan p = plan_smem(c->nz, cfg.ty, cfg.stages, cfg.kb, c->t_bytes, per_col(c));
     if (smem_bytes) *smem_bytes = p.total;
     // the per-SM budget: ctas_per_sm CTAs plus 1 KB runtime reserve each
-    return cfg.stages >= 3 && cfg.ctas_per_sm >= 1 && p.total <= 227 * 1024 &&
+    return cfg.stages >= 3 && (cfg.kb == 2 || cfg.kb == 4) && cfg.ctas_per_sm >= 1 && p.total <= 227 * 1024 &&
            cfg.ctas_per_sm * (p.total + 1024) <= 228 * 1024;
 }
 
 StepCfg default_cfg(const wx_ctx *c) {
-    // Most resident consumer warps per SM first (capped at 16), then taller
-    // tiles (less halo), then the deeper TMA ring (3..8 stages of 2 planes);
-    // the L2 prefetch runs 8 stages ahead.
+    // The TMA unit of an SM completes boxes at a roughly fixed rate, so big
+    // boxes (4 planes) and tall tiles come first; then the most resident
+    // consumer warps per SM (capped at 16), then the deeper ring (3..8 slots).
     StepCfg best;
     best.ty = 1;
     best.stages = 3;
+    best.kb = 2;
     best.ctas_per_sm = 1;
-    int best_warps = -1, best_st = 0;
-    for (int ty : {1, 2, 4, 8}) {
-        for (int st = 8; st >= 3; --st) {
-            StepCfg g;
-            g.ty = ty;
-            g.stages = st;
-            g.kb = kKB;
-            int bytes = 0;
-            g.ctas_per_sm = 1;
-            if (!cfg_fits(c, g, &bytes)) continue;
-            g.ctas_per_sm = std::min(228 * 1024 / (bytes + 1024), 2048 / (32 * (ty + 1)));
-            const int warps = std::min(g.ctas_per_sm * ty, 16);
-            if (warps > best_warps || (warps == best_warps && (ty > best.ty || (ty == best.ty && st > best_st)))) {
-                best = g;
-                best_warps = warps;
-                best_st = st;
+    long best_score = -1;
+    for (int kb : {2, 4}) {
+        for (int ty : {1, 2, 4, 8}) {
+            for (int st = 8; st >= 3; --st) {
+                StepCfg g;
+                g.ty = ty;
+                g.stages = st;
+                g.kb = kb;
+                int bytes = 0;
+                g.ctas_per_sm = 1;
+                if (!cfg_fits(c, g, &bytes)) continue;
+                g.ctas_per_sm = std::min(228 * 1024 / (bytes + 1024), 2048 / (32 * (ty + 1)));
+                const int warps = std::min(g.ctas_per_sm * ty, 16);
+                const long box = (long)kb * 2 * (ty + 2) * kBoxX * c->t_bytes;  // both fields
+                const long score = ((box >= 16384) ? 1L << 40 : 0) + ((long)warps << 20) + ((long)ty << 10) + st;
+                if (score > best_score) {
+                    best = g;
+                    best_score = score;
+                }
             }
         }
     }
-    best.prefetch = 8;
+    best.prefetch = 0;
     return best;
 }
 
-template <typename T, int TY, int KMODE, bool PHYS, bool SUMS>
+template <typename T, int TY, int KB, int KMODE, bool PHYS, bool SUMS>
 static int launch_step_t(wx_ctx *c, cudaStream_t s, const CUtensorMap &tm, void *out) {
-    auto kern = step_kernel<T, TY, KMODE, PHYS, SUMS>;
-    const SmemPlan pl = plan_smem(c->nz, TY, c->cfg.stages, kKB, c->t_bytes, KMODE == 1);
+    auto kern = step_kernel<T, TY, KB, KMODE, PHYS, SUMS>;
+    const SmemPlan pl = plan_smem(c->nz, TY, c->cfg.stages, KB, c->t_bytes, KMODE == 1);
     WX_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.total), "smem attr");
     StepArgs<T> a;
     a.out = reinterpret_cast<T *>(out);
@@ -771,12 +806,16 @@ static int launch_step_t(wx_ctx *c, cudaStream_t s, const CUtensorMap &tm, void 
 
 template <typename T, int KMODE, bool PHYS, bool SUMS>
 static int dispatch_ty(wx_ctx *c, cudaStream_t s, const CUtensorMap &tm, void *out) {
-    switch (c->cfg.ty) {
-        case 1: return launch_step_t<T, 1, KMODE, PHYS, SUMS>(c, s, tm, out);
-        case 2: return launch_step_t<T, 2, KMODE, PHYS, SUMS>(c, s, tm, out);
-        case 4: return launch_step_t<T, 4, KMODE, PHYS, SUMS>(c, s, tm, out);
-        case 8: return launch_step_t<T, 8, KMODE, PHYS, SUMS>(c, s, tm, out);
-        default: c->err = "unsupported tile rows"; return WX_EUNSUPPORTED;
+    const int key = c->cfg.ty * 10 + c->cfg.kb;
+    switch (key) {
+        case 12: return launch_step_t<T, 1, 2, KMODE, PHYS, SUMS>(c, s, tm, out);
+        case 22: return launch_step_t<T, 2, 2, KMODE, PHYS, SUMS>(c, s, tm, out);
+        case 42: return launch_step_t<T, 4, 2, KMODE, PHYS, SUMS>(c, s, tm, out);
+        case 82: return launch_step_t<T, 8, 2, KMODE, PHYS, SUMS>(c, s, tm, out);
+        case 24: return launch_step_t<T, 2, 4, KMODE, PHYS, SUMS>(c, s, tm, out);
+        case 44: return launch_step_t<T, 4, 4, KMODE, PHYS, SUMS>(c, s, tm, out);
+        case 84: return launch_step_t<T, 8, 4, KMODE, PHYS, SUMS>(c, s, tm, out);
+        default: c->err = "unsupported tile rows / planes per stage"; return WX_EUNSUPPORTED;
     }
 }
 

@@ -57,8 +57,8 @@ SIGNATURES = [
                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long)]),
     ("wx_last_launches", ctypes.c_long, [_VP]),
-    ("wx_set_step_config", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
-    ("wx_get_step_config", ctypes.c_int, [_VP] + [ctypes.POINTER(ctypes.c_int)] * 5),
+    ("wx_set_step_config", ctypes.c_int, [_VP] + [ctypes.c_int] * 5),
+    ("wx_get_step_config", ctypes.c_int, [_VP] + [ctypes.POINTER(ctypes.c_int)] * 6),
     ("wx_sums_noalloc", ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int, _VP, ctypes.c_double, _VP, _VP]),
     ("wx_sums_noalloc_error", ctypes.c_char_p, []),
@@ -189,13 +189,13 @@ class Context:
         return dict(nx=v[0].value, ny=v[1].value, nz=v[2].value, dtype=v[3].value,
                     pitch=pitch.value, device_bytes=nbytes.value)
 
-    def set_step_config(self, ty, stages, ctas_per_sm, prefetch):
-        _check(lib().wx_set_step_config(self.ptr, ty, stages, ctas_per_sm, prefetch), self.ptr)
+    def set_step_config(self, ty, kb, stages, ctas_per_sm, prefetch=0):
+        _check(lib().wx_set_step_config(self.ptr, ty, kb, stages, ctas_per_sm, prefetch), self.ptr)
 
     def step_config(self):
-        v = [ctypes.c_int() for _ in range(5)]
+        v = [ctypes.c_int() for _ in range(6)]
         _check(lib().wx_get_step_config(self.ptr, *[ctypes.byref(x) for x in v]), self.ptr)
-        return dict(zip(("ty", "stages", "ctas_per_sm", "prefetch", "smem_bytes"), (x.value for x in v)))
+        return dict(zip(("ty", "kb", "stages", "ctas_per_sm", "prefetch", "smem_bytes"), (x.value for x in v)))
 
     def last_launches(self):
         return int(lib().wx_last_launches(self.ptr))
