@@ -95,27 +95,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_case(dtype):
+def make_case(dtype, nx=1581, ny=1301, nz=58):
     from paper_1802_05839_gb300 import inputs
-    case = inputs.paper_grid_case(near_singular=(dtype == "mixed"))
+    case = inputs.paper_grid_case(nx, ny, nz, near_singular=(dtype == "mixed"))
     return inputs.round_to_f32(case) if dtype in ("f32", "mixed") else case
 
 
-def time_steps(ctx, stream, steps, warmup, flags_sums=False):
-    """Per-step CUDA-event times (ms) of `steps` steps after `warmup`."""
-    import torch
-    for _ in range(warmup):
-        ctx.step(1, stream=stream)
-    ctx.sync()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
-    torch.cuda.synchronize()
-    with torch.cuda.stream(stream):
-        ev[0].record(stream)
-        for s in range(steps):
-            ctx.step(1, stream=stream)
-            ev[s + 1].record(stream)
-    stream.synchronize()
-    return [ev[s].elapsed_time(ev[s + 1]) for s in range(steps)]
+def traffic_record(dtype):
+    """DRAM bytes per launch of the step kernel from the committed ncu
+    summary, or None when the kernel source changed since the capture."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    src = os.path.join(ROOT, "paper_1802_05839_gb300", "csrc", "wx_step.cu")
+    if not os.path.exists(p):
+        return None
+    rec = json.load(open(p)).get(dtype)
+    if not rec:
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return rec["traffic_bytes_per_launch"] if rec.get("wx_step_cu_sha256") == sha else None
 
 
 def cpu_baseline(case, budget_s=12.0):
@@ -129,7 +127,7 @@ def cpu_baseline(case, budget_s=12.0):
         oracle.step_columns(case, case.T, case.q, case.U, case.V, ci, cj)
         done += 1
         el = time.perf_counter() - t0
-        if el > budget_s or done >= 20:
+        if el > budget_s:
             break
     return {"value": done * len(cols) * case.nz / el, "unit": "cell-steps/s",
             "cores": oracle.threads(), "kind": "oracle",
@@ -140,13 +138,13 @@ def cpu_baseline(case, budget_s=12.0):
 
 def run_reference(args):
     """--impl reference: the FP64 CPU oracle, as it stands, on this host's
-    cores; each step a bounded sample (every 20th column) of the workload."""
+    cores; each step a bounded sample (every 50th column) of the workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle
     case = make_case("f64")
-    cols = np.arange(0, case.nx * case.ny, 20)
+    cols = np.arange(0, case.nx * case.ny, 50)
     ci, cj = (cols % case.nx).astype(np.int32), (cols // case.nx).astype(np.int32)
     for _ in range(args.warmup):
         oracle.step_columns(case, case.T, case.q, case.U, case.V, ci, cj)
@@ -157,7 +155,7 @@ def run_reference(args):
         times.append(time.perf_counter() - t0)
     per = sum(times) / len(times)
     value = len(cols) * case.nz / per
-    sample = (f"oracle step on {len(cols)} of {case.nx * case.ny} columns (every 20th) of the "
+    sample = (f"oracle step on {len(cols)} of {case.nx * case.ny} columns (every 50th) of the "
               f"{case.nx}x{case.ny}x{case.nz} workload per step")
     print(json.dumps({
         "impl": "reference", "metric": args.metric, "value": value, "unit": "cell-steps/s",
@@ -215,9 +213,11 @@ def run_ours(args):
         dist.init_process_group("nccl")
 
     dtype = args.dtype
-    case = make_case(dtype)
+    case = make_case(dtype, args.nx, args.ny, args.nz)
     ctx = wx.Context(case.nx, case.ny, case.nz, dtype)
-    ctx.set_params(case)
+    # the mixed-precision workload records FP64 mass/energy sums every step
+    flags = wx.WX_ADVECTION | wx.WX_PHYSICS | (wx.WX_SUMS if dtype == "mixed" else 0)
+    ctx.set_params(case, flags=flags)
     ctx.load_fields(case.T, case.q, case.U, case.V)
     stream = torch.cuda.Stream()
 
@@ -249,6 +249,7 @@ def run_ours(args):
         dist.barrier()
         total_ms = float(t.item())
     launches = ctx.last_launches() * args.steps  # one wx_step(1) per timed step
+    step_cfg = ctx.step_config()
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
@@ -268,11 +269,12 @@ def run_ours(args):
         "dtype": {"f32": "f32", "f64": "f64", "mixed": "f32+f64"}[dtype], "data": "synthetic",
         "config": {"workload": f"paper grid {case.nx}x{case.ny}x{case.nz} ({dtype}), "
                                "dynamics + column physics per step",
+                   "step_config": step_cfg,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (2 x field buffers of "
                          f"{case.cells * CELL_BYTES[dtype] // 2 / 1e6:.0f} MB), no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": traffic_record(dtype),
                      "kernel": "step_kernel", "alg_bytes_per_launch": alg_bytes,
                      "kernel_ms": kern_ms, "peak_source": peak_kind},
         "gpu_launches": launches,
@@ -288,12 +290,15 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64", "mixed"])
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--nx", type=int, default=1581, help="grid override (profiling captures only)")
+    ap.add_argument("--ny", type=int, default=1301, help="grid override (profiling captures only)")
+    ap.add_argument("--nz", type=int, default=58, help="grid override (profiling captures only)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     args.metric = "cell-steps/s at 1581x1301x58 (FP32 vs FP64), % HBM peak"

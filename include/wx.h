@@ -155,6 +155,10 @@ int wx_set_step_config(wx_ctx *c, int ty, int kb, int stages, int ctas_per_sm,
 int wx_get_step_config(const wx_ctx *c, int *ty, int *kb, int *stages,
                        int *ctas_per_sm, int *prefetch, int *smem_bytes);
 
+/* WX_MIXED: number of columns flagged for the FP64 elimination (dominance
+ * ratio below dd_threshold), 0 for other contexts. */
+int wx_flagged_columns(const wx_ctx *c, long *n_flagged);
+
 /* Number of kernel launches the last wx_step issued. */
 long wx_last_launches(const wx_ctx *c);
 

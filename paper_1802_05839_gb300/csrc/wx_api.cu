@@ -128,7 +128,9 @@ extern "C" int wx_create(int nx, int ny, int nz, int dtype, wx_ctx **out) {
                   {(void **)&c->d_lev, 3 * (size_t)nz * sizeof(double)},
                   {(void **)&c->d_status, sizeof(unsigned)},
                   {(void **)&c->partials, 2 * nblk_max * sizeof(double)},
-                  {(void **)&c->sums_ring, 2 * (size_t)c->sums_cap * sizeof(double)}};
+                  {(void **)&c->sums_ring, 2 * (size_t)c->sums_cap * sizeof(double)},
+                  {(void **)&c->fin_park, 2 * 64 * sizeof(double)},
+                  {(void **)&c->fin_ticket, sizeof(unsigned)}};
     for (auto &a : allocs) {
         cudaError_t e = cudaMalloc(a.p, a.n);
         if (e != cudaSuccess) {
@@ -140,6 +142,7 @@ extern "C" int wx_create(int nx, int ny, int nz, int dtype, wx_ctx **out) {
     c->partials_cap = nblk_max;
     if (cudaMemset(c->fld[0], 0, fbytes) != cudaSuccess || cudaMemset(c->fld[1], 0, fbytes) != cudaSuccess ||
         cudaMemset(c->d_status, 0, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(c->fin_ticket, 0, sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(c->U, 0, cols * c->t_bytes) != cudaSuccess ||
         cudaMemset(c->V, 0, cols * c->t_bytes) != cudaSuccess) {
         c->err = "wx_create: cudaMemset failed";
@@ -155,7 +158,8 @@ extern "C" void wx_destroy(wx_ctx *c) {
     if (!c) return;
     void *ptrs[] = {c->fld[0], c->fld[1], c->U,        c->V,         c->kmult,     c->tab,
                     c->d_lev,  c->staging, c->d_status, c->partials, c->sums_ring, c->flag_list,
-                    c->flag_fac, c->flag_mask, c->flag_rhs};
+                    c->flag_idx, c->flag_fac, c->flag_e, c->flag_side, c->flag_corr,
+                    c->fin_park, c->fin_ticket};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete c;
@@ -177,6 +181,12 @@ extern "C" int wx_info(const wx_ctx *c, int *nx, int *ny, int *nz, int *dtype, l
 }
 
 extern "C" long wx_last_launches(const wx_ctx *c) { return c ? c->last_launches : -1; }
+
+extern "C" int wx_flagged_columns(const wx_ctx *c, long *n) {
+    if (!c || !n) return WX_EINVAL;
+    *n = c->n_flag;
+    return WX_OK;
+}
 
 extern "C" int wx_set_step_config(wx_ctx *c, int ty, int kb, int stages, int ctas_per_sm, int prefetch) {
     if (!c) return WX_EINVAL;
@@ -264,11 +274,15 @@ extern "C" int wx_set_params(wx_ctx *c, const wx_params *p) {
         cudaError_t e = cudaMemcpy(tmp, p->kappa_mult, cols * sizeof(double), cudaMemcpyHostToDevice);
         int rc = (e == cudaSuccess) ? launch_convert(c, tmp, c->kmult, cols, 0) : cuda_fail(c, e, "upload kappa_mult");
         cudaDeviceSynchronize();
+        if (rc == WX_OK) rc = setup_mixed(c, tmp);
         cudaFree(tmp);
         if (rc != WX_OK) return rc;
-    } else if (c->kmult) {
-        cudaFree(c->kmult);
-        c->kmult = nullptr;
+    } else {
+        if (c->kmult) {
+            cudaFree(c->kmult);
+            c->kmult = nullptr;
+        }
+        RC(setup_mixed(c, nullptr));
     }
     CK(cudaDeviceSynchronize(), "wx_set_params");
     // the kernel variant (and its shared-memory plan) depends on kappa_mult

@@ -59,6 +59,10 @@ template <typename T> struct StepArgs {
     int nx, ny, nz, P, R;
     T dth, dh;                    // dt/h, dt*kappa_h/h^2
     int advection;
+    // WX_MIXED: listed columns park T* and dt*H in side[k][0][f], side[k][1][f]
+    const int *flag_idx;          // [ny][nx]: index f of a listed column, else -1
+    float *side;                  // [nz][2][n_list]
+    long n_list;
 };
 
 // A step-kernel configuration: rows per tile, TMA ring stages (2 planes
@@ -113,6 +117,8 @@ struct wx_ctx {
     double *partials = nullptr;
     size_t partials_cap = 0;
     double *sums_ring = nullptr;
+    double *fin_park = nullptr;     // [64][2] per-block results of the sums reduction
+    unsigned *fin_ticket = nullptr; // arrival counter of the sums reduction (self-resetting)
     int sums_cap = 4096;
     long sums_count = 0;
 
@@ -124,10 +130,13 @@ struct wx_ctx {
 
     // WX_MIXED: columns whose elimination runs in FP64
     int *flag_list = nullptr;    // [n_flag] column index j*nx+i
-    double *flag_fac = nullptr;  // FP64 elimination factors of flagged columns
-    unsigned char *flag_mask = nullptr;  // [ny*nx]
-    float *flag_rhs = nullptr;   // side buffer of flagged columns
-    long n_flag = 0;
+    int *flag_idx = nullptr;     // [ny*nx] f or -1
+    double *flag_fac = nullptr;  // [nz][n_list][2] FP64 (1/m_k, c_k/m_k) from the top
+    float *flag_e = nullptr;     // [nz][n_list] e_k for the FP32 back substitution
+    float *flag_side = nullptr;  // [nz][2][n_list] T* and dt*H parked by the step kernel
+    double *flag_corr = nullptr; // [n_flag] energy correction of the FP64 solve (sums)
+    long n_flag = 0;             // columns solved in FP64 (first in the list)
+    long n_list = 0;             // all listed columns (kappa_mult != 1)
 
     wx::StepCfg cfg;
     bool cfg_forced = false;
@@ -147,6 +156,7 @@ int launch_step(wx_ctx *c, cudaStream_t s, long *launches);
 int launch_columns(wx_ctx *c, const void *Ts, const void *qs, const void *km, void *Tout, void *tend,
                    long ncol, cudaStream_t s);
 StepCfg default_cfg(const wx_ctx *c);
+int setup_mixed(wx_ctx *c, const double *km64);
 bool cfg_fits(const wx_ctx *c, const StepCfg &cfg, int *smem_bytes);
 int encode_tmap(wx_ctx *c, int which, int ty, int kb);
 

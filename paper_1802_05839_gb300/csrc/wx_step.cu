@@ -67,16 +67,17 @@ template <typename T> __device__ __forceinline__ T recip(T m);
 template <> __device__ __forceinline__ float recip<float>(float m) { return __frcp_rn(m); }
 template <> __device__ __forceinline__ double recip<double>(double m) { return 1.0 / m; }
 
-// Column sums of phi*dz for the lane's two columns, compensated in FP32
-// (exact product error + TwoSum) so the FP64 total is not limited by a
-// 58-term FP32 sum; plain FMA accumulation in FP64.
+// Column sums of phi*dz for the lane's two columns.  FP32: dz is carried as
+// hi + lo floats and every product and addition is compensated (exact
+// product error, TwoSum), so the FP64 total is that of the stored FP32
+// values times the FP64 dz; FP64: plain FMA accumulation.
 template <typename T> struct ColSum2;
 template <> struct ColSum2<float> {
     float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
-    __device__ __forceinline__ void add(float2 v, float w) {
-        const float2 w2 = make_float2(w, w), m1 = make_float2(-1.f, -1.f);
+    __device__ __forceinline__ void add(float2 v, float whi, float wlo) {
+        const float2 w2 = make_float2(whi, whi), m1 = make_float2(-1.f, -1.f);
         const float2 p = __fmul2_rn(v, w2);
-        const float2 pe = __ffma2_rn(v, w2, __fmul2_rn(p, m1));
+        const float2 pe = __ffma2_rn(v, make_float2(wlo, wlo), __ffma2_rn(v, w2, __fmul2_rn(p, m1)));
         const float2 s1 = __fadd2_rn(s, p);
         const float2 bp = __ffma2_rn(s, m1, s1);  // s1 - s
         const float2 sa = __ffma2_rn(bp, m1, s1); // s1 - bp
@@ -90,7 +91,7 @@ template <> struct ColSum2<float> {
 };
 template <> struct ColSum2<double> {
     double2 s = make_double2(0.0, 0.0);
-    __device__ __forceinline__ void add(double2 v, double w) {
+    __device__ __forceinline__ void add(double2 v, double w, double) {
         s.x = ::fma(v.x, w, s.x);
         s.y = ::fma(v.y, w, s.y);
     }
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
     const int gx = (nx + kTileX - 1) / kTileX, gy = (ny + TY - 1) / TY;
     const int ntiles = gx * gy;
     const int n_st = (nz + KB - 1) / KB;  // stages per tile
-    const SmemPlan pl = plan_smem(nz, TY, S, KB, (int)sizeof(T), KMODE == 1);
+    const SmemPlan pl = plan_smem(nz, TY, S, KB, (int)sizeof(T), KMODE == 1);  // e_k per column
     R4 *tab = reinterpret_cast<R4 *>(smem + pl.tab_off);
     T *ring = reinterpret_cast<T *>(smem + pl.ring_off);
     V *stF = reinterpret_cast<V *>(smem + pl.state_off);  // [nz][NT] F of the 2 columns
@@ -247,6 +248,7 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
         const Winds wc = wnext;
         if (t + (int)gridDim.x < ntiles) wnext = load_winds(t + gridDim.x);  // in flight during the tile
         V cC, cE, cW, cN, cS, km;
+        int fl[2];
         {
             T c5[2][5], k1[2];
 #pragma unroll
@@ -260,6 +262,7 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
                            a.dth * (fmax(ue, zero) - fmin(uw, zero) + fmax(vn, zero) - fmin(vs, zero));
                 const bool v = c ? vb : va;
                 k1[c] = (KMODE == 1 && a.kmult && v) ? a.kmult[(size_t)j * nx + i0 + c] : T(1);
+                fl[c] = (KMODE == 2 && v) ? a.flag_idx[(size_t)j * nx + i0 + c] : -1;
             }
             cC = V{c5[0][0], c5[1][0]};
             cE = V{c5[0][1], c5[1][1]};
@@ -334,7 +337,7 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
             qp -= lev;
             const V Qm = EDGE ? V{va ? Qs.x : T(0), vb ? Qs.y : T(0)} : Qs;
             if (SUMS)
-                sumQ.add(Qm, tF[k].z);
+                sumQ.add(Qm, tF[k].z, tF[k].w);
             else
                 chk = PK::add(chk, Qm);
 
@@ -348,7 +351,7 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
                 tau = tb;
                 // elimination from the top
                 V fk, ek;
-                if (KMODE == 0) {
+                if (KMODE != 1) {
                     const R4 D = tD[k];
                     fk = PK::mul(PK::fma(V{C.z, C.w}, f_up, Ts), V{D.x, D.y});
                     ek = V{D.z, D.w};
@@ -362,6 +365,17 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
                     fk = PK::mul(PK::fma(nck, f_up, Ts), inv);
                     ek = PK::mul(ak, inv);
                     stE[k * NT + tid] = PK::mul(ek, m1);
+                }
+                if (KMODE == 2) {  // listed columns: T* and dt*H for the side solve, [k][2][n]
+                    float *sd = a.side + (size_t)k * 2 * a.n_list;
+                    if (fl[0] >= 0) {
+                        sd[fl[0]] = (float)Ts.x;
+                        sd[a.n_list + fl[0]] = (float)hk.x;
+                    }
+                    if (fl[1] >= 0) {
+                        sd[fl[1]] = (float)Ts.y;
+                        sd[a.n_list + fl[1]] = (float)hk.y;
+                    }
                 }
                 // F_{k+1} = f_{k+1} + h_{k+1} + e_{k+1} h_k  (complete now)
                 if (k + 1 < nz) Fp[NT] = PK::fma(e_up, hk, PK::add(f_up, h_up));
@@ -421,14 +435,14 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
                 const R4 Fr = tF[k];
                 V tn = stF[k * NT + tid];
                 if (PHYS) {
-                    const V ne = (KMODE == 0) ? V{Fr.x, Fr.y} : stE[k * NT + tid];
+                    const V ne = (KMODE != 1) ? V{Fr.x, Fr.y} : stE[k * NT + tid];
                     tn = PK::fma(ne, Tprev, tn);
                     Tprev = tn;
                 }
                 *reinterpret_cast<V *>(tp) = tn;
                 tp += lev;
                 if (SUMS)
-                    sumT.add(tn, Fr.z);
+                    sumT.add(tn, Fr.z, Fr.w);
                 else
                     chk = PK::add(chk, tn);
             }
@@ -437,7 +451,7 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
                 const R4 Fr = tF[k];
                 V tn = stF[k * NT + tid];
                 if (PHYS) {
-                    const V ne = (KMODE == 0) ? V{Fr.x, Fr.y} : stE[k * NT + tid];
+                    const V ne = (KMODE != 1) ? V{Fr.x, Fr.y} : stE[k * NT + tid];
                     tn = PK::fma(ne, Tprev, tn);
                     Tprev = tn;
                 }
@@ -459,7 +473,7 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
                 }
                 const V tm = V{va ? tn.x : T(0), vb ? tn.y : T(0)};
                 if (SUMS)
-                    sumT.add(tm, Fr.z);
+                    sumT.add(tm, Fr.z, Fr.w);
                 else
                     chk = PK::add(chk, tm);
             }
@@ -494,15 +508,27 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
     if (!ok && tx == 0) atomicOr(a.status, ST_TIMEOUT);
 }
 
-// Fixed-order FP64 reduction of the per-tile partials into one ring entry.
-__global__ void __launch_bounds__(1024) sums_finalize(const double *__restrict__ part, long nblk, double h2,
-                                                      double *__restrict__ dst) {
-    __shared__ double sq[1024], st[1024];
+// Fixed-order FP64 reduction of the per-tile partials (and of the side
+// solve's energy corrections) into one ring entry.  Block b reduces a fixed
+// chunk with a fixed tree and parks its result; the last block to finish
+// (ticket) adds the parked results in block order, so the total does not
+// depend on scheduling.
+constexpr int kFinBlocks = 64;
+__global__ void __launch_bounds__(256) sums_finalize(const double *__restrict__ part, long nblk,
+                                                     const double *__restrict__ corr, long ncorr, double h2,
+                                                     double *__restrict__ park, unsigned *__restrict__ ticket,
+                                                     double *__restrict__ dst) {
+    __shared__ double sq[256], st[256];
+    __shared__ bool last;
+    const long per = (nblk + gridDim.x - 1) / gridDim.x, perc = (ncorr + gridDim.x - 1) / gridDim.x;
+    const long b0 = blockIdx.x * per, b1 = min(nblk, b0 + per);
+    const long c0 = blockIdx.x * perc, c1 = min(ncorr, c0 + perc);
     double q = 0.0, t = 0.0;
-    for (long b = threadIdx.x; b < nblk; b += blockDim.x) {
+    for (long b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
         q += part[2 * b];
         t += part[2 * b + 1];
     }
+    for (long b = c0 + threadIdx.x; b < c1; b += blockDim.x) t += corr[b];
     sq[threadIdx.x] = q;
     st[threadIdx.x] = t;
     __syncthreads();
@@ -514,9 +540,162 @@ __global__ void __launch_bounds__(1024) sums_finalize(const double *__restrict__
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        dst[0] = h2 * sq[0];
-        dst[1] = h2 * st[0];
+        park[2 * blockIdx.x] = sq[0];
+        park[2 * blockIdx.x + 1] = st[0];
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double Q = 0.0, Tt = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) {
+            Q += ((volatile double *)park)[2 * b];
+            Tt += ((volatile double *)park)[2 * b + 1];
+        }
+        dst[0] = h2 * Q;
+        dst[1] = h2 * Tt;
+        *ticket = 0u;  // ready for the next step
+    }
+}
+
+// ------------------------------------------------------------ WX_MIXED
+// Dominance ratio of column (i, j): min_k |b_k| / (|a_k| + |c_k|) of its
+// implicit vertical-diffusion matrix, in FP64.
+__device__ double column_ratio(const double *lev, int nz, double dt, double km) {
+    const double *dz = lev, *kl = lev + nz;
+    double r = 1e300;
+    for (int k = 0; k < nz; ++k) {
+        double ak = 0, ck = 0;
+        if (k > 0) ak = -dt * km * (0.5 * (kl[k - 1] + kl[k])) / (dz[k] * 0.5 * (dz[k - 1] + dz[k]));
+        if (k < nz - 1) ck = -dt * km * (0.5 * (kl[k] + kl[k + 1])) / (dz[k] * 0.5 * (dz[k] + dz[k + 1]));
+        const double off = fabs(ak) + fabs(ck);
+        if (off > 0) r = fmin(r, fabs(1.0 - ak - ck) / off);
+    }
+    return r;
+}
+
+// One thread per column: 1 = FP64 solve (dominance ratio below the
+// threshold), 2 = FP32 side solve (other kappa_mult != 1), 0 = neither.
+__global__ void flag_class_kernel(const double *lev, const double *km, long ncol, int nz, double dt, double thr,
+                                  unsigned char *cls) {
+    const long col = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncol) return;
+    const double s = km[col];
+    cls[col] = column_ratio(lev, nz, dt, s) < thr ? 1 : (s != 1.0 ? 2 : 0);
+}
+
+// One thread per row: how many columns of each class row j holds.
+__global__ void flag_count_kernel(const unsigned char *cls, int nx, int ny, int *count64, int *count32) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ny) return;
+    int n64 = 0, n32 = 0;
+    for (int i = 0; i < nx; ++i) {
+        const unsigned char c = cls[(size_t)j * nx + i];
+        n64 += c == 1;
+        n32 += c == 2;
+    }
+    count64[j] = n64;
+    count32[j] = n32;
+}
+
+// One thread per row: the row's listed columns in raster order from its
+// offsets (FP64 columns first in the list, then the FP32 ones), -1 for the
+// columns the step kernel finishes itself.
+__global__ void flag_fill_kernel(const unsigned char *cls, const int *off64, const int *off32, int nx, int ny,
+                                 int *list, int *idx) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ny) return;
+    int f64 = off64[j], f32 = off32[j];
+    for (int i = 0; i < nx; ++i) {
+        const size_t col = (size_t)j * nx + i;
+        const unsigned char c = cls[col];
+        const int f = c == 1 ? f64++ : (c == 2 ? f32++ : -1);
+        if (f >= 0) list[f] = (int)col;
+        idx[col] = f;
+    }
+}
+
+// One thread per listed column: the top-down elimination factors in FP64,
+// m_k = b_k - c_k e_{k+1}, stored as (1/m_k, c_k/m_k) in fac[k][f], and
+// e_k = a_k/m_k in fe[k][f] (level-major, so warps read them coalesced).
+__global__ void flag_factor_kernel(const double *lev, const double *km, const int *list, long nflag, int nz,
+                                   double dt, double2 *fac, float *fe) {
+    const long f = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nflag) return;
+    const double *dz = lev, *kl = lev + nz;
+    const double s = km[list[f]];
+    double e_up = 0.0;
+    for (int k = nz - 1; k >= 0; --k) {
+        double ak = 0, ck = 0;
+        if (k > 0) ak = -dt * s * (0.5 * (kl[k - 1] + kl[k])) / (dz[k] * 0.5 * (dz[k - 1] + dz[k]));
+        if (k < nz - 1) ck = -dt * s * (0.5 * (kl[k] + kl[k + 1])) / (dz[k] * 0.5 * (dz[k] + dz[k + 1]));
+        const double inv = 1.0 / ((1.0 - ak - ck) - ck * e_up);
+        const double e = ak * inv;
+        fac[(size_t)k * nflag + f] = make_double2(inv, ck * inv);
+        fe[(size_t)k * nflag + f] = (float)e;
+        e_up = e;
+    }
+}
+
+// One thread per listed column (warps of listed work only): the elimination
+// from the top of the T* the step kernel parked -- in FP64 for the first
+// n64 columns (dominance ratio below the threshold), in FP32 for the rest --
+// then the FP32 back substitution plus the parked heating.  The column's T
+// (and its ghost copies) in the new state is overwritten; with sums, the
+// FP64 energy change of the column is recorded for the finalize kernel.
+__global__ void __launch_bounds__(128) mixed_fixup_kernel(const int *__restrict__ list, long nflag, long n64,
+                                                          const double2 *__restrict__ fac,
+                                                          const float *__restrict__ fe, float *__restrict__ side,
+                                                          const Q4<float> *__restrict__ dz2, float *__restrict__ out,
+                                                          double *__restrict__ corr, int nx, int ny, int nz, int P,
+                                                          int R) {
+    const long f = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nflag) return;
+    const int col = list[f], i = col % nx, j = col / nx;
+    float *r = side + f;  // r[2k*nflag]: T*_k, overwritten by f_k; r[(2k+1)*nflag]: dt*H_k
+    const size_t st = 2 * (size_t)nflag;
+    if (f < n64) {  // weakly dominant: elimination in FP64
+        double fu = 0.0;
+        for (int k = nz - 1; k >= 0; --k) {
+            const double2 c2 = fac[(size_t)k * nflag + f];
+            fu = fma(-c2.y, fu, c2.x * (double)r[k * st]);  // (T*_k - c_k f_{k+1}) / m_k
+            r[k * st] = (float)fu;
+        }
+    } else {  // other kappa_mult != 1 columns: FP32
+        float fu = 0.f;
+        for (int k = nz - 1; k >= 0; --k) {
+            const double2 c2 = fac[(size_t)k * nflag + f];
+            fu = fmaf(-(float)c2.y, fu, (float)c2.x * r[k * st]);
+            r[k * st] = fu;
+        }
+    }
+    const size_t lev = (size_t)2 * R * P;
+    const int ip = i + kGhostX, jp = j + 1;
+    float x = 0.f;
+    float sE = 0.f, cE = 0.f;  // compensated sum of (T_new - T_old) dz
+    for (int k = 0; k < nz; ++k) {
+        x = fmaf(-fe[(size_t)k * nflag + f], x, r[k * st]);
+        const float tn = x + r[k * st + nflag];
+        float *row = out + k * lev + (size_t)jp * P;
+        if (corr) {
+            // tn and the old value are close, so their FP32 difference is
+            // exact; the product with dz (hi + lo) and the sum are
+            // compensated (exact product error, TwoSum)
+            const float d = tn - row[ip];
+            const float dzh = dz2[k].z, dzl = dz2[k].w;  // dz as hi + lo floats
+            const float p = d * dzh, pe = fmaf(d, dzh, -p) + d * dzl;
+            const float s1 = sE + p, bp = s1 - sE;
+            cE += ((sE - (s1 - bp)) + (p - bp)) + pe;
+            sE = s1;
+        }
+        row[ip] = tn;
+        if (i == 0) row[kGhostX + nx] = tn;
+        if (i == nx - 1) row[kGhostX - 1] = tn;
+        if (j == 0) out[k * lev + (size_t)(ny + 1) * P + ip] = tn;
+        if (j == ny - 1) out[k * lev + ip] = tn;
+    }
+    if (corr) corr[f] = (double)sE + (double)cE;
 }
 
 // Per-level table from FP64 dz, kappa_lev, alpha.  One thread: the
@@ -550,7 +729,8 @@ __global__ void tables_kernel(const double *lev, int nz, double dt, double kappa
         tab[REC_C * nz + k] = Q4<T>{(T)wH, (T)wH, (T)(-ch), (T)(-ch)};
         tab[REC_D * nz + k] = Q4<T>{(T)(1.0 / m), (T)(1.0 / m), (T)e, (T)e};
         tab[REC_E * nz + k] = Q4<T>{(T)ah, (T)ch, (T)dz[k], (T)0};
-        tab[REC_F * nz + k] = Q4<T>{(T)(-e), (T)(-e), (T)dz[k], (T)dz[k]};
+        const T dz_hi = (T)dz[k];
+        tab[REC_F * nz + k] = Q4<T>{(T)(-e), (T)(-e), dz_hi, (T)(dz[k] - (double)dz_hi)};
     }
 }
 
@@ -729,7 +909,10 @@ int launch_columns(wx_ctx *c, const void *Ts, const void *qs, const void *km, vo
 }
 
 
-static bool per_col(const wx_ctx *c) { return c->kmult != nullptr; }
+// WX_MIXED routes every column with kappa_mult != 1 through the side list,
+// so its step kernel keeps the kappa_mult = 1 table path (KMODE 2).
+static bool mixed(const wx_ctx *c) { return c->dtype == WX_MIXED && c->n_list > 0; }
+static bool per_col(const wx_ctx *c) { return c->kmult != nullptr && c->dtype != WX_MIXED; }
 
 bool cfg_fits(const wx_ctx *c, const StepCfg &cfg, int *smem_bytes) {
     const SmemPlan p = plan_smem(c->nz, cfg.ty, cfg.stages, cfg.kb, c->t_bytes, per_col(c));
@@ -795,6 +978,9 @@ static int launch_step_t(wx_ctx *c, cudaStream_t s, const CUtensorMap &tm, void 
     a.dth = (T)(c->dt / c->h);
     a.dh = (T)(c->dt * c->kappa_h / (c->h * c->h));
     a.advection = (c->flags & WX_ADVECTION) ? 1 : 0;
+    a.flag_idx = c->flag_idx;
+    a.side = c->flag_side;
+    a.n_list = c->n_list;
     const long ntiles = (long)((c->nx + kTileX - 1) / kTileX) * ((c->ny + TY - 1) / TY);
     const long resident = (long)c->num_sms * c->cfg.ctas_per_sm;
     dim3 grid((unsigned)std::max(1L, std::min(ntiles, resident)));
@@ -830,7 +1016,10 @@ static int dispatch_flags(wx_ctx *c, cudaStream_t s, const CUtensorMap &tm, void
 
 template <typename T>
 static int dispatch_kmode(wx_ctx *c, cudaStream_t s, const CUtensorMap &tm, void *out) {
-    return per_col(c) ? dispatch_flags<T, 1>(c, s, tm, out) : dispatch_flags<T, 0>(c, s, tm, out);
+    if constexpr (std::is_same<T, float>::value)
+        if (mixed(c)) return dispatch_flags<T, 2>(c, s, tm, out);
+    if (!per_col(c)) return dispatch_flags<T, 0>(c, s, tm, out);
+    return dispatch_flags<T, 1>(c, s, tm, out);
 }
 
 int launch_step(wx_ctx *c, cudaStream_t s, long *launches) {
@@ -839,15 +1028,86 @@ int launch_step(wx_ctx *c, cudaStream_t s, long *launches) {
                                : dispatch_kmode<double>(c, s, c->tmap[src], c->fld[dst]);
     if (rc != WX_OK) return rc;
     ++*launches;
-    if (c->flags & WX_SUMS) {
+    const bool sums = c->flags & WX_SUMS;
+    if (mixed(c) && (c->flags & WX_PHYSICS)) {
+        const int nt = 128;
+        mixed_fixup_kernel<<<(unsigned)((c->n_list + nt - 1) / nt), nt, 0, s>>>(
+            c->flag_list, c->n_list, c->n_flag, (const double2 *)c->flag_fac, c->flag_e, c->flag_side,
+            (const Q4<float> *)c->tab + REC_F * c->nz, (float *)c->fld[dst],
+            sums ? c->flag_corr : nullptr, c->nx, c->ny, c->nz, c->P, c->R);
+        WX_CK(cudaGetLastError(), "mixed fixup kernel");
+        ++*launches;
+    }
+    if (sums) {
         const long ntiles = (long)((c->nx + kTileX - 1) / kTileX) * ((c->ny + c->cfg.ty - 1) / c->cfg.ty);
         double *dst_sum = c->sums_ring + 2 * (c->sums_count % c->sums_cap);
-        sums_finalize<<<1, 1024, 0, s>>>(c->partials, ntiles, c->h * c->h, dst_sum);
+        const long ncorr = (mixed(c) && (c->flags & WX_PHYSICS)) ? c->n_list : 0;
+        sums_finalize<<<kFinBlocks, 256, 0, s>>>(c->partials, ntiles, c->flag_corr, ncorr, c->h * c->h,
+                                                 c->fin_park, c->fin_ticket, dst_sum);
         WX_CK(cudaGetLastError(), "sums kernel");
         ++*launches;
         ++c->sums_count;
     }
     c->cur = dst;
+    return WX_OK;
+}
+
+// WX_MIXED set-up: flag the columns whose dominance ratio is below the
+// threshold (deterministic raster order) and precompute their FP64 factors.
+// km64 is the FP64 kappa_mult on the device.
+int setup_mixed(wx_ctx *c, const double *km64) {
+    for (void **p : {(void **)&c->flag_list, (void **)&c->flag_idx, (void **)&c->flag_fac, (void **)&c->flag_e,
+                     (void **)&c->flag_side, (void **)&c->flag_corr})
+        if (*p) {
+            cudaFree(*p);
+            *p = nullptr;
+        }
+    c->n_flag = c->n_list = 0;
+    if (c->dtype != WX_MIXED || !km64) return WX_OK;
+    const int ny = c->ny, nx = c->nx, nz = c->nz;
+    const size_t ncol = (size_t)nx * ny;
+    int *d_cnt = nullptr;  // [4][ny]: count64, count32, off64, off32; then the classes
+    WX_CK(cudaMalloc(&d_cnt, 4 * (size_t)ny * sizeof(int) + ncol), "alloc flag counts");
+    unsigned char *cls = reinterpret_cast<unsigned char *>(d_cnt + 4 * (size_t)ny);
+    flag_class_kernel<<<(unsigned)((ncol + 255) / 256), 256>>>(c->d_lev, km64, (long)ncol, nz, c->dt,
+                                                               c->dd_threshold, cls);
+    flag_count_kernel<<<(ny + 127) / 128, 128>>>(cls, nx, ny, d_cnt, d_cnt + ny);
+    std::vector<int> cnt(2 * (size_t)ny), off(2 * (size_t)ny);
+    cudaError_t e = cudaMemcpy(cnt.data(), d_cnt, 2 * ny * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        cudaFree(d_cnt);
+        return cuda_fail(c, e, "flag counts");
+    }
+    long n64 = 0, n32 = 0;
+    for (int j = 0; j < ny; ++j) n64 += cnt[j];
+    long a64 = 0, a32 = n64;
+    for (int j = 0; j < ny; ++j) {
+        off[j] = (int)a64;
+        a64 += cnt[j];
+        off[ny + j] = (int)a32;
+        a32 += cnt[ny + j];
+        n32 += cnt[ny + j];
+    }
+    const long n = n64 + n32;
+    c->n_flag = n64;
+    c->n_list = n;
+    WX_CK(cudaMalloc(&c->flag_idx, (size_t)nx * ny * sizeof(int)), "alloc flag index");
+    if (n > 0) {
+        WX_CK(cudaMalloc(&c->flag_list, n * sizeof(int)), "alloc flag list");
+        WX_CK(cudaMalloc(&c->flag_fac, (size_t)n * nz * 2 * sizeof(double)), "alloc flag factors");
+        WX_CK(cudaMalloc(&c->flag_e, (size_t)n * nz * sizeof(float)), "alloc flag e");
+        WX_CK(cudaMalloc(&c->flag_side, (size_t)n * 2 * nz * sizeof(float)), "alloc flag side buffer");
+        WX_CK(cudaMalloc(&c->flag_corr, (size_t)n * sizeof(double)), "alloc flag corrections");
+    }
+    WX_CK(cudaMemcpy(d_cnt + 2 * ny, off.data(), 2 * ny * sizeof(int), cudaMemcpyHostToDevice), "flag offsets");
+    flag_fill_kernel<<<(ny + 127) / 128, 128>>>(cls, d_cnt + 2 * ny, d_cnt + 3 * ny, nx, ny, c->flag_list,
+                                                c->flag_idx);
+    if (n > 0)
+        flag_factor_kernel<<<(unsigned)((n + 127) / 128), 128>>>(c->d_lev, km64, c->flag_list, n, nz, c->dt,
+                                                                  (double2 *)c->flag_fac, c->flag_e);
+    e = cudaDeviceSynchronize();
+    cudaFree(d_cnt);
+    if (e != cudaSuccess) return cuda_fail(c, e, "mixed-precision set-up");
     return WX_OK;
 }
 

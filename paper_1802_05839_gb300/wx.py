@@ -57,6 +57,7 @@ SIGNATURES = [
                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long)]),
     ("wx_last_launches", ctypes.c_long, [_VP]),
+    ("wx_flagged_columns", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_long)]),
     ("wx_set_step_config", ctypes.c_int, [_VP] + [ctypes.c_int] * 5),
     ("wx_get_step_config", ctypes.c_int, [_VP] + [ctypes.POINTER(ctypes.c_int)] * 6),
     ("wx_sums_noalloc", ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -196,6 +197,11 @@ class Context:
         v = [ctypes.c_int() for _ in range(6)]
         _check(lib().wx_get_step_config(self.ptr, *[ctypes.byref(x) for x in v]), self.ptr)
         return dict(zip(("ty", "kb", "stages", "ctas_per_sm", "prefetch", "smem_bytes"), (x.value for x in v)))
+
+    def flagged_columns(self):
+        n = ctypes.c_long()
+        _check(lib().wx_flagged_columns(self.ptr, ctypes.byref(n)), self.ptr)
+        return n.value
 
     def last_launches(self):
         return int(lib().wx_last_launches(self.ptr))

@@ -1,0 +1,84 @@
+"""WX_MIXED: FP32 fields and stencil, FP64 conservation sums, and the FP64
+Thomas elimination for columns whose diagonal dominance ratio
+min_k |b_k|/(|a_k|+|c_k|) is below 1.1.  Errors are stated against the FP64
+oracle run on the same FP32-rounded inputs."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1802_05839_gb300 import inputs, wx
+
+pytestmark = pytest.mark.gpu
+
+
+def maxrel(g, o):
+    return float(np.max(np.abs(g - o)) / np.max(np.abs(o)))
+
+
+def dominance_ratio(case, km):
+    a, b, c = oracle.vdiff_coeffs(case.nz, case.dt, case.dz, case.kappa_lev, km)
+    off = np.abs(a) + np.abs(c)
+    return np.min(np.abs(b)[off > 0] / off[off > 0])
+
+
+def run(case, dtype, n, sums=False):
+    ctx = wx.Context(case.nx, case.ny, case.nz, dtype)
+    flags = wx.WX_ADVECTION | wx.WX_PHYSICS | (wx.WX_SUMS if sums else 0)
+    ctx.set_params(case, flags=flags)
+    ctx.load_fields(case.T, case.q, case.U, case.V)
+    nflag = ctx.flagged_columns()
+    ctx.step(n)
+    ctx.sync()
+    T, q = ctx.read_fields()
+    m, e = ctx.sums() if sums else (None, None)
+    ctx.close()
+    return T, q, nflag, m, e
+
+
+def test_flagged_columns_are_the_weakly_dominant_ones():
+    case = inputs.round_to_f32(inputs.paper_grid_case(97, 61, 58, seed=3, near_singular=True))
+    km = case.kappa_mult.reshape(-1)
+    expect = int(np.sum([dominance_ratio(case, s) < 1.1 for s in km]))
+    ctx = wx.Context(case.nx, case.ny, case.nz, "mixed")
+    ctx.set_params(case)
+    assert ctx.flagged_columns() == expect
+    frac = expect / km.size
+    assert 0.03 < frac < 0.07  # about 5% of columns, as the input recipe seeds
+    ctx.close()
+
+
+@pytest.mark.parametrize("shape", [(97, 61, 58), (70, 33, 17), (1, 5, 9)])
+def test_mixed_matches_oracle(shape):
+    nx, ny, nz = shape
+    case = inputs.round_to_f32(inputs.paper_grid_case(nx, ny, nz, seed=5, near_singular=True))
+    Tg, qg, nflag, _, _ = run(case, "mixed", 5)
+    To, qo = oracle.run(case, 5, case.T, case.q, case.U, case.V)
+    assert maxrel(Tg, To) <= 3e-5 and maxrel(qg, qo) <= 3e-5
+
+
+def test_mixed_improves_flagged_columns_over_fp32():
+    """On the near-singular columns the FP64 elimination is at least as close
+    to the FP64 oracle as the all-FP32 path (stated per field)."""
+    case = inputs.round_to_f32(inputs.paper_grid_case(128, 96, 58, seed=8, near_singular=True))
+    To, qo = oracle.run(case, 10, case.T, case.q, case.U, case.V)
+    Tm, qm, nflag, _, _ = run(case, "mixed", 10)
+    Tf, qf, _, _, _ = run(case, "f32", 10)
+    mask = (case.kappa_mult > 1)[None]
+    err_m = np.max(np.abs(Tm - To)[np.broadcast_to(mask, To.shape)])
+    err_f = np.max(np.abs(Tf - To)[np.broadcast_to(mask, To.shape)])
+    print(f"flagged {nflag}: max |T err| mixed {err_m:.3e} K, fp32 {err_f:.3e} K")
+    assert nflag > 0
+    assert err_m <= err_f * 1.05 + 1e-6
+    assert maxrel(qm, qo) <= 1e-4
+
+
+def test_mixed_sums_each_step():
+    case = inputs.round_to_f32(inputs.paper_grid_case(90, 70, 30, seed=2, near_singular=True))
+    Tg, qg, nflag, m, e = run(case, "mixed", 6, sums=True)
+    _, _, mo, eo = oracle.run(case, 6, case.T, case.q, case.U, case.V, sums=True)
+    assert len(m) == 6
+    assert np.max(np.abs(m - mo) / np.abs(mo)) <= 1e-5
+    assert np.max(np.abs(e - eo) / np.abs(eo)) <= 1e-5
+    w = case.h ** 2 * case.dz[:, None, None]
+    assert abs(e[-1] - np.sum(Tg * w)) / abs(e[-1]) < 1e-12
+    assert abs(m[-1] - np.sum(qg * w)) / abs(m[-1]) < 1e-12
