@@ -187,6 +187,57 @@ int wx_sums_noalloc(const void *T, const void *q, int dtype, int nx, int ny,
 /* Message of the last failing wx_sums_noalloc call on this host thread. */
 const char *wx_sums_noalloc_error(void);
 
+/* Autotune the step kernel's launch configuration for this context (grid,
+ * dtype, options): candidate tile rows x planes per TMA box x ring slots x
+ * CTAs per SM are each timed with CUDA events over a few steps on the
+ * caller's stream, on a copy of the state that is restored afterwards, and
+ * the fastest is applied.  cache_path (or NULL) names a text file that keeps
+ * the winner per (GPU, dtype, options, grid); with force = 0 a cached entry
+ * is applied without timing.  *best_ms (optional) gets its time per step.
+ * Synchronous. */
+int wx_tune(wx_ctx *c, const char *cache_path, int force, void *cuda_stream,
+            double *best_ms);
+
+/* ---------------------------------------------------------- ensembles
+ * A batch of up to 16 member grids of uneven sizes (the same dtype and
+ * options), stepped together: each step is ONE persistent launch of the
+ * step kernel over the combined (member, tile) work list, followed by the
+ * members' sums kernels when enabled.  Members are ordinary contexts owned
+ * by the ensemble: set their parameters, load and read their fields with
+ * the wx_* calls on wx_ens_member(e, i).  (The paper's ensemble context is
+ * its many-GPU strong-scaling runs, Sec. 5.5; this batches independent
+ * grids on one GPU.) */
+typedef struct wx_ens wx_ens;
+
+/* m in 1..16 members of sizes nx[i] x ny[i] x nz[i]; dtype WX_F32 or
+ * WX_F64. */
+int wx_ens_create(int m, const int *nx, const int *ny, const int *nz,
+                  int dtype, wx_ens **out);
+int wx_ens_size(const wx_ens *e);
+/* Member i (owned by the ensemble; do not destroy it), NULL if out of range. */
+wx_ctx *wx_ens_member(wx_ens *e, int i);
+/* Advance every member n_steps >= 0 steps on the caller's stream.  With
+ * use_graph = 1 the n_steps launches are captured once into a CUDA graph
+ * (cached per step count, buffer parity, member state generation and
+ * configuration) and replayed with one graph launch.  Members must share
+ * their option flags and kappa_mult use (WX_EINVAL otherwise). */
+int wx_ens_step(wx_ens *e, int n_steps, int use_graph, void *cuda_stream);
+/* Wait for the last stream; WX_ETIMEOUT / WX_ENONFINITE as wx_sync. */
+int wx_ens_sync(wx_ens *e);
+/* One launch configuration for all members (see wx_set_step_config); it
+ * must fit the member with the deepest columns. */
+int wx_ens_set_step_config(wx_ens *e, int ty, int kb, int stages,
+                           int ctas_per_sm, int prefetch);
+int wx_ens_get_step_config(const wx_ens *e, int *ty, int *kb, int *stages,
+                           int *ctas_per_sm, int *prefetch);
+/* wx_tune for the whole batch (one configuration for the batched launch). */
+int wx_ens_tune(wx_ens *e, const char *cache_path, int force,
+                void *cuda_stream, double *best_ms);
+/* Kernel launches the last wx_ens_step issued (per replay for graphs). */
+long wx_ens_last_launches(const wx_ens *e);
+void wx_ens_destroy(wx_ens *e);          /* NULL-safe; frees the members */
+const char *wx_ens_last_error(const wx_ens *e);
+
 /* Free the context and its device memory.  NULL-safe. */
 void wx_destroy(wx_ctx *c);
 

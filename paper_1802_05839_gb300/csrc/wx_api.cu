@@ -74,12 +74,15 @@ int encode_tmap(wx_ctx *c, int which, int ty, int kb) {
 }
 }  // namespace wx
 
-static int apply_cfg(wx_ctx *c, const StepCfg &g) {
+namespace wx {
+int apply_cfg(wx_ctx *c, const StepCfg &g) {
     c->cfg = g;
+    ++c->generation;
     RC(encode_tmap(c, 0, g.ty, g.kb));
     RC(encode_tmap(c, 1, g.ty, g.kb));
     return WX_OK;
 }
+}  // namespace wx
 
 // ------------------------------------------------------------ life cycle
 extern "C" int wx_create(int nx, int ny, int nz, int dtype, wx_ctx **out) {
@@ -130,7 +133,8 @@ extern "C" int wx_create(int nx, int ny, int nz, int dtype, wx_ctx **out) {
                   {(void **)&c->partials, 2 * nblk_max * sizeof(double)},
                   {(void **)&c->sums_ring, 2 * (size_t)c->sums_cap * sizeof(double)},
                   {(void **)&c->fin_park, 2 * 64 * sizeof(double)},
-                  {(void **)&c->fin_ticket, sizeof(unsigned)}};
+                  {(void **)&c->fin_ticket, sizeof(unsigned)},
+                  {(void **)&c->d_sums_count, sizeof(long long)}};
     for (auto &a : allocs) {
         cudaError_t e = cudaMalloc(a.p, a.n);
         if (e != cudaSuccess) {
@@ -143,6 +147,7 @@ extern "C" int wx_create(int nx, int ny, int nz, int dtype, wx_ctx **out) {
     if (cudaMemset(c->fld[0], 0, fbytes) != cudaSuccess || cudaMemset(c->fld[1], 0, fbytes) != cudaSuccess ||
         cudaMemset(c->d_status, 0, sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(c->fin_ticket, 0, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(c->d_sums_count, 0, sizeof(long long)) != cudaSuccess ||
         cudaMemset(c->U, 0, cols * c->t_bytes) != cudaSuccess ||
         cudaMemset(c->V, 0, cols * c->t_bytes) != cudaSuccess) {
         c->err = "wx_create: cudaMemset failed";
@@ -159,7 +164,7 @@ extern "C" void wx_destroy(wx_ctx *c) {
     void *ptrs[] = {c->fld[0], c->fld[1], c->U,        c->V,         c->kmult,     c->tab,
                     c->d_lev,  c->staging, c->d_status, c->partials, c->sums_ring, c->flag_list,
                     c->flag_idx, c->flag_fac, c->flag_e, c->flag_side, c->flag_corr,
-                    c->fin_park, c->fin_ticket};
+                    c->fin_park, c->fin_ticket, c->d_sums_count};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete c;
@@ -287,6 +292,7 @@ extern "C" int wx_set_params(wx_ctx *c, const wx_params *p) {
     CK(cudaDeviceSynchronize(), "wx_set_params");
     // the kernel variant (and its shared-memory plan) depends on kappa_mult
     if (!c->cfg_forced || !cfg_fits(c, c->cfg, nullptr)) RC(apply_cfg(c, default_cfg(c)));
+    ++c->generation;
     c->params_set = true;
     c->cfl_ok = false;
     return WX_OK;
@@ -296,7 +302,7 @@ extern "C" int wx_set_params(wx_ctx *c, const wx_params *p) {
 // combination of old values must be >= 0 (this is what keeps the first-order
 // upwind + diffusion scheme monotone).  Checked on the host from the FP64
 // parameters and winds.
-static int check_cfl(wx_ctx *c) {
+int wx::check_cfl(wx_ctx *c) {
     if (c->cfl_ok) return WX_OK;
     const int nx = c->nx, ny = c->ny, nz = c->nz;
     const double dh = c->dt * c->kappa_h / (c->h * c->h), dth = c->dt / c->h;
@@ -380,8 +386,9 @@ extern "C" int wx_load_fields(wx_ctx *c, const double *T, const double *q, const
     }
     RC(launch_convert(c, dU, c->U, cols, 0));
     RC(launch_convert(c, dV, c->V, cols, 0));
+    CK(cudaMemset(c->d_sums_count, 0, sizeof(long long)), "reset sums count");
     CK(cudaDeviceSynchronize(), "wx_load_fields");
-    c->sums_count = 0;
+    ++c->generation;
     c->fields_loaded = true;
     c->cfl_ok = false;
     return WX_OK;
@@ -436,15 +443,17 @@ extern "C" int wx_get_sums(wx_ctx *c, double *mass_q, double *energy_T, int max_
     if (!c) return WX_EINVAL;
     if (max_steps < 0) return fail(c, WX_EINVAL, "wx_get_sums: max_steps < 0");
     CK(cudaDeviceSynchronize(), "wx_get_sums");
-    const long avail = std::min<long>(c->sums_count, c->sums_cap);
+    long long count = 0;
+    CK(cudaMemcpy(&count, c->d_sums_count, sizeof count, cudaMemcpyDeviceToHost), "read sums count");
+    const long avail = (long)std::min<long long>(count, c->sums_cap);
     const long n = std::min<long>(avail, max_steps);
     std::vector<double> ring(2 * (size_t)c->sums_cap);
     if (n > 0)
         CK(cudaMemcpy(ring.data(), c->sums_ring, ring.size() * sizeof(double), cudaMemcpyDeviceToHost),
            "download sums");
     for (long e = 0; e < n; ++e) {
-        const long step = c->sums_count - n + e;
-        const long slot = step % c->sums_cap;
+        const long long step = count - n + e;
+        const long slot = (long)(step % c->sums_cap);
         if (mass_q) mass_q[e] = ring[2 * slot];
         if (energy_T) energy_T[e] = ring[2 * slot + 1];
     }

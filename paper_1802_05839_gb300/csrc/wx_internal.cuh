@@ -65,6 +65,24 @@ template <typename T> struct StepArgs {
     long n_list;
 };
 
+// One member of a (possibly single-member) batch stepped by one launch:
+// its input-state descriptor, its arguments and the first index of its tiles
+// in the combined (member, tile) work list.
+constexpr int kMaxMembers = 16;
+template <typename T> struct alignas(64) Member {
+    CUtensorMap tin;
+    StepArgs<T> a;
+    long tile0;
+    int gx, gy;
+};
+template <typename T> struct Members {
+    Member<T> m[kMaxMembers];
+    int n;
+    int nz_max;
+    long total;          // work items (tiles of all members)
+    unsigned *status;
+};
+
 // A step-kernel configuration: rows per tile, TMA ring stages (2 planes
 // each), resident CTAs per SM and L2 prefetch distance in stages.  Chosen by
 // a heuristic at create time or set by the autotuner.
@@ -120,7 +138,7 @@ struct wx_ctx {
     double *fin_park = nullptr;     // [64][2] per-block results of the sums reduction
     unsigned *fin_ticket = nullptr; // arrival counter of the sums reduction (self-resetting)
     int sums_cap = 4096;
-    long sums_count = 0;
+    long long *d_sums_count = nullptr;  // steps recorded since the last load (device)
 
     // parameters (host copies)
     double dt = 0, h = 0, kappa_h = 0, S0 = 0, q_ref = 0, dd_threshold = 1.1;
@@ -142,6 +160,7 @@ struct wx_ctx {
     bool cfg_forced = false;
     cudaStream_t last_stream = nullptr;
     long last_launches = 0;
+    unsigned generation = 0;     // bumped by every change a captured graph would bake in
     std::string err;
 };
 
@@ -153,11 +172,15 @@ int launch_pack(wx_ctx *c, const double *T, const double *q, void *dst, cudaStre
 int launch_unpack(wx_ctx *c, const void *src, double *T, double *q, cudaStream_t s);
 int launch_convert(wx_ctx *c, const double *src, void *dst, size_t n, cudaStream_t s);
 int launch_step(wx_ctx *c, cudaStream_t s, long *launches);
+int launch_batch(wx_ctx *const *members, int n, const StepCfg &cfg, unsigned *status, cudaStream_t s,
+                 long *launches, std::string &err);
 int launch_columns(wx_ctx *c, const void *Ts, const void *qs, const void *km, void *Tout, void *tend,
                    long ncol, cudaStream_t s);
 StepCfg default_cfg(const wx_ctx *c);
 int setup_mixed(wx_ctx *c, const double *km64);
 bool cfg_fits(const wx_ctx *c, const StepCfg &cfg, int *smem_bytes);
 int encode_tmap(wx_ctx *c, int which, int ty, int kb);
+int apply_cfg(wx_ctx *c, const StepCfg &g);
+int check_cfl(wx_ctx *c);
 
 }  // namespace wx

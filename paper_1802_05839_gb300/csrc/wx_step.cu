@@ -122,8 +122,8 @@ __device__ __forceinline__ void consumer_sync(int nthreads) {
 // elimination coefficients come from the table); KMODE 1: per-column
 // kappa_mult, eliminated on the fly.
 template <typename T, int TY, int KB, int KMODE, bool PHYS, bool SUMS>
-__global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_constant__ CUtensorMap tin,
-                                                             const StepArgs<T> a, const int S, const int PF) {
+__global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_constant__ Members<T> ms, const int S,
+                                                             const int PF) {
     using PK = Pk<T>;
     using V = typename PK::V;
     using R4 = Q4<T>;
@@ -132,18 +132,22 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
     extern __shared__ __align__(128) unsigned char smem[];
 
     const int tx = threadIdx.x, wy = threadIdx.y;
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const int gx = (nx + kTileX - 1) / kTileX, gy = (ny + TY - 1) / TY;
-    const int ntiles = gx * gy;
-    const int n_st = (nz + KB - 1) / KB;  // stages per tile
-    const SmemPlan pl = plan_smem(nz, TY, S, KB, (int)sizeof(T), KMODE == 1);  // e_k per column
+    const SmemPlan pl = plan_smem(ms.nz_max, TY, S, KB, (int)sizeof(T), KMODE == 1);  // e_k per column
     R4 *tab = reinterpret_cast<R4 *>(smem + pl.tab_off);
     T *ring = reinterpret_cast<T *>(smem + pl.ring_off);
     V *stF = reinterpret_cast<V *>(smem + pl.state_off);  // [nz][NT] F of the 2 columns
-    V *stE = stF + nz * NT;                                // [nz][NT] e   (KMODE 1)
+    V *stE = stF + ms.nz_max * NT;                         // [nz][NT] e   (KMODE 1)
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + pl.bar_off);
     uint64_t *empty = full + S;
     const int SC = pl.stage_bytes / (int)sizeof(T);
+    const long total = ms.total;
+
+    // work item w -> member index
+    auto member_of = [&](long w) -> int {
+        int mi = 0;
+        while (mi + 1 < ms.n && w >= ms.m[mi + 1].tile0) ++mi;
+        return mi;
+    };
 
     const int tid_all = tx + 32 * wy;
     if (tid_all == 0) {
@@ -153,50 +157,64 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
         }
         fence_mbar_init();
     }
-    for (int e = tid_all; e < kTabRec * nz; e += 32 * (TY + 1)) tab[e] = a.tab[e];
     __syncthreads();
 
-    // ---------------- producer warp: stage g of tile n covers planes
-    // z0 = nz - (s+1)*KB .. z0+KB-1 (s = g mod n_st), top of the column first
+    // ---------------- producer warp: stage g of a tile covers planes
+    // z0 = nz - (g+1)*KB .. z0+KB-1, top of the column first
     if (wy == TY) {
-        if (tx == 0 && (int)blockIdx.x < ntiles) {
-            prefetch_tmap(&tin);
-            const int my_tiles = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-            const long total = (long)my_tiles * n_st;
+        if (tx == 0 && (long)blockIdx.x < total) {
             const uint32_t tx_bytes = (uint32_t)(KB * 2 * PL * sizeof(T));
-            auto coords = [&](long g) -> int3 {
-                const int n = (int)(g / n_st), s = (int)(g - (long)n * n_st);
-                const int t = (int)blockIdx.x + n * (int)gridDim.x;
-                const int bx = t % gx, by = t / gx;
-                // x start is a multiple of 4 elements: 16-byte aligned in FP32 and FP64
-                return make_int3(kGhostX - kBoxX0 + bx * kTileX, by * TY, nz - (s + 1) * KB);
-            };
-            for (long g = 0; g < PF && g < total; ++g) {
-                const int3 c3 = coords(g);
-                tma_prefetch_l2_4d(&tin, c3.x, c3.y, 0, c3.z);
-            }
             int slot = 0, fill = 0;
             long issued = 0;
             bool ok = true;
-            for (long g = 0; g < total; ++g) {
-                if (g + PF < total) {
-                    const int3 c3 = coords(g + PF);
-                    tma_prefetch_l2_4d(&tin, c3.x, c3.y, 0, c3.z);
-                }
-                if (g >= S && !mbar_wait_bounded(&empty[slot], (uint32_t)((fill - 1) & 1))) {
-                    ok = false;
-                    break;
-                }
-                const int3 c3 = coords(g);
-                mbar_arrive_expect_tx(&full[slot], tx_bytes);
-                tma_load_4d(ring + slot * SC, &tin, &full[slot], c3.x, c3.y, 0, c3.z);
-                ++issued;
-                if (++slot == S) {
-                    slot = 0;
-                    ++fill;
+            // the stage sequence is (work item, stage) in order; PF stages ahead
+            // of the TMA loads, L2 bulk prefetches of the same boxes
+            long pw = blockIdx.x;
+            int pg = 0;
+            for (int ahead = 0; ahead < PF && pw < total; ++ahead) {
+                const int mi = member_of(pw);
+                const Member<T> &M = ms.m[mi];
+                const int t = (int)(pw - M.tile0), nst = (M.a.nz + KB - 1) / KB;
+                tma_prefetch_l2_4d(&M.tin, kGhostX - kBoxX0 + (t % M.gx) * kTileX, (t / M.gx) * TY, 0,
+                                   M.a.nz - (pg + 1) * KB);
+                if (++pg == nst) {
+                    pg = 0;
+                    pw += gridDim.x;
                 }
             }
-            if (!ok) atomicOr(a.status, ST_TIMEOUT);
+            for (long w = blockIdx.x; w < total && ok; w += gridDim.x) {
+                const int mi = member_of(w);
+                const Member<T> &M = ms.m[mi];
+                prefetch_tmap(&M.tin);
+                const int t = (int)(w - M.tile0), nz = M.a.nz, nst = (nz + KB - 1) / KB;
+                const int x0 = kGhostX - kBoxX0 + (t % M.gx) * kTileX;  // multiple of 4 elements
+                const int y0 = (t / M.gx) * TY;
+                for (int g = 0; g < nst; ++g) {
+                    if (PF > 0 && pw < total) {
+                        const int pmi = member_of(pw);
+                        const Member<T> &PM = ms.m[pmi];
+                        const int pt = (int)(pw - PM.tile0), pnst = (PM.a.nz + KB - 1) / KB;
+                        tma_prefetch_l2_4d(&PM.tin, kGhostX - kBoxX0 + (pt % PM.gx) * kTileX, (pt / PM.gx) * TY, 0,
+                                           PM.a.nz - (pg + 1) * KB);
+                        if (++pg == pnst) {
+                            pg = 0;
+                            pw += gridDim.x;
+                        }
+                    }
+                    if (issued >= S && !mbar_wait_bounded(&empty[slot], (uint32_t)((fill - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[slot], tx_bytes);
+                    tma_load_4d(ring + slot * SC, &M.tin, &full[slot], x0, y0, 0, nz - (g + 1) * KB);
+                    ++issued;
+                    if (++slot == S) {
+                        slot = 0;
+                        ++fill;
+                    }
+                }
+            }
+            if (!ok) atomicOr(ms.status, ST_TIMEOUT);
             // keep this thread until its last copy into every slot has landed
             for (int s = 0; s < S && s < issued; ++s)
                 (void)mbar_wait_bounded(&full[s], (uint32_t)(((issued - 1 - s) / S) & 1));
@@ -206,39 +224,54 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
 
     // ---------------- consumers: two adjacent columns per lane
     const int tid = tx + 32 * wy;
-    const R4 *tA = tab + REC_A * nz, *tB = tab + REC_B * nz, *tC = tab + REC_C * nz, *tD = tab + REC_D * nz,
-             *tE = tab + REC_E * nz, *tF = tab + REC_F * nz;
     const int ctr = (wy + 1) * kBoxX + kBoxX0 + 2 * tx;  // column pair in a staged plane (8-byte aligned)
-    const size_t lev = (size_t)2 * a.R * a.P;              // elements between levels
-    const size_t fld = (size_t)a.R * a.P;                  // T plane -> q plane
     const T zero = T(0);
     const V m1 = PK::dup(T(-1));
     int slot = 0;
     uint32_t par = 0;
     bool ok = true;
+    int cur_member = -1;
 
     // face winds of a tile's two columns (a, b): Ue, Uw, Vn, Vs each
     struct Winds {
         T v[8];
     };
-    auto load_winds = [&](int t) -> Winds {
-        Winds w;
-        const int bx = t % gx, by = t / gx;
-        const int i0 = bx * kTileX + 2 * tx, j = by * TY + wy;
+    auto load_winds = [&](long w) -> Winds {
+        Winds wd;
+        const Member<T> &M = ms.m[member_of(w)];
+        const int t = (int)(w - M.tile0);
+        const int nx = M.a.nx, ny = M.a.ny;
+        const int i0 = (t % M.gx) * kTileX + 2 * tx, j = (t / M.gx) * TY + wy;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-            const bool v = (i0 + c < nx) && (j < ny) && a.advection;
+            const bool v = (i0 + c < nx) && (j < ny) && M.a.advection;
             const int ic = v ? i0 + c : 0, jc = v ? j : 0;
-            w.v[4 * c + 0] = v ? a.U[(size_t)jc * nx + ic] : T(0);
-            w.v[4 * c + 1] = v ? a.U[(size_t)jc * nx + (ic == 0 ? nx - 1 : ic - 1)] : T(0);
-            w.v[4 * c + 2] = v ? a.V[(size_t)jc * nx + ic] : T(0);
-            w.v[4 * c + 3] = v ? a.V[(size_t)(jc == 0 ? ny - 1 : jc - 1) * nx + ic] : T(0);
+            wd.v[4 * c + 0] = v ? M.a.U[(size_t)jc * nx + ic] : T(0);
+            wd.v[4 * c + 1] = v ? M.a.U[(size_t)jc * nx + (ic == 0 ? nx - 1 : ic - 1)] : T(0);
+            wd.v[4 * c + 2] = v ? M.a.V[(size_t)jc * nx + ic] : T(0);
+            wd.v[4 * c + 3] = v ? M.a.V[(size_t)(jc == 0 ? ny - 1 : jc - 1) * nx + ic] : T(0);
         }
-        return w;
+        return wd;
     };
-    Winds wnext = load_winds(blockIdx.x < ntiles ? (int)blockIdx.x : 0);
+    Winds wnext = load_winds((long)blockIdx.x < total ? (long)blockIdx.x : 0);
 
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (long w = blockIdx.x; w < total; w += gridDim.x) {
+        const int mi = member_of(w);
+        const StepArgs<T> a = ms.m[mi].a;
+        const int nx = a.nx, ny = a.ny, nz = a.nz;
+        const int gx = ms.m[mi].gx, gy = ms.m[mi].gy;
+        const int n_st = (nz + KB - 1) / KB;
+        const size_t lev = (size_t)2 * a.R * a.P;  // elements between levels
+        const size_t fld = (size_t)a.R * a.P;      // T plane -> q plane
+        if (mi != cur_member) {  // stage the member's per-level table
+            consumer_sync(NT);
+            for (int e = tid; e < kTabRec * nz; e += NT) tab[e] = a.tab[e];
+            consumer_sync(NT);
+            cur_member = mi;
+        }
+        const R4 *tA = tab + REC_A * nz, *tB = tab + REC_B * nz, *tC = tab + REC_C * nz, *tD = tab + REC_D * nz,
+                 *tE = tab + REC_E * nz, *tF = tab + REC_F * nz;
+        const int t = (int)(w - ms.m[mi].tile0);
         const int bx = t % gx, by = t / gx;
         const int i0 = bx * kTileX + 2 * tx, j = by * TY + wy;
         const bool va = (i0 < nx) && (j < ny), vb = (i0 + 1 < nx) && (j < ny);
@@ -246,7 +279,7 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
 
         // per-column coefficients of the horizontal operator, paired (a, b)
         const Winds wc = wnext;
-        if (t + (int)gridDim.x < ntiles) wnext = load_winds(t + gridDim.x);  // in flight during the tile
+        if (w + (long)gridDim.x < total) wnext = load_winds(w + gridDim.x);  // in flight during the tile
         V cC, cE, cW, cN, cS, km;
         int fl[2];
         {
@@ -505,7 +538,7 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
             atomicOr(a.status, ST_NONFINITE);  // edge tiles tallied only their valid columns
         }
     }
-    if (!ok && tx == 0) atomicOr(a.status, ST_TIMEOUT);
+    if (!ok && tx == 0) atomicOr(ms.status, ST_TIMEOUT);
 }
 
 // Fixed-order FP64 reduction of the per-tile partials (and of the side
@@ -517,7 +550,8 @@ constexpr int kFinBlocks = 64;
 __global__ void __launch_bounds__(256) sums_finalize(const double *__restrict__ part, long nblk,
                                                      const double *__restrict__ corr, long ncorr, double h2,
                                                      double *__restrict__ park, unsigned *__restrict__ ticket,
-                                                     double *__restrict__ dst) {
+                                                     double *__restrict__ ring, long long *__restrict__ count,
+                                                     int cap) {
     __shared__ double sq[256], st[256];
     __shared__ bool last;
     const long per = (nblk + gridDim.x - 1) / gridDim.x, perc = (ncorr + gridDim.x - 1) / gridDim.x;
@@ -553,8 +587,13 @@ __global__ void __launch_bounds__(256) sums_finalize(const double *__restrict__ 
             Q += ((volatile double *)park)[2 * b];
             Tt += ((volatile double *)park)[2 * b + 1];
         }
+        // the ring slot comes from a device counter, so a captured graph
+        // replays into the next slots
+        const long long n = *count;
+        double *dst = ring + 2 * (n % cap);
         dst[0] = h2 * Q;
         dst[1] = h2 * Tt;
+        *count = n + 1;
         *ticket = 0u;  // ready for the next step
     }
 }
@@ -957,13 +996,14 @@ StepCfg default_cfg(const wx_ctx *c) {
     return best;
 }
 
-template <typename T, int TY, int KB, int KMODE, bool PHYS, bool SUMS>
-static int launch_step_t(wx_ctx *c, cudaStream_t s, const CUtensorMap &tm, void *out) {
-    auto kern = step_kernel<T, TY, KB, KMODE, PHYS, SUMS>;
-    const SmemPlan pl = plan_smem(c->nz, TY, c->cfg.stages, KB, c->t_bytes, KMODE == 1);
-    WX_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.total), "smem attr");
-    StepArgs<T> a;
-    a.out = reinterpret_cast<T *>(out);
+// ------------------------------------------------------------- batches
+// A batch = the members one launch steps (one context, or an ensemble's
+// members), with the launch configuration of its owner.
+template <typename T> static void fill_member(const wx_ctx *c, Member<T> &M, long tile0, int ty) {
+    const int src = c->cur, dst = 1 - c->cur;
+    M.tin = c->tmap[src];
+    StepArgs<T> &a = M.a;
+    a.out = reinterpret_cast<T *>(c->fld[dst]);
     a.U = (const T *)c->U;
     a.V = (const T *)c->V;
     a.kmult = (const T *)c->kmult;
@@ -981,75 +1021,131 @@ static int launch_step_t(wx_ctx *c, cudaStream_t s, const CUtensorMap &tm, void 
     a.flag_idx = c->flag_idx;
     a.side = c->flag_side;
     a.n_list = c->n_list;
-    const long ntiles = (long)((c->nx + kTileX - 1) / kTileX) * ((c->ny + TY - 1) / TY);
-    const long resident = (long)c->num_sms * c->cfg.ctas_per_sm;
-    dim3 grid((unsigned)std::max(1L, std::min(ntiles, resident)));
+    M.tile0 = tile0;
+    M.gx = (c->nx + kTileX - 1) / kTileX;
+    M.gy = (c->ny + ty - 1) / ty;
+}
+
+template <typename T, int TY, int KB, int KMODE, bool PHYS, bool SUMS>
+static int launch_batch_t(wx_ctx *const *mem, int n, const StepCfg &cfg, int num_sms, unsigned *status,
+                          cudaStream_t s, std::string &err) {
+    auto kern = step_kernel<T, TY, KB, KMODE, PHYS, SUMS>;
+    Members<T> ms;
+    long total = 0;
+    int nz_max = 1;
+    for (int i = 0; i < n; ++i) {
+        fill_member<T>(mem[i], ms.m[i], total, TY);
+        total += (long)ms.m[i].gx * ms.m[i].gy;
+        nz_max = std::max(nz_max, mem[i]->nz);
+    }
+    ms.n = n;
+    ms.nz_max = nz_max;
+    ms.total = total;
+    ms.status = status;
+    const SmemPlan pl = plan_smem(nz_max, TY, cfg.stages, KB, (int)sizeof(T), KMODE == 1);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.total);
+    if (e != cudaSuccess) {
+        err = std::string("smem attr: ") + cudaGetErrorString(e);
+        return WX_ECUDA;
+    }
+    const long resident = (long)num_sms * cfg.ctas_per_sm;
+    dim3 grid((unsigned)std::max(1L, std::min(total, resident)));
     dim3 block(32, TY + 1);
-    kern<<<grid, block, pl.total, s>>>(tm, a, c->cfg.stages, c->cfg.prefetch);
-    WX_CK(cudaGetLastError(), "step kernel");
+    kern<<<grid, block, pl.total, s>>>(ms, cfg.stages, cfg.prefetch);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        err = std::string("step kernel: ") + cudaGetErrorString(e);
+        return WX_ECUDA;
+    }
     return WX_OK;
 }
 
 template <typename T, int KMODE, bool PHYS, bool SUMS>
-static int dispatch_ty(wx_ctx *c, cudaStream_t s, const CUtensorMap &tm, void *out) {
-    const int key = c->cfg.ty * 10 + c->cfg.kb;
-    switch (key) {
-        case 12: return launch_step_t<T, 1, 2, KMODE, PHYS, SUMS>(c, s, tm, out);
-        case 22: return launch_step_t<T, 2, 2, KMODE, PHYS, SUMS>(c, s, tm, out);
-        case 42: return launch_step_t<T, 4, 2, KMODE, PHYS, SUMS>(c, s, tm, out);
-        case 82: return launch_step_t<T, 8, 2, KMODE, PHYS, SUMS>(c, s, tm, out);
-        case 24: return launch_step_t<T, 2, 4, KMODE, PHYS, SUMS>(c, s, tm, out);
-        case 44: return launch_step_t<T, 4, 4, KMODE, PHYS, SUMS>(c, s, tm, out);
-        case 84: return launch_step_t<T, 8, 4, KMODE, PHYS, SUMS>(c, s, tm, out);
-        default: c->err = "unsupported tile rows / planes per stage"; return WX_EUNSUPPORTED;
+static int dispatch_ty(wx_ctx *const *mem, int n, const StepCfg &cfg, int sms, unsigned *st, cudaStream_t s,
+                       std::string &err) {
+    switch (cfg.ty * 10 + cfg.kb) {
+        case 12: return launch_batch_t<T, 1, 2, KMODE, PHYS, SUMS>(mem, n, cfg, sms, st, s, err);
+        case 22: return launch_batch_t<T, 2, 2, KMODE, PHYS, SUMS>(mem, n, cfg, sms, st, s, err);
+        case 42: return launch_batch_t<T, 4, 2, KMODE, PHYS, SUMS>(mem, n, cfg, sms, st, s, err);
+        case 82: return launch_batch_t<T, 8, 2, KMODE, PHYS, SUMS>(mem, n, cfg, sms, st, s, err);
+        case 24: return launch_batch_t<T, 2, 4, KMODE, PHYS, SUMS>(mem, n, cfg, sms, st, s, err);
+        case 44: return launch_batch_t<T, 4, 4, KMODE, PHYS, SUMS>(mem, n, cfg, sms, st, s, err);
+        case 84: return launch_batch_t<T, 8, 4, KMODE, PHYS, SUMS>(mem, n, cfg, sms, st, s, err);
+        default: err = "unsupported tile rows / planes per stage"; return WX_EUNSUPPORTED;
     }
 }
 
 template <typename T, int KMODE>
-static int dispatch_flags(wx_ctx *c, cudaStream_t s, const CUtensorMap &tm, void *out) {
-    const bool phys = c->flags & WX_PHYSICS, sums = c->flags & WX_SUMS;
-    if (phys && sums) return dispatch_ty<T, KMODE, true, true>(c, s, tm, out);
-    if (phys) return dispatch_ty<T, KMODE, true, false>(c, s, tm, out);
-    if (sums) return dispatch_ty<T, KMODE, false, true>(c, s, tm, out);
-    return dispatch_ty<T, KMODE, false, false>(c, s, tm, out);
+static int dispatch_flags(wx_ctx *const *mem, int n, const StepCfg &cfg, int sms, unsigned *st, cudaStream_t s,
+                          std::string &err) {
+    const unsigned f = mem[0]->flags;
+    const bool phys = f & WX_PHYSICS, sums = f & WX_SUMS;
+    if (phys && sums) return dispatch_ty<T, KMODE, true, true>(mem, n, cfg, sms, st, s, err);
+    if (phys) return dispatch_ty<T, KMODE, true, false>(mem, n, cfg, sms, st, s, err);
+    if (sums) return dispatch_ty<T, KMODE, false, true>(mem, n, cfg, sms, st, s, err);
+    return dispatch_ty<T, KMODE, false, false>(mem, n, cfg, sms, st, s, err);
 }
 
 template <typename T>
-static int dispatch_kmode(wx_ctx *c, cudaStream_t s, const CUtensorMap &tm, void *out) {
+static int dispatch_kmode(wx_ctx *const *mem, int n, const StepCfg &cfg, int sms, unsigned *st, cudaStream_t s,
+                          std::string &err) {
     if constexpr (std::is_same<T, float>::value)
-        if (mixed(c)) return dispatch_flags<T, 2>(c, s, tm, out);
-    if (!per_col(c)) return dispatch_flags<T, 0>(c, s, tm, out);
-    return dispatch_flags<T, 1>(c, s, tm, out);
+        if (mixed(mem[0])) return dispatch_flags<T, 2>(mem, n, cfg, sms, st, s, err);
+    if (!per_col(mem[0])) return dispatch_flags<T, 0>(mem, n, cfg, sms, st, s, err);
+    return dispatch_flags<T, 1>(mem, n, cfg, sms, st, s, err);
 }
 
-int launch_step(wx_ctx *c, cudaStream_t s, long *launches) {
-    const int src = c->cur, dst = 1 - c->cur;
-    int rc = (c->t_bytes == 4) ? dispatch_kmode<float>(c, s, c->tmap[src], c->fld[dst])
-                               : dispatch_kmode<double>(c, s, c->tmap[src], c->fld[dst]);
-    if (rc != WX_OK) return rc;
-    ++*launches;
+// The per-member kernels that follow the step kernel: the side solve of
+// WX_MIXED and the sums reduction; then the member's buffers swap.
+static int after_step(wx_ctx *c, int ty_used, cudaStream_t s, long *launches) {
+    const int dst = 1 - c->cur;
     const bool sums = c->flags & WX_SUMS;
     if (mixed(c) && (c->flags & WX_PHYSICS)) {
         const int nt = 128;
         mixed_fixup_kernel<<<(unsigned)((c->n_list + nt - 1) / nt), nt, 0, s>>>(
             c->flag_list, c->n_list, c->n_flag, (const double2 *)c->flag_fac, c->flag_e, c->flag_side,
-            (const Q4<float> *)c->tab + REC_F * c->nz, (float *)c->fld[dst],
-            sums ? c->flag_corr : nullptr, c->nx, c->ny, c->nz, c->P, c->R);
+            (const Q4<float> *)c->tab + REC_F * c->nz, (float *)c->fld[dst], sums ? c->flag_corr : nullptr, c->nx,
+            c->ny, c->nz, c->P, c->R);
         WX_CK(cudaGetLastError(), "mixed fixup kernel");
         ++*launches;
     }
     if (sums) {
-        const long ntiles = (long)((c->nx + kTileX - 1) / kTileX) * ((c->ny + c->cfg.ty - 1) / c->cfg.ty);
-        double *dst_sum = c->sums_ring + 2 * (c->sums_count % c->sums_cap);
+        const long ntiles = (long)((c->nx + kTileX - 1) / kTileX) * ((c->ny + ty_used - 1) / ty_used);
         const long ncorr = (mixed(c) && (c->flags & WX_PHYSICS)) ? c->n_list : 0;
         sums_finalize<<<kFinBlocks, 256, 0, s>>>(c->partials, ntiles, c->flag_corr, ncorr, c->h * c->h,
-                                                 c->fin_park, c->fin_ticket, dst_sum);
+                                                 c->fin_park, c->fin_ticket, c->sums_ring, c->d_sums_count,
+                                                 c->sums_cap);
         WX_CK(cudaGetLastError(), "sums kernel");
         ++*launches;
-        ++c->sums_count;
     }
     c->cur = dst;
     return WX_OK;
+}
+
+int launch_batch(wx_ctx *const *mem, int n, const StepCfg &cfg, unsigned *status, cudaStream_t s,
+                 long *launches, std::string &err) {
+    if (n < 1 || n > kMaxMembers) {
+        err = "batch size out of range";
+        return WX_EINVAL;
+    }
+    const int sms = mem[0]->num_sms;
+    const int rc = (mem[0]->t_bytes == 4) ? dispatch_kmode<float>(mem, n, cfg, sms, status, s, err)
+                                          : dispatch_kmode<double>(mem, n, cfg, sms, status, s, err);
+    if (rc != WX_OK) return rc;
+    ++*launches;
+    for (int i = 0; i < n; ++i) {
+        const int r2 = after_step(mem[i], cfg.ty, s, launches);
+        if (r2 != WX_OK) {
+            err = mem[i]->err;
+            return r2;
+        }
+    }
+    return WX_OK;
+}
+
+int launch_step(wx_ctx *c, cudaStream_t s, long *launches) {
+    wx_ctx *mem[1] = {c};
+    return launch_batch(mem, 1, c->cfg, c->d_status, s, launches, c->err);
 }
 
 // WX_MIXED set-up: flag the columns whose dominance ratio is below the

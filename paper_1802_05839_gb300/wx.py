@@ -63,6 +63,19 @@ SIGNATURES = [
     ("wx_sums_noalloc", ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int, _VP, ctypes.c_double, _VP, _VP]),
     ("wx_sums_noalloc_error", ctypes.c_char_p, []),
+    ("wx_tune", ctypes.c_int, [_VP, ctypes.c_char_p, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_double)]),
+    ("wx_ens_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(_VP)]),
+    ("wx_ens_size", ctypes.c_int, [_VP]),
+    ("wx_ens_member", _VP, [_VP, ctypes.c_int]),
+    ("wx_ens_step", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP]),
+    ("wx_ens_sync", ctypes.c_int, [_VP]),
+    ("wx_ens_set_step_config", ctypes.c_int, [_VP] + [ctypes.c_int] * 5),
+    ("wx_ens_get_step_config", ctypes.c_int, [_VP] + [ctypes.POINTER(ctypes.c_int)] * 5),
+    ("wx_ens_tune", ctypes.c_int, [_VP, ctypes.c_char_p, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_double)]),
+    ("wx_ens_last_launches", ctypes.c_long, [_VP]),
+    ("wx_ens_destroy", None, [_VP]),
+    ("wx_ens_last_error", ctypes.c_char_p, [_VP]),
     ("wx_destroy", None, [_VP]),
     ("wx_last_error", ctypes.c_char_p, [_VP]),
 ]
@@ -205,6 +218,77 @@ class Context:
 
     def last_launches(self):
         return int(lib().wx_last_launches(self.ptr))
+
+    def tune(self, cache_path=None, force=False, stream=None):
+        """Autotune the launch configuration (state restored); returns ms/step."""
+        ms = ctypes.c_double()
+        _check(lib().wx_tune(self.ptr, cache_path.encode() if cache_path else None, int(force),
+                             _stream_ptr(stream), ctypes.byref(ms)), self.ptr)
+        return ms.value
+
+
+class _Member(Context):
+    """A member context owned by an Ensemble (never destroyed on its own)."""
+
+    def __init__(self, ptr, nx, ny, nz, dtype):
+        self.ptr, self.nx, self.ny, self.nz, self.dtype = ptr, nx, ny, nz, dtype
+        self._keep = None
+
+    def close(self):
+        self.ptr = None
+
+    __del__ = close
+
+
+def _echeck(code, e):
+    if code != 0:
+        msg = lib().wx_ens_last_error(e)
+        raise WxError(code, msg.decode() if msg else "")
+
+
+class Ensemble:
+    """Up to 16 grids of uneven sizes stepped by one persistent launch per
+    step (replayed from a CUDA graph)."""
+
+    def __init__(self, sizes, dtype="f32"):
+        m = len(sizes)
+        arr = lambda k: (ctypes.c_int * m)(*[int(s[k]) for s in sizes])
+        p = _VP()
+        _echeck(lib().wx_ens_create(m, arr(0), arr(1), arr(2), DTYPES[dtype], ctypes.byref(p)), None)
+        self.ptr = p
+        self.members = [_Member(_VP(lib().wx_ens_member(p, i)), *sizes[i], dtype) for i in range(m)]
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            for mem in self.members:
+                mem.ptr = None
+            lib().wx_ens_destroy(self.ptr)
+            self.ptr = None
+
+    __del__ = close
+
+    def step(self, n_steps=1, graph=True, stream=None):
+        _echeck(lib().wx_ens_step(self.ptr, int(n_steps), int(graph), _stream_ptr(stream)), self.ptr)
+
+    def sync(self):
+        _echeck(lib().wx_ens_sync(self.ptr), self.ptr)
+
+    def set_step_config(self, ty, kb, stages, ctas_per_sm, prefetch=0):
+        _echeck(lib().wx_ens_set_step_config(self.ptr, ty, kb, stages, ctas_per_sm, prefetch), self.ptr)
+
+    def step_config(self):
+        v = [ctypes.c_int() for _ in range(5)]
+        _echeck(lib().wx_ens_get_step_config(self.ptr, *[ctypes.byref(x) for x in v]), self.ptr)
+        return dict(zip(("ty", "kb", "stages", "ctas_per_sm", "prefetch"), (x.value for x in v)))
+
+    def tune(self, cache_path=None, force=False, stream=None):
+        ms = ctypes.c_double()
+        _echeck(lib().wx_ens_tune(self.ptr, cache_path.encode() if cache_path else None, int(force),
+                                  _stream_ptr(stream), ctypes.byref(ms)), self.ptr)
+        return ms.value
+
+    def last_launches(self):
+        return int(lib().wx_ens_last_launches(self.ptr))
 
 
 def wx_sums_noalloc(T, q, dz, h, out, stream=None):
