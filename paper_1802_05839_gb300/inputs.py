@@ -261,3 +261,25 @@ def round_to_f32(case: Case) -> Case:
     c.dz, c.kappa_lev, c.alpha, c.kappa_mult = r(c.dz), r(c.kappa_lev), r(c.alpha), r(c.kappa_mult)
     c.dt, c.h, c.kappa_h, c.S0, c.q_ref = f(c.dt), f(c.h), f(c.kappa_h), f(c.S0), f(c.q_ref)
     return c
+
+
+# ----------------------------------------------------------------- MLP
+MLP_SIZES = [(232, 512), (512, 512), (512, 512), (512, 116)]  # (fan_in, fan_out)
+
+
+def mlp_init(seed: int = 2024):
+    """Random initial weights of the column-physics MLP: He/Kaiming-uniform
+    W_l ~ U(-sqrt(6/fan_in), sqrt(6/fan_in)) in [fan_out][fan_in] layout,
+    biases zero.  Stream 100 + l of `seed` per layer."""
+    Ws, bs = [], []
+    for l, (fi, fo) in enumerate(MLP_SIZES):
+        bound = np.sqrt(6.0 / fi)
+        u = uniform(seed, 100 + l, fi * fo)
+        Ws.append(((2.0 * u - 1.0) * bound).reshape(fo, fi))
+        bs.append(np.zeros(fo))
+    return Ws, bs
+
+
+def column_sample(ncol_total: int, n: int, seed: int, stream: int = 200) -> np.ndarray:
+    """n distinct-ish column indices drawn uniformly from [0, ncol_total)."""
+    return np.minimum((uniform(seed, stream, n) * ncol_total).astype(np.int64), ncol_total - 1)
