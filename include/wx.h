@@ -66,7 +66,8 @@ enum {
 enum {
     WX_ADVECTION = 1u, /* include the upwind advection term                    */
     WX_PHYSICS = 2u,   /* run the column physics (Thomas solve + radiation)    */
-    WX_SUMS = 4u       /* record FP64 mass/energy sums after every step        */
+    WX_SUMS = 4u,      /* record FP64 mass/energy sums after every step        */
+    WX_SURROGATE = 8u  /* column physics by the attached MLP, residual-checked */
 };
 
 typedef struct {
@@ -82,7 +83,7 @@ typedef struct {
     const double *kappa_lev; /* [nz] vertical diffusivity profile (>= 0), host */
     const double *alpha;     /* [nz] absorber coefficient (>= 0), host         */
     const double *kappa_mult;/* [ny*nx] per-column multiplier (>= 0) or NULL   */
-    unsigned flags;          /* WX_ADVECTION | WX_PHYSICS | WX_SUMS            */
+    unsigned flags;          /* WX_ADVECTION | WX_PHYSICS | WX_SUMS | WX_SURROGATE */
 } wx_params;
 
 /* Create a context for an nx x ny x nz grid (each >= 1; nz <= 256).
@@ -237,6 +238,106 @@ int wx_ens_tune(wx_ens *e, const char *cache_path, int force,
 long wx_ens_last_launches(const wx_ens *e);
 void wx_ens_destroy(wx_ens *e);          /* NULL-safe; frees the members */
 const char *wx_ens_last_error(const wx_ens *e);
+
+/* ----------------------------------------------- learned column physics
+ * A small MLP surrogate of the column physics (232 -> 512 -> 512 -> 512 ->
+ * 116, exact-erf GELU): BF16 weights and activations, FP32 accumulation in
+ * tensor memory, hand-written tcgen05 GEMMs.  The paper has no learned
+ * part; this follows the batched per-column interface of its physics
+ * (Sec. 3.1: every K column is processed independently). */
+
+/* C[M][N] = A[M][K] . B[N][K]^T on device BF16 operands (both K-major),
+ * FP32 accumulation; M, N multiples of 128, K of 64.  epilogue:
+ *   0  out (f32)  = C + bias (bias may be NULL)
+ *   1  out (bf16) = GELU(C + bias), out2 (bf16) = C + bias (out2 may be
+ *      NULL: the pre-activation is then not stored)
+ *   2  out (bf16) = C * GELU'(aux), aux (bf16 [M][N]) = the saved C + bias
+ *   3  out (bf16) = C + bias (bias may be NULL)
+ * status: device word that receives WX_ETIMEOUT's bit on a bounded-wait
+ * timeout.  Asynchronous on the stream. */
+int wx_gemm_bf16(const void *A, const void *B, int M, int N, int K,
+                 int epilogue, const float *bias, const void *aux, void *out,
+                 void *out2, unsigned *status, void *cuda_stream);
+
+/* Message of the last failing wx_gemm_bf16 / wx_mlp_* call on this thread. */
+const char *wx_mlp_last_error(void);
+
+/* The surrogate network.  Layer l maps fan_in(l) -> fan_out(l) with
+ * (232, 512), (512, 512), (512, 512), (512, 116); weights are FP32 masters
+ * with BF16 copies, [fan_out][fan_in] row-major on the host side of the
+ * get/set calls.  Inputs x = [T*_k | q*_k | kappa_mult kappa_lev(k) |
+ * alpha_k dz_k] (k = 0..57, bottom first) are normalised per feature;
+ * outputs y = [H_k | (T**_k - T*_k)/dt] likewise, where T** is the implicit
+ * vertical diffusion's result and H the radiative heating (Sec. 3.1's
+ * column physics, Eq. 1).  On the device, normalised inputs are BF16 rows
+ * of 256 (232 used, zero padding) and outputs FP32 rows of 128 (116 used);
+ * row counts are multiples of 128. */
+typedef struct wx_mlp wx_mlp;
+/* Allocate a network whose training and activation buffers hold max_batch
+ * rows (multiple of 128); weights zero, normalisation identity. */
+int wx_mlp_create(int max_batch, wx_mlp **out);
+void wx_mlp_destroy(wx_mlp *m);                    /* NULL-safe */
+/* Host FP32 weights W[l] ([fan_out][fan_in]) and biases b[l] (4 each);
+ * resets the Adam moments and step count. */
+int wx_mlp_set_weights(wx_mlp *m, const float *const *W, const float *const *b);
+int wx_mlp_get_weights(wx_mlp *m, float *const *W, float *const *b);
+/* Gradients of the last wx_mlp_gradients / wx_mlp_train_step (host FP32,
+ * same layout as the weights). */
+int wx_mlp_get_grads(wx_mlp *m, float *const *dW, float *const *db);
+/* Normalisation: host mean/std of the 232 inputs and of the 116 outputs. */
+int wx_mlp_set_norm(wx_mlp *m, const float *mean_in, const float *std_in,
+                    const float *mean_out, const float *std_out);
+int wx_mlp_get_norm(wx_mlp *m, float *mean_in, float *std_in,
+                    float *mean_out, float *std_out);
+/* Per-level constants of the features: kappa_lev[58] and alpha*dz [58]
+ * (host); nz must be 58 (WX_EUNSUPPORTED otherwise). */
+int wx_mlp_set_levels(wx_mlp *m, int nz, const float *kappa_lev,
+                      const float *alpha_dz);
+/* Fit the normalisation to a training set on the device: T*, q* [ncol][58],
+ * kappa_mult [ncol] (NULL = 1), tend [ncol][2][58] as written by
+ * wx_physics_columns.  Per-feature mean and population standard deviation
+ * in FP64 (floor 1e-6 |mean|).  Asynchronous. */
+int wx_mlp_fit_norm(wx_mlp *m, const float *Ts, const float *qs,
+                    const float *kappa_mult, const float *tend, long ncol,
+                    void *cuda_stream);
+/* Normalised BF16 input rows X [ceil128(ncol)][256] and, when tend and Yt
+ * are given, FP32 target rows Yt [ceil128(ncol)][128] of device columns
+ * (padding rows zero).  Asynchronous. */
+int wx_mlp_prepare(wx_mlp *m, const float *Ts, const float *qs,
+                   const float *kappa_mult, const float *tend, long ncol,
+                   void *X, float *Yt, void *cuda_stream);
+/* Normalised outputs Y [M][128] (FP32) of BF16 rows X [M][256]; any M that
+ * is a multiple of 128 (processed in chunks of max_batch). */
+int wx_mlp_forward(wx_mlp *m, const void *X, int M, float *Y,
+                   void *cuda_stream);
+/* Forward and backward of the mean-squared error over the 116 outputs of
+ * M rows (M multiple of 128, <= max_batch): gradients into the network's
+ * buffers; loss (device float or NULL) = the batch loss. */
+int wx_mlp_gradients(wx_mlp *m, const void *X, const float *Yt, int M,
+                     float *loss, void *cuda_stream);
+/* wx_mlp_gradients followed by one Adam step (beta1 0.9, beta2 0.999,
+ * eps 1e-8, bias-corrected) at learning rate lr on the FP32 masters; BF16
+ * copies refreshed. */
+int wx_mlp_train_step(wx_mlp *m, const void *X, const float *Yt, int M,
+                      float lr, float *loss, void *cuda_stream);
+/* WX_OK, or WX_ETIMEOUT if a bounded device wait of a GEMM gave up since the
+ * last call (synchronises). */
+int wx_mlp_status(wx_mlp *m);
+
+/* Attach (m != NULL) or detach (NULL) a trained network to an FP32 context
+ * with nz = 58.  With WX_SURROGATE in the flags, each wx_step then runs the
+ * dynamics, predicts the column physics with the network and accepts a
+ * column's prediction only if both residuals stay within fallback_tol:
+ *   rho_vd = ||A x - T*|| / ||A T* - T*||  (A = the implicit vertical-
+ *            diffusion matrix of the column, x = T* + dt y_vd);
+ *   rho_H  = |sum_k H_k dz_k - S0 (1 - exp(-tau_tot))| / (S0 (1 - exp(-tau_tot))).
+ * Rejected columns are recomputed exactly (Thomas sweep and scan).  The
+ * network must outlive the attachment; the context owns its own activation
+ * buffers.  WX_SURROGATE excludes WX_SUMS. */
+int wx_set_surrogate(wx_ctx *c, wx_mlp *m, double fallback_tol);
+/* Columns the residual check sent to the exact path in the last step
+ * (synchronises). */
+int wx_surrogate_fallbacks(wx_ctx *c, long *n_fallback);
 
 /* Free the context and its device memory.  NULL-safe. */
 void wx_destroy(wx_ctx *c);

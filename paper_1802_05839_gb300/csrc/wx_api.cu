@@ -161,6 +161,7 @@ extern "C" int wx_create(int nx, int ny, int nz, int dtype, wx_ctx **out) {
 
 extern "C" void wx_destroy(wx_ctx *c) {
     if (!c) return;
+    free_surrogate(c);
     void *ptrs[] = {c->fld[0], c->fld[1], c->U,        c->V,         c->kmult,     c->tab,
                     c->d_lev,  c->staging, c->d_status, c->partials, c->sums_ring, c->flag_list,
                     c->flag_idx, c->flag_fac, c->flag_e, c->flag_side, c->flag_corr,
@@ -237,8 +238,10 @@ extern "C" int wx_set_params(wx_ctx *c, const wx_params *p) {
         return fail(c, WX_EINVAL, "wx_set_params: kappa_h and S0 must be finite and >= 0");
     if (!p->dz || !p->kappa_lev || !p->alpha)
         return fail(c, WX_EINVAL, "wx_set_params: dz, kappa_lev and alpha are required");
-    if (p->flags & ~(unsigned)(WX_ADVECTION | WX_PHYSICS | WX_SUMS))
+    if (p->flags & ~(unsigned)(WX_ADVECTION | WX_PHYSICS | WX_SUMS | WX_SURROGATE))
         return fail(c, WX_EINVAL, "wx_set_params: unknown flag bits");
+    if ((p->flags & WX_SURROGATE) && (c->dtype != WX_F32 || c->nz != 58 || (p->flags & WX_SUMS)))
+        return fail(c, WX_EUNSUPPORTED, "wx_set_params: WX_SURROGATE needs WX_F32, nz = 58 and no WX_SUMS");
     const int nz = c->nz;
     for (int k = 0; k < nz; ++k) {
         if (!finite_pos(p->dz[k])) return fail(c, WX_EINVAL, "wx_set_params: dz must be finite and > 0");
@@ -421,7 +424,12 @@ extern "C" int wx_step(wx_ctx *c, int n_steps, void *stream) {
     RC(check_cfl(c));
     cudaStream_t s = (cudaStream_t)stream;
     long launches = 0;
-    for (int n = 0; n < n_steps; ++n) RC(launch_step(c, s, &launches));
+    if (c->flags & WX_SURROGATE) {
+        if (!c->sur) return fail(c, WX_ESTATE, "wx_step: WX_SURROGATE without an attached network");
+        for (int n = 0; n < n_steps; ++n) RC(launch_surrogate_step(c, s, &launches));
+    } else {
+        for (int n = 0; n < n_steps; ++n) RC(launch_step(c, s, &launches));
+    }
     c->last_launches = launches;
     c->last_stream = s;
     return WX_OK;

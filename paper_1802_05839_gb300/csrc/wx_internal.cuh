@@ -156,6 +156,15 @@ struct wx_ctx {
     long n_flag = 0;             // columns solved in FP64 (first in the list)
     long n_list = 0;             // all listed columns (kappa_mult != 1)
 
+    // WX_SURROGATE: the attached network and this grid's activation buffers
+    struct wx_mlp *sur = nullptr;
+    double sur_tol = 2e-2;
+    long sur_rows = 0;            // nx*ny rounded up to 128
+    void *sur_X = nullptr, *sur_H[2] = {nullptr, nullptr};
+    float *sur_Y = nullptr, *sur_lev = nullptr;  // [rows][128]; [2][nz] kappa_lev, alpha dz
+    unsigned long long *sur_nfb = nullptr;       // fallback columns of the last step
+    unsigned sur_gen = ~0u;       // generation sur_lev was built for
+
     wx::StepCfg cfg;
     bool cfg_forced = false;
     cudaStream_t last_stream = nullptr;
@@ -182,5 +191,8 @@ bool cfg_fits(const wx_ctx *c, const StepCfg &cfg, int *smem_bytes);
 int encode_tmap(wx_ctx *c, int which, int ty, int kb);
 int apply_cfg(wx_ctx *c, const StepCfg &g);
 int check_cfl(wx_ctx *c);
+// WX_SURROGATE (wx_mlp.cu)
+int launch_surrogate_step(wx_ctx *c, cudaStream_t s, long *launches);
+void free_surrogate(wx_ctx *c);
 
 }  // namespace wx

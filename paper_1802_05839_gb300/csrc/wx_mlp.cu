@@ -1,0 +1,1160 @@
+// wx_mlp.cu -- BF16 tcgen05 GEMMs and the MLP surrogate of the column
+// physics: forward, backward, Adam, the residual-checked surrogate step.
+//
+// GEMM: C[M][N] = A[M][K] . B[N][K]^T, A and B BF16 and K-major in global
+// memory, FP32 accumulation in tensor memory.  One CTA (4 warps) per 128 x BN
+// output tile: thread 0 streams 128 x 64 and BN x 64 K-slabs of A and B
+// through a 4-slot shared-memory ring with TMA (128-byte swizzle); thread 32
+// issues tcgen05.mma (M = 128, N = BN, K = 16, four per slab) and commits
+// each slab back to its ring slot; when the last slab's MMAs complete, the
+// four warps drain their 32 TMEM lanes each with tcgen05.ld and apply the
+// epilogue (bias, GELU, GELU' for backward) on the way to global memory.
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "ptx.cuh"
+#include "wx_internal.cuh"
+
+namespace wx {
+
+enum GemmEpi : int {
+    EPI_F32 = 0,        // out_f32 = acc (+ bias)
+    EPI_GELU = 1,       // z = acc + bias: out_bf16 = GELU(z), out2_bf16 = z
+    EPI_DGELU = 2,      // out_bf16 = acc * GELU'(aux), aux = saved z (bf16)
+    EPI_BIAS_BF16 = 3,  // out_bf16 = acc + bias
+};
+
+struct GemmArgs {
+    int M, N, K;
+    const float *bias;          // [N] or nullptr
+    const __nv_bfloat16 *aux;   // [M][N] (EPI_DGELU)
+    void *out;                  // [M][N] f32 or bf16
+    __nv_bfloat16 *out2;        // [M][N] (EPI_GELU)
+    unsigned *status;
+};
+
+constexpr int kGemmBK = 64;  // BF16 K per slab: one 128-byte swizzle row
+// Ring depth: two slots of 48 KB for 256-column tiles, three of 32 KB for
+// 128-column tiles, so that two CTAs share an SM and one's epilogue runs
+// under the other's MMAs.
+__host__ __device__ constexpr int gemm_stages(int BN) { return BN == 256 ? 2 : 3; }
+__host__ __device__ constexpr int gemm_smem(int BN) {
+    return gemm_stages(BN) * (128 * kGemmBK * 2 + BN * kGemmBK * 2) + 1024 + 256;
+}
+
+// exact GELU (the erf form) and its derivative
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+    const float cdf = 0.5f * (1.f + erff(z * 0.70710678118654752f));
+    const float pdf = 0.39894228040143268f * expf(-0.5f * z * z);
+    return cdf + z * pdf;
+}
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(256, 2) gemm_kernel(const __grid_constant__ CUtensorMap ta,
+                                                   const __grid_constant__ CUtensorMap tb, const GemmArgs g) {
+    constexpr int BM = 128;
+    constexpr int kGemmStages = gemm_stages(BN);
+    constexpr uint32_t A_BYTES = BM * kGemmBK * 2, B_BYTES = BN * kGemmBK * 2;
+    constexpr uint32_t STAGE = A_BYTES + B_BYTES;
+    extern __shared__ __align__(1024) unsigned char gsm[];
+    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(gsm) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(base + kGemmStages * STAGE);
+    uint64_t *empty = full + kGemmStages;
+    uint64_t *done = empty + kGemmStages;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int nk = g.K / kGemmBK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kGemmStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(tmem_slot, BN);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (threadIdx.x == 0) {
+        // producer: K-slabs of A and B into the ring
+        prefetch_tmap(&ta);
+        prefetch_tmap(&tb);
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % kGemmStages;
+            if (kb >= kGemmStages && !mbar_wait_bounded(&empty[s], ((kb / kGemmStages) - 1) & 1)) {
+                *abort_flag = 1;
+                break;
+            }
+            unsigned char *sa = base + s * STAGE;
+            mbar_arrive_expect_tx(&full[s], STAGE);
+            tma_load_2d(sa, &ta, &full[s], kb * kGemmBK, m0);
+            tma_load_2d(sa + A_BYTES, &tb, &full[s], kb * kGemmBK, n0);
+        }
+    } else if (threadIdx.x == 32) {
+        // MMA issuer
+        constexpr uint32_t idesc = idesc_bf16(BM, BN);
+        bool ok = true;
+        for (int kb = 0; kb < nk && ok; ++kb) {
+            const int s = kb % kGemmStages;
+            if (!mbar_wait_bounded(&full[s], (kb / kGemmStages) & 1)) {
+                ok = false;
+                *abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const unsigned char *sa = base + s * STAGE;
+            const uint64_t ad = smem_desc_sw128(sa), bd = smem_desc_sw128(sa + A_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < kGemmBK / 16; ++kk) {
+                // +32 bytes per K = 16 step inside the 128-byte swizzle row
+                tc_mma_bf16(tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, (kb | kk) != 0);
+            }
+            tc_commit(&empty[s]);
+        }
+        tc_commit(done);  // arrives once every MMA issued above has completed
+    }
+
+    // epilogue: warp w drains TMEM lanes 32(w%4)..+31 (rows m0+32(w%4)+lane),
+    // columns [BN/2 (w/4), BN/2 (w/4 + 1))
+    __syncwarp();
+    const bool ok = mbar_wait_bounded(done, 0);
+    __syncwarp();
+    tc_fence_after();
+    if (!ok || *abort_flag) {
+        if (threadIdx.x == 0) atomicOr(g.status, ST_TIMEOUT);
+    } else {
+        const int quarter = warp & 3, half = warp >> 2;
+        const int row = m0 + quarter * 32 + lane;
+        const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
+        for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 16) {
+            float v[16];
+            tmem_ld16(trow + c0, v);
+            const int col = n0 + c0;
+            const size_t o = (size_t)row * g.N + col;
+            if (EPI == EPI_F32) {
+                float *out = reinterpret_cast<float *>(g.out) + o;
+#pragma unroll
+                for (int i = 0; i < 16; i += 4) {
+                    float4 w4;
+                    w4.x = v[i] + (g.bias ? g.bias[col + i] : 0.f);
+                    w4.y = v[i + 1] + (g.bias ? g.bias[col + i + 1] : 0.f);
+                    w4.z = v[i + 2] + (g.bias ? g.bias[col + i + 2] : 0.f);
+                    w4.w = v[i + 3] + (g.bias ? g.bias[col + i + 3] : 0.f);
+                    *reinterpret_cast<float4 *>(out + i) = w4;
+                }
+            } else {
+                __align__(16) __nv_bfloat16 o1[16];
+                __align__(16) __nv_bfloat16 o2[16];
+                __align__(16) __nv_bfloat16 zin[16];
+                if (EPI == EPI_DGELU) {
+                    const uint4 *zp = reinterpret_cast<const uint4 *>(g.aux + o);
+                    *reinterpret_cast<uint4 *>(zin) = zp[0];
+                    *reinterpret_cast<uint4 *>(zin + 8) = zp[1];
+                }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    if (EPI == EPI_GELU) {
+                        const float z = v[i] + g.bias[col + i];
+                        o1[i] = __float2bfloat16_rn(gelu(z));
+                        o2[i] = __float2bfloat16_rn(z);
+                    } else if (EPI == EPI_DGELU) {
+                        o1[i] = __float2bfloat16_rn(v[i] * gelu_grad(__bfloat162float(zin[i])));
+                    } else {
+                        o1[i] = __float2bfloat16_rn(v[i] + (g.bias ? g.bias[col + i] : 0.f));
+                    }
+                }
+                __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(g.out) + o;
+                reinterpret_cast<uint4 *>(out)[0] = *reinterpret_cast<uint4 *>(o1);
+                reinterpret_cast<uint4 *>(out)[1] = *reinterpret_cast<uint4 *>(o1 + 8);
+                if (EPI == EPI_GELU && g.out2) {
+                    __nv_bfloat16 *out2 = g.out2 + o;
+                    reinterpret_cast<uint4 *>(out2)[0] = *reinterpret_cast<uint4 *>(o2);
+                    reinterpret_cast<uint4 *>(out2)[1] = *reinterpret_cast<uint4 *>(o2 + 8);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, BN);
+}
+
+// ------------------------------------------------------------ launcher
+static PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 2D BF16 row-major [rows][K] operand, box 64 (K) x box_rows, 128-byte swizzle.
+static bool encode_operand(CUtensorMap *m, const void *ptr, int rows, int K, int box_rows) {
+    auto enc = encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kGemmBK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Descriptors are cached per (pointer, shape): the MLP reuses its buffers.
+static std::mutex g_map_mu;
+static std::map<std::tuple<const void *, int, int, int>, CUtensorMap> g_maps;
+
+static bool operand_map(CUtensorMap *m, const void *ptr, int rows, int K, int box_rows) {
+    std::lock_guard<std::mutex> lk(g_map_mu);
+    auto key = std::make_tuple(ptr, rows, K, box_rows);
+    auto it = g_maps.find(key);
+    if (it != g_maps.end()) {
+        *m = it->second;
+        return true;
+    }
+    if (!encode_operand(m, ptr, rows, K, box_rows)) return false;
+    g_maps[key] = *m;
+    return true;
+}
+
+template <int BN, int EPI> static cudaError_t gemm_launch(const CUtensorMap &a, const CUtensorMap &b, const GemmArgs &g,
+                                                         cudaStream_t s) {
+    auto k = gemm_kernel<BN, EPI>;
+    const int smem = gemm_smem(BN);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    // n fastest: the CTAs of one 128-row block run together and share its A
+    // tile in L2
+    dim3 grid(g.N / BN, g.M / 128);
+    k<<<grid, 256, smem, s>>>(a, b, g);
+    return cudaGetLastError();
+}
+
+// C = A . B^T with the epilogue `epi`.  M % 128 == 0, K % 64 == 0, N % 128
+// == 0 (tiles of 256 columns when N % 256 == 0).
+int gemm(const void *A, const void *B, int M, int N, int K, int epi, const float *bias, const void *aux, void *out,
+         void *out2, unsigned *status, cudaStream_t s, std::string &err) {
+    if (M <= 0 || N <= 0 || K <= 0 || M % 128 || N % 128 || K % kGemmBK) {
+        err = "gemm: M and N must be multiples of 128 and K of 64";
+        return WX_EINVAL;
+    }
+    if (M / 128 > 65535) {
+        err = "gemm: M above 65535 x 128 rows";
+        return WX_EINVAL;
+    }
+    const int BN = (N % 256 == 0) ? 256 : 128;
+    CUtensorMap ta, tb;
+    if (!operand_map(&ta, A, M, K, 128) || !operand_map(&tb, B, N, K, BN)) {
+        err = "gemm: tensor map encoding failed (alignment?)";
+        return WX_ECUDA;
+    }
+    GemmArgs g{M, N, K, bias, reinterpret_cast<const __nv_bfloat16 *>(aux), out,
+               reinterpret_cast<__nv_bfloat16 *>(out2), status};
+    cudaError_t e = cudaErrorInvalidValue;
+#define WX_GEMM_CASE(E)                                                                        \
+    case E:                                                                                    \
+        e = (BN == 256) ? gemm_launch<256, E>(ta, tb, g, s) : gemm_launch<128, E>(ta, tb, g, s); \
+        break;
+    switch (epi) {
+        WX_GEMM_CASE(EPI_F32)
+        WX_GEMM_CASE(EPI_GELU)
+        WX_GEMM_CASE(EPI_DGELU)
+        WX_GEMM_CASE(EPI_BIAS_BF16)
+        default: err = "gemm: unknown epilogue"; return WX_EINVAL;
+    }
+#undef WX_GEMM_CASE
+    if (e != cudaSuccess) {
+        err = std::string("gemm: ") + cudaGetErrorString(e);
+        return WX_ECUDA;
+    }
+    return WX_OK;
+}
+
+}  // namespace wx
+
+using namespace wx;
+
+static thread_local std::string g_mlp_err;
+
+extern "C" const char *wx_mlp_last_error(void) { return g_mlp_err.c_str(); }
+
+extern "C" int wx_gemm_bf16(const void *A, const void *B, int M, int N, int K, int epilogue, const float *bias,
+                            const void *aux, void *out, void *out2, unsigned *status, void *stream) {
+    if (!A || !B || !out || !status) {
+        g_mlp_err = "wx_gemm_bf16: NULL pointer";
+        return WX_EINVAL;
+    }
+    if ((epilogue == EPI_GELU && !bias) || (epilogue == EPI_DGELU && !aux)) {
+        g_mlp_err = "wx_gemm_bf16: epilogue needs bias/out2 (GELU) or aux (GELU')";
+        return WX_EINVAL;
+    }
+    return gemm(A, B, M, N, K, epilogue, bias, aux, out, out2, status, (cudaStream_t)stream, g_mlp_err);
+}
+
+// =====================================================================
+// MLP surrogate of the column physics
+//   x (232 = T*, q*, kappa_v, alpha dz per level; normalised, padded to 256)
+//   -> 512 -> 512 -> 512 (GELU) -> 116 (dt-free tendencies H and vdiff rate,
+//   normalised, padded to 128)
+// =====================================================================
+namespace wx {
+
+constexpr int kNZ = 58, kIn = 4 * kNZ, kInP = 256, kHid = 512, kOut = 2 * kNZ, kOutP = 128;
+constexpr int kLayers = 4;
+__host__ __device__ constexpr int layer_in(int l) { return l == 0 ? kInP : kHid; }
+__host__ __device__ constexpr int layer_out(int l) { return l == 3 ? kOutP : kHid; }
+
+}  // namespace wx
+
+struct wx_mlp {
+    int max_batch = 0;
+    float *W[wx::kLayers] = {}, *b[wx::kLayers] = {};          // FP32 master [N][K], [N]
+    __nv_bfloat16 *Wb[wx::kLayers] = {}, *WbT[wx::kLayers] = {};  // BF16 [N][K] and [K][N]
+    float *mW[wx::kLayers] = {}, *vW[wx::kLayers] = {}, *mb[wx::kLayers] = {}, *vb[wx::kLayers] = {};
+    float *dW[wx::kLayers] = {}, *db[wx::kLayers] = {};
+    float *norm = nullptr;   // [4][kIn | kOut]: mean_in, std_in, mean_out, std_out (padded to 256)
+    float *lev = nullptr;    // [2][kNZ]: kappa_lev, alpha*dz (feature inputs)
+    // activations for batch rows
+    __nv_bfloat16 *X = nullptr, *Z[3] = {}, *H[3] = {}, *dY = nullptr, *dZ[3] = {}, *TA = nullptr, *TB = nullptr;
+    float *Y = nullptr, *loss = nullptr;
+    unsigned *status = nullptr;
+    long adam_t = 0;
+    std::string err;
+};
+
+namespace wx {
+
+// ------------------------------------------------------------ small kernels
+__global__ void transpose_bf16_kernel(const __nv_bfloat16 *__restrict__ in, __nv_bfloat16 *__restrict__ out,
+                                      int rows, int cols) {
+    __shared__ __nv_bfloat16 t[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int r = r0 + y, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) t[y][threadIdx.x] = in[(size_t)r * cols + c];
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int c = c0 + y, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) out[(size_t)c * rows + r] = t[threadIdx.x][y];
+    }
+}
+
+// db[n] = sum_m dZT[n][m], one block per row, fixed-order tree.
+__global__ void rowsum_bf16_kernel(const __nv_bfloat16 *__restrict__ in, int cols, float *__restrict__ out) {
+    __shared__ float red[256];
+    const int r = blockIdx.x;
+    float s = 0.f;
+    for (int c = threadIdx.x; c < cols; c += blockDim.x) s += __bfloat162float(in[(size_t)r * cols + c]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[r] = red[0];
+}
+
+// dY = 2 (Y - Yt) / (M * kOut) on the kOut real outputs (bf16), 0 on the
+// padding; per-block squared-error partials for the loss.
+__global__ void mse_grad_kernel(const float *__restrict__ Y, const float *__restrict__ Yt, int M,
+                                __nv_bfloat16 *__restrict__ dY, float *__restrict__ part) {
+    __shared__ float red[256];
+    float s = 0.f;
+    const size_t n = (size_t)M * kOutP;
+    const float scale = 2.f / ((float)M * kOut);
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e % kOutP);
+        float g = 0.f;
+        if (c < kOut) {
+            const float d = Y[e] - Yt[e];
+            s += d * d;
+            g = scale * d;
+        }
+        dY[e] = __float2bfloat16_rn(g);
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void loss_finalize_kernel(const float *__restrict__ part, int n, int M, float *__restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += part[i];
+    out[0] = (float)(s / ((double)M * kOut));
+}
+
+// Adam (beta1, beta2, eps) on FP32 masters, then the BF16 copies [N][K] and
+// [K][N] (the latter feeds the input-gradient GEMM).
+__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, long n, int N, int K, float lr, float b1, float b2, float eps,
+                            float c1, float c2, __nv_bfloat16 *__restrict__ pb, __nv_bfloat16 *__restrict__ pbT) {
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+        const float gi = g[e];
+        const float mi = b1 * m[e] + (1.f - b1) * gi;
+        const float vi = b2 * v[e] + (1.f - b2) * gi * gi;
+        m[e] = mi;
+        v[e] = vi;
+        const float pi = p[e] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        p[e] = pi;
+        if (pb) {
+            const __nv_bfloat16 q = __float2bfloat16_rn(pi);
+            pb[e] = q;
+            const int nn = (int)(e / K), kk = (int)(e % K);
+            pbT[(size_t)kk * N + nn] = q;
+        }
+    }
+}
+
+__global__ void to_bf16_kernel(const float *__restrict__ p, long n, int N, int K, __nv_bfloat16 *__restrict__ pb,
+                               __nv_bfloat16 *__restrict__ pbT) {
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+        const __nv_bfloat16 q = __float2bfloat16_rn(p[e]);
+        pb[e] = q;
+        pbT[(size_t)(e % K) * N + (e / K)] = q;
+    }
+}
+
+// Features of ncol columns given as [ncol][nz] arrays (T*, q*), kappa_mult
+// per column (NULL = 1): normalised BF16 rows [ncol_pad][256].
+__global__ void features_cols_kernel(const float *__restrict__ Ts, const float *__restrict__ qs,
+                                     const float *__restrict__ km, long ncol, long ncol_pad,
+                                     const float *__restrict__ lev, const float *__restrict__ norm,
+                                     __nv_bfloat16 *__restrict__ X) {
+    const long col = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncol_pad) return;
+    __nv_bfloat16 *row = X + col * kInP;
+    if (col >= ncol) {
+        for (int f = 0; f < kInP; ++f) row[f] = __float2bfloat16_rn(0.f);
+        return;
+    }
+    const float s = km ? km[col] : 1.f;
+    for (int f = 0; f < kInP; ++f) {
+        float x = 0.f;
+        if (f < kIn) {
+            const int k = f % kNZ, kind = f / kNZ;
+            const float raw = kind == 0 ? Ts[col * kNZ + k]
+                              : kind == 1 ? qs[col * kNZ + k]
+                              : kind == 2 ? s * lev[k]
+                                          : lev[kNZ + k];
+            x = (raw - norm[f]) / norm[kInP + f];
+        }
+        row[f] = __float2bfloat16_rn(x);
+    }
+}
+
+// Targets from tend [ncol][2][nz] = (H_k, vdiff_k): normalised FP32 rows
+// [ncol_pad][128] (zeros past the data and on the padding columns).
+__global__ void targets_kernel(const float *__restrict__ tend, long ncol, long ncol_pad,
+                               const float *__restrict__ norm, float *__restrict__ Yt) {
+    const long col = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncol_pad) return;
+    const float *mo = norm + 2 * kInP, *so = norm + 3 * kInP;
+    for (int c = 0; c < kOutP; ++c) {
+        float y = 0.f;
+        if (c < kOut && col < ncol) y = (tend[col * kOut + c] - mo[c]) / so[c];
+        Yt[col * kOutP + c] = y;
+    }
+}
+
+// Per-feature mean and standard deviation over rows of raw features, in
+// FP64, fixed order (one block per feature).
+__global__ void feature_stats_kernel(const float *__restrict__ Ts, const float *__restrict__ qs,
+                                     const float *__restrict__ km, const float *__restrict__ tend, long ncol,
+                                     const float *__restrict__ lev, float *__restrict__ norm) {
+    __shared__ double s1[256], s2[256];
+    const int f = blockIdx.x;  // 0..kIn-1 inputs, kIn..kIn+kOut-1 targets
+    double a = 0.0, b = 0.0;
+    for (long c = threadIdx.x; c < ncol; c += blockDim.x) {
+        float raw;
+        if (f < kIn) {
+            const int k = f % kNZ, kind = f / kNZ;
+            raw = kind == 0 ? Ts[c * kNZ + k]
+                  : kind == 1 ? qs[c * kNZ + k]
+                  : kind == 2 ? (km ? km[c] : 1.f) * lev[k]
+                              : lev[kNZ + k];
+        } else {
+            raw = tend[c * kOut + (f - kIn)];
+        }
+        a += raw;
+        b += (double)raw * raw;
+    }
+    s1[threadIdx.x] = a;
+    s2[threadIdx.x] = b;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            s1[threadIdx.x] += s1[threadIdx.x + o];
+            s2[threadIdx.x] += s2[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double mean = s1[0] / (double)ncol;
+        const double var = fmax(s2[0] / (double)ncol - mean * mean, 0.0);
+        const float sd = (float)fmax(sqrt(var), 1e-6 * fmax(fabs(mean), 1e-12));
+        if (f < kIn) {
+            norm[f] = (float)mean;
+            norm[kInP + f] = sd > 0 ? sd : 1.f;
+        } else {
+            norm[2 * kInP + f - kIn] = (float)mean;
+            norm[3 * kInP + f - kIn] = sd > 0 ? sd : 1.f;
+        }
+    }
+}
+
+static int grid1(long n, int t = 256) { return (int)std::min<long>(std::max<long>((n + t - 1) / t, 1), 65535L * 16); }
+
+}  // namespace wx
+
+// ------------------------------------------------------------ C ABI
+static int mfail(wx_mlp *m, int code, const std::string &msg) {
+    g_mlp_err = msg;
+    if (m) m->err = msg;
+    return code;
+}
+
+#define MCK(call, what)                                                                         \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) return mfail(m, WX_ECUDA, std::string(what) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+extern "C" void wx_mlp_destroy(wx_mlp *m) {
+    if (!m) return;
+    for (int l = 0; l < kLayers; ++l)
+        for (void *p : {(void *)m->W[l], (void *)m->b[l], (void *)m->Wb[l], (void *)m->WbT[l], (void *)m->mW[l],
+                        (void *)m->vW[l], (void *)m->mb[l], (void *)m->vb[l], (void *)m->dW[l], (void *)m->db[l]})
+            if (p) cudaFree(p);
+    for (int i = 0; i < 3; ++i)
+        for (void *p : {(void *)m->Z[i], (void *)m->H[i], (void *)m->dZ[i]})
+            if (p) cudaFree(p);
+    for (void *p : {(void *)m->norm, (void *)m->lev, (void *)m->X, (void *)m->dY, (void *)m->TA, (void *)m->TB,
+                    (void *)m->Y, (void *)m->loss, (void *)m->status})
+        if (p) cudaFree(p);
+    delete m;
+}
+
+extern "C" int wx_mlp_create(int max_batch, wx_mlp **out) {
+    if (!out) return mfail(nullptr, WX_EINVAL, "wx_mlp_create: out is NULL");
+    *out = nullptr;
+    if (max_batch < 128 || max_batch % 128) return mfail(nullptr, WX_EINVAL, "wx_mlp_create: max_batch % 128 != 0");
+    wx_mlp *m = new (std::nothrow) wx_mlp();
+    if (!m) return mfail(nullptr, WX_ENOMEM, "wx_mlp_create: host allocation");
+    m->max_batch = max_batch;
+    auto alloc = [&](void **p, size_t bytes) {
+        if (cudaMalloc(p, bytes) != cudaSuccess) return false;
+        return cudaMemset(*p, 0, bytes) == cudaSuccess;
+    };
+    bool ok = true;
+    for (int l = 0; l < kLayers && ok; ++l) {
+        const size_t nk = (size_t)layer_out(l) * layer_in(l), n = layer_out(l);
+        ok = alloc((void **)&m->W[l], nk * 4) && alloc((void **)&m->b[l], n * 4) &&
+             alloc((void **)&m->Wb[l], nk * 2) && alloc((void **)&m->WbT[l], nk * 2) &&
+             alloc((void **)&m->mW[l], nk * 4) && alloc((void **)&m->vW[l], nk * 4) &&
+             alloc((void **)&m->mb[l], n * 4) && alloc((void **)&m->vb[l], n * 4) &&
+             alloc((void **)&m->dW[l], nk * 4) && alloc((void **)&m->db[l], n * 4);
+    }
+    const size_t B = max_batch;
+    for (int i = 0; i < 3 && ok; ++i)
+        ok = alloc((void **)&m->Z[i], B * kHid * 2) && alloc((void **)&m->H[i], B * kHid * 2) &&
+             alloc((void **)&m->dZ[i], B * kHid * 2);
+    ok = ok && alloc((void **)&m->norm, 4 * kInP * 4) && alloc((void **)&m->lev, 2 * kNZ * 4) &&
+         alloc((void **)&m->X, B * kInP * 2) && alloc((void **)&m->dY, B * kOutP * 2) &&
+         alloc((void **)&m->TA, B * kHid * 2) && alloc((void **)&m->TB, B * kHid * 2) &&
+         alloc((void **)&m->Y, B * kOutP * 4) && alloc((void **)&m->loss, 1024 * 4) &&
+         alloc((void **)&m->status, sizeof(unsigned));
+    if (!ok) {
+        cudaGetLastError();
+        wx_mlp_destroy(m);
+        return mfail(nullptr, WX_ENOMEM, "wx_mlp_create: device allocation failed");
+    }
+    // unit normalisation until set
+    std::vector<float> nrm(4 * kInP, 0.f);
+    for (int i = 0; i < kInP; ++i) nrm[kInP + i] = nrm[3 * kInP + i] = 1.f;
+    cudaMemcpy(m->norm, nrm.data(), nrm.size() * 4, cudaMemcpyHostToDevice);
+    *out = m;
+    return WX_OK;
+}
+
+// Weights from host FP32 arrays W_l [out][in] (real sizes 512x232, 512x512,
+// 512x512, 116x512) and biases b_l [out]; zero-padded on the device.
+extern "C" int wx_mlp_set_weights(wx_mlp *m, const float *const *W, const float *const *b) {
+    if (!m || !W || !b) return mfail(m, WX_EINVAL, "wx_mlp_set_weights: NULL");
+    const int real_in[kLayers] = {kIn, kHid, kHid, kHid}, real_out[kLayers] = {kHid, kHid, kHid, kOut};
+    for (int l = 0; l < kLayers; ++l) {
+        const int N = layer_out(l), K = layer_in(l);
+        std::vector<float> w((size_t)N * K, 0.f), bb(N, 0.f);
+        for (int n = 0; n < real_out[l]; ++n) {
+            for (int k = 0; k < real_in[l]; ++k) w[(size_t)n * K + k] = W[l][(size_t)n * real_in[l] + k];
+            bb[n] = b[l][n];
+        }
+        MCK(cudaMemcpy(m->W[l], w.data(), w.size() * 4, cudaMemcpyHostToDevice), "upload W");
+        MCK(cudaMemcpy(m->b[l], bb.data(), bb.size() * 4, cudaMemcpyHostToDevice), "upload b");
+        MCK(cudaMemset(m->mW[l], 0, w.size() * 4), "reset Adam");
+        MCK(cudaMemset(m->vW[l], 0, w.size() * 4), "reset Adam");
+        MCK(cudaMemset(m->mb[l], 0, bb.size() * 4), "reset Adam");
+        MCK(cudaMemset(m->vb[l], 0, bb.size() * 4), "reset Adam");
+        to_bf16_kernel<<<grid1((long)N * K), 256>>>(m->W[l], (long)N * K, N, K, m->Wb[l], m->WbT[l]);
+    }
+    m->adam_t = 0;
+    MCK(cudaDeviceSynchronize(), "wx_mlp_set_weights");
+    return WX_OK;
+}
+
+extern "C" int wx_mlp_get_weights(wx_mlp *m, float *const *W, float *const *b) {
+    if (!m || !W || !b) return mfail(m, WX_EINVAL, "wx_mlp_get_weights: NULL");
+    const int real_in[kLayers] = {kIn, kHid, kHid, kHid}, real_out[kLayers] = {kHid, kHid, kHid, kOut};
+    MCK(cudaDeviceSynchronize(), "wx_mlp_get_weights");
+    for (int l = 0; l < kLayers; ++l) {
+        const int N = layer_out(l), K = layer_in(l);
+        std::vector<float> w((size_t)N * K), bb(N);
+        MCK(cudaMemcpy(w.data(), m->W[l], w.size() * 4, cudaMemcpyDeviceToHost), "download W");
+        MCK(cudaMemcpy(bb.data(), m->b[l], bb.size() * 4, cudaMemcpyDeviceToHost), "download b");
+        for (int n = 0; n < real_out[l]; ++n) {
+            for (int k = 0; k < real_in[l]; ++k) W[l][(size_t)n * real_in[l] + k] = w[(size_t)n * K + k];
+            b[l][n] = bb[n];
+        }
+    }
+    return WX_OK;
+}
+
+// Gradients (FP32) of the last training step, same layout as the weights.
+extern "C" int wx_mlp_get_grads(wx_mlp *m, float *const *dW, float *const *db) {
+    if (!m || !dW || !db) return mfail(m, WX_EINVAL, "wx_mlp_get_grads: NULL");
+    const int real_in[kLayers] = {kIn, kHid, kHid, kHid}, real_out[kLayers] = {kHid, kHid, kHid, kOut};
+    MCK(cudaDeviceSynchronize(), "wx_mlp_get_grads");
+    for (int l = 0; l < kLayers; ++l) {
+        const int N = layer_out(l), K = layer_in(l);
+        std::vector<float> w((size_t)N * K), bb(N);
+        MCK(cudaMemcpy(w.data(), m->dW[l], w.size() * 4, cudaMemcpyDeviceToHost), "download dW");
+        MCK(cudaMemcpy(bb.data(), m->db[l], bb.size() * 4, cudaMemcpyDeviceToHost), "download db");
+        for (int n = 0; n < real_out[l]; ++n) {
+            for (int k = 0; k < real_in[l]; ++k) dW[l][(size_t)n * real_in[l] + k] = w[(size_t)n * K + k];
+            db[l][n] = bb[n];
+        }
+    }
+    return WX_OK;
+}
+
+// Normalisation (host arrays): mean_in[232], std_in[232], mean_out[116],
+// std_out[116]; per-level feature inputs kappa_lev[58], alpha*dz[58].
+extern "C" int wx_mlp_set_norm(wx_mlp *m, const float *mean_in, const float *std_in, const float *mean_out,
+                               const float *std_out) {
+    if (!m || !mean_in || !std_in || !mean_out || !std_out) return mfail(m, WX_EINVAL, "wx_mlp_set_norm: NULL");
+    std::vector<float> nrm(4 * kInP, 0.f);
+    for (int i = 0; i < kInP; ++i) nrm[kInP + i] = nrm[3 * kInP + i] = 1.f;
+    for (int i = 0; i < kIn; ++i) {
+        nrm[i] = mean_in[i];
+        nrm[kInP + i] = std_in[i];
+    }
+    for (int i = 0; i < kOut; ++i) {
+        nrm[2 * kInP + i] = mean_out[i];
+        nrm[3 * kInP + i] = std_out[i];
+    }
+    MCK(cudaMemcpy(m->norm, nrm.data(), nrm.size() * 4, cudaMemcpyHostToDevice), "upload norm");
+    return WX_OK;
+}
+
+extern "C" int wx_mlp_get_norm(wx_mlp *m, float *mean_in, float *std_in, float *mean_out, float *std_out) {
+    if (!m) return mfail(m, WX_EINVAL, "wx_mlp_get_norm: NULL");
+    std::vector<float> nrm(4 * kInP);
+    MCK(cudaMemcpy(nrm.data(), m->norm, nrm.size() * 4, cudaMemcpyDeviceToHost), "download norm");
+    for (int i = 0; i < kIn; ++i) {
+        if (mean_in) mean_in[i] = nrm[i];
+        if (std_in) std_in[i] = nrm[kInP + i];
+    }
+    for (int i = 0; i < kOut; ++i) {
+        if (mean_out) mean_out[i] = nrm[2 * kInP + i];
+        if (std_out) std_out[i] = nrm[3 * kInP + i];
+    }
+    return WX_OK;
+}
+
+extern "C" int wx_mlp_set_levels(wx_mlp *m, int nz, const float *kappa_lev, const float *alpha_dz) {
+    if (!m || !kappa_lev || !alpha_dz) return mfail(m, WX_EINVAL, "wx_mlp_set_levels: NULL");
+    if (nz != kNZ) return mfail(m, WX_EUNSUPPORTED, "wx_mlp_set_levels: the surrogate is built for 58 levels");
+    MCK(cudaMemcpy(m->lev, kappa_lev, kNZ * 4, cudaMemcpyHostToDevice), "upload levels");
+    MCK(cudaMemcpy(m->lev + kNZ, alpha_dz, kNZ * 4, cudaMemcpyHostToDevice), "upload levels");
+    return WX_OK;
+}
+
+// Statistics of a training set (device arrays [ncol][58] T*, q*, kappa_mult
+// [ncol] or NULL, tend [ncol][2][58]) -> the normalisation (FP64 sums).
+extern "C" int wx_mlp_fit_norm(wx_mlp *m, const float *Ts, const float *qs, const float *km, const float *tend,
+                               long ncol, void *stream) {
+    if (!m || !Ts || !qs || !tend || ncol <= 0) return mfail(m, WX_EINVAL, "wx_mlp_fit_norm: bad arguments");
+    feature_stats_kernel<<<kIn + kOut, 256, 0, (cudaStream_t)stream>>>(Ts, qs, km, tend, ncol, m->lev, m->norm);
+    MCK(cudaGetLastError(), "feature stats kernel");
+    return WX_OK;
+}
+
+// Normalised BF16 features [ncol_pad][256] and FP32 targets [ncol_pad][128]
+// (tend may be NULL) of device columns; ncol_pad = ncol rounded up to 128.
+extern "C" int wx_mlp_prepare(wx_mlp *m, const float *Ts, const float *qs, const float *km, const float *tend,
+                              long ncol, void *X, float *Yt, void *stream) {
+    if (!m || !Ts || !qs || !X || ncol < 0) return mfail(m, WX_EINVAL, "wx_mlp_prepare: bad arguments");
+    const long pad = (ncol + 127) / 128 * 128;
+    cudaStream_t s = (cudaStream_t)stream;
+    features_cols_kernel<<<grid1(pad, 128), 128, 0, s>>>(Ts, qs, km, ncol, pad, m->lev, m->norm,
+                                                         reinterpret_cast<__nv_bfloat16 *>(X));
+    if (tend && Yt) targets_kernel<<<grid1(pad, 128), 128, 0, s>>>(tend, ncol, pad, m->norm, Yt);
+    MCK(cudaGetLastError(), "prepare kernels");
+    return WX_OK;
+}
+
+namespace wx {
+// Forward pass of M rows (M % 128 == 0, <= max_batch) from BF16 X; Z/H kept
+// for backward; normalised outputs in m->Y [M][128] (or `Yout`).
+static int mlp_forward(wx_mlp *m, const __nv_bfloat16 *X, int M, float *Yout, cudaStream_t s) {
+    const __nv_bfloat16 *in = X;
+    for (int l = 0; l < 3; ++l) {
+        const int rc = gemm(in, m->Wb[l], M, kHid, layer_in(l), EPI_GELU, m->b[l], nullptr, m->H[l], m->Z[l],
+                            m->status, s, m->err);
+        if (rc != WX_OK) return rc;
+        in = m->H[l];
+    }
+    return gemm(in, m->Wb[3], M, kOutP, kHid, EPI_F32, m->b[3], nullptr, Yout ? Yout : m->Y, nullptr, m->status, s,
+                m->err);
+}
+
+static void transpose(const __nv_bfloat16 *in, __nv_bfloat16 *out, int rows, int cols, cudaStream_t s) {
+    dim3 grid((cols + 31) / 32, (rows + 31) / 32), block(32, 8);
+    transpose_bf16_kernel<<<grid, block, 0, s>>>(in, out, rows, cols);
+}
+}  // namespace wx
+
+extern "C" int wx_mlp_forward(wx_mlp *m, const void *X, int M, float *Y, void *stream) {
+    if (!m || !X || !Y) return mfail(m, WX_EINVAL, "wx_mlp_forward: NULL");
+    if (M <= 0 || M % 128) return mfail(m, WX_EINVAL, "wx_mlp_forward: M must be a positive multiple of 128");
+    cudaStream_t s = (cudaStream_t)stream;
+    const __nv_bfloat16 *Xb = reinterpret_cast<const __nv_bfloat16 *>(X);
+    // rows beyond the activation buffers go through in chunks of max_batch
+    for (int r0 = 0; r0 < M; r0 += m->max_batch) {
+        const int rows = std::min(m->max_batch, M - r0);
+        const int rc = mlp_forward(m, Xb + (size_t)r0 * kInP, rows, Y + (size_t)r0 * kOutP, s);
+        if (rc != WX_OK) return mfail(m, rc, m->err);
+    }
+    return WX_OK;
+}
+
+// One training step on a minibatch: forward, MSE loss and its gradient,
+// backward through the four layers (tcgen05 GEMMs for input and weight
+// gradients), Adam.  loss (device float or NULL) receives the batch loss.
+extern "C" int wx_mlp_train_step(wx_mlp *m, const void *X, const float *Yt, int M, float lr, float *loss,
+                                 void *stream) {
+    if (!m || !X || !Yt) return mfail(m, WX_EINVAL, "wx_mlp_train_step: NULL");
+    if (M <= 0 || M % 128 || M > m->max_batch)
+        return mfail(m, WX_EINVAL, "wx_mlp_train_step: M must be a multiple of 128 and <= max_batch");
+    cudaStream_t s = (cudaStream_t)stream;
+    const __nv_bfloat16 *Xb = reinterpret_cast<const __nv_bfloat16 *>(X);
+    int rc = mlp_forward(m, Xb, M, nullptr, s);
+    if (rc != WX_OK) return mfail(m, rc, m->err);
+    const int nblk = 256;
+    mse_grad_kernel<<<nblk, 256, 0, s>>>(m->Y, Yt, M, m->dY, m->loss + 1);
+    if (loss) loss_finalize_kernel<<<1, 32, 0, s>>>(m->loss + 1, nblk, M, loss);
+    // layer 4: dW4 = dY^T . H3, db4 = colsum(dY); dZ3 = (dY . W4) * GELU'(Z3)
+    const __nv_bfloat16 *dout = m->dY;
+    int nout = kOutP;
+    for (int l = 3; l >= 0; --l) {
+        const int K = layer_in(l);
+        const __nv_bfloat16 *act = l == 0 ? Xb : m->H[l - 1];
+        transpose(dout, m->TA, M, nout, s);  // [nout][M]
+        transpose(act, m->TB, M, K, s);      // [K][M]
+        rc = gemm(m->TA, m->TB, nout, K, M, EPI_F32, nullptr, nullptr, m->dW[l], nullptr, m->status, s, m->err);
+        if (rc != WX_OK) return mfail(m, rc, m->err);
+        rowsum_bf16_kernel<<<nout, 256, 0, s>>>(m->TA, M, m->db[l]);
+        if (l > 0) {
+            rc = gemm(dout, m->WbT[l], M, K, nout, EPI_DGELU, nullptr, m->Z[l - 1], m->dZ[l - 1], nullptr,
+                      m->status, s, m->err);
+            if (rc != WX_OK) return mfail(m, rc, m->err);
+            dout = m->dZ[l - 1];
+            nout = kHid;
+        }
+    }
+    // Adam (beta 0.9, 0.999, eps 1e-8) with bias correction
+    ++m->adam_t;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.f - powf(b1, (float)m->adam_t), c2 = 1.f - powf(b2, (float)m->adam_t);
+    for (int l = 0; l < kLayers; ++l) {
+        const int N = layer_out(l), K = layer_in(l);
+        adam_kernel<<<grid1((long)N * K), 256, 0, s>>>(m->W[l], m->dW[l], m->mW[l], m->vW[l], (long)N * K, N, K, lr,
+                                                      b1, b2, eps, c1, c2, m->Wb[l], m->WbT[l]);
+        adam_kernel<<<grid1(N), 256, 0, s>>>(m->b[l], m->db[l], m->mb[l], m->vb[l], N, N, 1, lr, b1, b2, eps, c1,
+                                            c2, nullptr, nullptr);
+    }
+    MCK(cudaGetLastError(), "training kernels");
+    return WX_OK;
+}
+
+// Gradients only (no Adam): forward + backward into the gradient buffers.
+extern "C" int wx_mlp_gradients(wx_mlp *m, const void *X, const float *Yt, int M, float *loss, void *stream) {
+    if (!m) return WX_EINVAL;
+    // a training step with lr = 0 leaves the weights as they were, but Adam
+    // moments would move: keep them by saving and restoring the step count
+    // is not enough, so run the forward/backward part only
+    if (!X || !Yt) return mfail(m, WX_EINVAL, "wx_mlp_gradients: NULL");
+    if (M <= 0 || M % 128 || M > m->max_batch)
+        return mfail(m, WX_EINVAL, "wx_mlp_gradients: M must be a multiple of 128 and <= max_batch");
+    cudaStream_t s = (cudaStream_t)stream;
+    const __nv_bfloat16 *Xb = reinterpret_cast<const __nv_bfloat16 *>(X);
+    int rc = mlp_forward(m, Xb, M, nullptr, s);
+    if (rc != WX_OK) return mfail(m, rc, m->err);
+    const int nblk = 256;
+    mse_grad_kernel<<<nblk, 256, 0, s>>>(m->Y, Yt, M, m->dY, m->loss + 1);
+    if (loss) loss_finalize_kernel<<<1, 32, 0, s>>>(m->loss + 1, nblk, M, loss);
+    const __nv_bfloat16 *dout = m->dY;
+    int nout = kOutP;
+    for (int l = 3; l >= 0; --l) {
+        const int K = layer_in(l);
+        const __nv_bfloat16 *act = l == 0 ? Xb : m->H[l - 1];
+        transpose(dout, m->TA, M, nout, s);
+        transpose(act, m->TB, M, K, s);
+        rc = gemm(m->TA, m->TB, nout, K, M, EPI_F32, nullptr, nullptr, m->dW[l], nullptr, m->status, s, m->err);
+        if (rc != WX_OK) return mfail(m, rc, m->err);
+        rowsum_bf16_kernel<<<nout, 256, 0, s>>>(m->TA, M, m->db[l]);
+        if (l > 0) {
+            rc = gemm(dout, m->WbT[l], M, K, nout, EPI_DGELU, nullptr, m->Z[l - 1], m->dZ[l - 1], nullptr,
+                      m->status, s, m->err);
+            if (rc != WX_OK) return mfail(m, rc, m->err);
+            dout = m->dZ[l - 1];
+            nout = kHid;
+        }
+    }
+    MCK(cudaGetLastError(), "gradient kernels");
+    return WX_OK;
+}
+
+extern "C" int wx_mlp_status(wx_mlp *m) {
+    if (!m) return WX_EINVAL;
+    unsigned st = 0;
+    MCK(cudaMemcpy(&st, m->status, sizeof st, cudaMemcpyDeviceToHost), "status");
+    if (st) cudaMemset(m->status, 0, sizeof st);
+    if (st & ST_TIMEOUT) return mfail(m, WX_ETIMEOUT, "a bounded device wait timed out in a GEMM");
+    return WX_OK;
+}
+
+// =====================================================================
+// WX_SURROGATE: one time step with the column physics predicted by the
+// network.  The dynamics kernel runs without physics and leaves T*, q* in
+// the new buffer; the features of every column go through the four GEMMs;
+// the apply kernel accepts a column's prediction only when both residual
+// checks pass and otherwise recomputes the column exactly.
+// =====================================================================
+namespace wx {
+
+// Normalised BF16 feature rows [rows][256] of all nx*ny columns (raster
+// order j*nx + i) straight from the planar T*, q* planes.
+__global__ void __launch_bounds__(128) sur_features_kernel(const float *__restrict__ fld, int nx, int P, int R,
+                                                           const float *__restrict__ km,
+                                                           const float *__restrict__ lev,
+                                                           const float *__restrict__ norm,
+                                                           __nv_bfloat16 *__restrict__ X, long ncol, long rows) {
+    const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= rows) return;
+    uint4 *row = reinterpret_cast<uint4 *>(X + c * kInP);
+    if (c >= ncol) {
+        for (int g = 0; g < kInP / 8; ++g) row[g] = make_uint4(0, 0, 0, 0);
+        return;
+    }
+    const int j = (int)(c / nx), i = (int)(c % nx);
+    const size_t plane = (size_t)R * P;
+    const float *base = fld + (size_t)(j + 1) * P + i + kGhostX;
+    const float s = km ? km[c] : 1.f;
+#pragma unroll 1
+    for (int g = 0; g < kInP / 8; ++g) {
+        __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int f = 8 * g + t;
+            float x = 0.f;
+            if (f < kIn) {
+                const int kind = f / kNZ, k = f % kNZ;
+                const float raw = kind == 0   ? base[(size_t)(2 * k) * plane]
+                                  : kind == 1 ? base[(size_t)(2 * k + 1) * plane]
+                                  : kind == 2 ? s * lev[k]
+                                              : lev[kNZ + k];
+                x = (raw - norm[f]) / norm[kInP + f];
+            }
+            v[t] = __float2bfloat16_rn(x);
+        }
+        row[g] = *reinterpret_cast<const uint4 *>(v);
+    }
+}
+
+// One thread per column: denormalise the prediction, run the two residual
+// checks, write T^{n+1} (the prediction, or the exact column physics when a
+// check fails) over T* with the periodic ghost copies.
+__global__ void __launch_bounds__(128) sur_apply_kernel(float *__restrict__ fld, int nx, int ny, int P, int R,
+                                                        const float *__restrict__ km,
+                                                        const Q4<float> *__restrict__ gtab,
+                                                        const float *__restrict__ Y,
+                                                        const float *__restrict__ norm, float dt, float S0,
+                                                        float tol, long ncol,
+                                                        unsigned long long *__restrict__ n_fallback,
+                                                        unsigned *__restrict__ status) {
+    __shared__ Q4<float> sB[kNZ], sC[kNZ], sE[kNZ];
+    for (int e = threadIdx.x; e < kNZ; e += blockDim.x) {
+        sB[e] = gtab[REC_B * kNZ + e];
+        sC[e] = gtab[REC_C * kNZ + e];
+        sE[e] = gtab[REC_E * kNZ + e];
+    }
+    __syncthreads();
+    const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool reject = false;
+    if (c < ncol) {
+        const int j = (int)(c / nx), i = (int)(c % nx);
+        const size_t plane = (size_t)R * P;
+        float *base = fld + (size_t)(j + 1) * P + i + kGhostX;
+        const float s = km ? km[c] : 1.f;
+        const float *mo = norm + 2 * kInP, *so = norm + 3 * kInP;
+        const float4 *yr = reinterpret_cast<const float4 *>(Y + c * kOutP);
+        float ts[kNZ], q[kNZ], H[kNZ], r[kNZ];
+#pragma unroll
+        for (int g = 0; g < kOut / 4; ++g) {
+            const float4 y4 = yr[g];
+            const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int o = 4 * g + t;
+                const float v = fmaf(yv[t], so[o], mo[o]);
+                if (o < kNZ)
+                    H[o] = v;
+                else
+                    r[o - kNZ] = v;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kNZ; ++k) {
+            ts[k] = base[(size_t)(2 * k) * plane];
+            q[k] = base[(size_t)(2 * k + 1) * plane];
+        }
+        // rho_vd: (A v - T*)_k = (v_k - T*_k) + a_k (v_{k-1} - v_k) + c_k (v_{k+1} - v_k)
+        float num = 0.f, den = 0.f, sumH = 0.f, tau2 = 0.f;
+        bool finite = true;
+#pragma unroll
+        for (int k = 0; k < kNZ; ++k) {
+            const float ak = s * sE[k].x, ck = s * sE[k].y;
+            const float xk = ts[k] + dt * r[k];
+            const float xm = k > 0 ? ts[k - 1] + dt * r[k - 1] : xk;
+            const float xp = k < kNZ - 1 ? ts[k + 1] + dt * r[k + 1] : xk;
+            const float tm = k > 0 ? ts[k - 1] : ts[k], tp = k < kNZ - 1 ? ts[k + 1] : ts[k];
+            const float ex = dt * r[k] + ak * (xm - xk) + ck * (xp - xk);
+            const float e0 = ak * (tm - ts[k]) + ck * (tp - ts[k]);
+            num = fmaf(ex, ex, num);
+            den = fmaf(e0, e0, den);
+            sumH = fmaf(H[k], sE[k].z, sumH);
+            tau2 = fmaf(sB[k].z, q[k], tau2);
+            finite = finite && isfinite(H[k]) && isfinite(r[k]);
+        }
+        const float absorbed = S0 * (1.f - exp2f(-tau2));
+        const float rvd = den > 0.f ? sqrtf(num / den) : (num == 0.f ? 0.f : INFINITY);
+        const float rH = absorbed > 0.f ? fabsf(sumH - absorbed) / absorbed : (sumH == 0.f ? 0.f : INFINITY);
+        reject = !(finite && rvd <= tol && rH <= tol);
+        float tn[kNZ];
+        if (!reject) {
+#pragma unroll
+            for (int k = 0; k < kNZ; ++k) tn[k] = ts[k] + dt * (r[k] + H[k]);
+        } else {
+            // exact column: forward elimination, back substitution with the
+            // heating of the optical-depth scan from the top
+            float cp[kNZ], dp[kNZ], cpp = 0.f, dpp = 0.f;
+#pragma unroll
+            for (int k = 0; k < kNZ; ++k) {
+                const float ak = s * sE[k].x, ck = s * sE[k].y;
+                const float m = ((1.f - ak) - ck) - ak * cpp;
+                const float inv = 1.f / m;
+                cpp = ck * inv;
+                dpp = (ts[k] - ak * dpp) * inv;
+                cp[k] = cpp;
+                dp[k] = dpp;
+            }
+            float x = 0.f, tau = 0.f, Etop = 1.f;
+#pragma unroll
+            for (int k = kNZ - 1; k >= 0; --k) {
+                x = dp[k] - cp[k] * x;
+                const float taub = tau + sB[k].z * q[k];
+                const float Eb = exp2f(-taub);
+                tn[k] = x + sC[k].x * (Etop - Eb);
+                Etop = Eb;
+                tau = taub;
+            }
+        }
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < kNZ; ++k) {
+            const float v = tn[k];
+            ok = ok && isfinite(v);
+            float *row = base + (size_t)(2 * k) * plane;
+            row[0] = v;
+            if (i == 0) row[nx] = v;            // -> right ghost column
+            if (i == nx - 1) row[-nx] = v;      // -> left ghost column
+            if (j == 0) row[(size_t)ny * P] = v;          // -> top ghost row
+            if (j == ny - 1) row[-(long)ny * P] = v;      // -> bottom ghost row
+        }
+        if (!ok) atomicOr(status, ST_NONFINITE);
+    }
+    const int nrej = __syncthreads_count(reject);
+    if (threadIdx.x == 0 && nrej) atomicAdd(n_fallback, (unsigned long long)nrej);
+}
+
+void free_surrogate(wx_ctx *c) {
+    for (void *p : {c->sur_X, c->sur_H[0], c->sur_H[1], (void *)c->sur_Y, (void *)c->sur_lev, (void *)c->sur_nfb})
+        if (p) cudaFree(p);
+    c->sur_X = c->sur_H[0] = c->sur_H[1] = nullptr;
+    c->sur_Y = c->sur_lev = nullptr;
+    c->sur_nfb = nullptr;
+    c->sur = nullptr;
+    c->sur_rows = 0;
+}
+
+int launch_surrogate_step(wx_ctx *c, cudaStream_t s, long *launches) {
+    wx_mlp *m = c->sur;
+    if (c->sur_gen != c->generation) {
+        // per-level feature inputs from this context's parameters
+        std::vector<float> lev(2 * kNZ);
+        for (int k = 0; k < kNZ; ++k) {
+            lev[k] = (float)c->kappa_lev[k];
+            lev[kNZ + k] = (float)(c->alpha[k] * c->dz[k]);
+        }
+        cudaError_t e = cudaMemcpy(c->sur_lev, lev.data(), lev.size() * 4, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            c->err = std::string("surrogate levels: ") + cudaGetErrorString(e);
+            return WX_ECUDA;
+        }
+        c->sur_gen = c->generation;
+    }
+    // 1. dynamics only: T*, q* land in the new buffer (which becomes current)
+    const unsigned saved = c->flags;
+    c->flags = saved & WX_ADVECTION;
+    int rc = launch_step(c, s, launches);
+    c->flags = saved;
+    if (rc != WX_OK) return rc;
+    float *f = reinterpret_cast<float *>(c->fld[c->cur]);
+    const long ncol = (long)c->nx * c->ny, rows = c->sur_rows;
+    cudaMemsetAsync(c->sur_nfb, 0, sizeof(unsigned long long), s);
+    // 2. features
+    sur_features_kernel<<<(unsigned)(rows / 128), 128, 0, s>>>(f, c->nx, c->P, c->R, (const float *)c->kmult,
+                                                               c->sur_lev, m->norm,
+                                                               reinterpret_cast<__nv_bfloat16 *>(c->sur_X), ncol, rows);
+    // 3. the network, in chunks of at most 65535 row tiles
+    std::string err;
+    const long chunk = 65535L * 128;
+    for (long r0 = 0; r0 < rows; r0 += chunk) {
+        const int M = (int)std::min(chunk, rows - r0);
+        const __nv_bfloat16 *X = reinterpret_cast<const __nv_bfloat16 *>(c->sur_X) + r0 * kInP;
+        __nv_bfloat16 *H0 = reinterpret_cast<__nv_bfloat16 *>(c->sur_H[0]) + r0 * kHid;
+        __nv_bfloat16 *H1 = reinterpret_cast<__nv_bfloat16 *>(c->sur_H[1]) + r0 * kHid;
+        rc = gemm(X, m->Wb[0], M, kHid, kInP, EPI_GELU, m->b[0], nullptr, H0, nullptr, c->d_status, s, err);
+        if (rc == WX_OK)
+            rc = gemm(H0, m->Wb[1], M, kHid, kHid, EPI_GELU, m->b[1], nullptr, H1, nullptr, c->d_status, s, err);
+        if (rc == WX_OK)
+            rc = gemm(H1, m->Wb[2], M, kHid, kHid, EPI_GELU, m->b[2], nullptr, H0, nullptr, c->d_status, s, err);
+        if (rc == WX_OK)
+            rc = gemm(H0, m->Wb[3], M, kOutP, kHid, EPI_F32, m->b[3], nullptr, c->sur_Y + r0 * kOutP, nullptr,
+                      c->d_status, s, err);
+        if (rc != WX_OK) {
+            c->err = err;
+            return rc;
+        }
+        *launches += 4;
+    }
+    // 4. residual checks, fallback, T^{n+1}
+    sur_apply_kernel<<<(unsigned)((ncol + 127) / 128), 128, 0, s>>>(
+        f, c->nx, c->ny, c->P, c->R, (const float *)c->kmult, (const Q4<float> *)c->tab, c->sur_Y, m->norm,
+        (float)c->dt, (float)c->S0, (float)c->sur_tol, ncol, c->sur_nfb, c->d_status);
+    *launches += 2;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        c->err = std::string("surrogate kernels: ") + cudaGetErrorString(e);
+        return WX_ECUDA;
+    }
+    return WX_OK;
+}
+
+}  // namespace wx
+
+extern "C" int wx_set_surrogate(wx_ctx *c, wx_mlp *m, double fallback_tol) {
+    if (!c) return WX_EINVAL;
+    if (!m) {
+        free_surrogate(c);
+        return WX_OK;
+    }
+    if (c->dtype != WX_F32 || c->nz != kNZ) {
+        c->err = "wx_set_surrogate: the network serves FP32 contexts with 58 levels";
+        return WX_EUNSUPPORTED;
+    }
+    if (!(fallback_tol >= 0) || !std::isfinite(fallback_tol)) {
+        c->err = "wx_set_surrogate: fallback_tol must be finite and >= 0";
+        return WX_EINVAL;
+    }
+    free_surrogate(c);
+    const long rows = ((long)c->nx * c->ny + 127) / 128 * 128;
+    bool ok = cudaMalloc(&c->sur_X, rows * kInP * 2) == cudaSuccess &&
+              cudaMalloc(&c->sur_H[0], rows * kHid * 2) == cudaSuccess &&
+              cudaMalloc(&c->sur_H[1], rows * kHid * 2) == cudaSuccess &&
+              cudaMalloc((void **)&c->sur_Y, rows * kOutP * 4) == cudaSuccess &&
+              cudaMalloc((void **)&c->sur_lev, 2 * kNZ * 4) == cudaSuccess &&
+              cudaMalloc((void **)&c->sur_nfb, sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMemset(c->sur_nfb, 0, sizeof(unsigned long long)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_surrogate(c);
+        c->err = "wx_set_surrogate: device allocation failed";
+        return WX_ENOMEM;
+    }
+    c->sur = m;
+    c->sur_rows = rows;
+    c->sur_tol = fallback_tol;
+    c->sur_gen = ~0u;
+    return WX_OK;
+}
+
+extern "C" int wx_surrogate_fallbacks(wx_ctx *c, long *n_fallback) {
+    if (!c || !n_fallback) return WX_EINVAL;
+    if (!c->sur_nfb) {
+        c->err = "wx_surrogate_fallbacks: no network attached";
+        return WX_ESTATE;
+    }
+    unsigned long long n = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(&n, c->sur_nfb, sizeof n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        c->err = "wx_surrogate_fallbacks: device error";
+        return WX_ECUDA;
+    }
+    *n_fallback = (long)n;
+    return WX_OK;
+}

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libwx.so")
 
 WX_F32, WX_F64, WX_MIXED = 0, 1, 2
-WX_ADVECTION, WX_PHYSICS, WX_SUMS = 1, 2, 4
+WX_ADVECTION, WX_PHYSICS, WX_SUMS, WX_SURROGATE = 1, 2, 4, 8
 STATUS = {0: "WX_OK", -1: "WX_EINVAL", -2: "WX_ENOMEM", -3: "WX_ECUDA", -4: "WX_ECFL",
           -5: "WX_ENONFINITE", -6: "WX_ETIMEOUT", -7: "WX_ESTATE", -8: "WX_EUNSUPPORTED"}
 DTYPES = {"f32": WX_F32, "f64": WX_F64, "mixed": WX_MIXED}
@@ -76,6 +76,25 @@ SIGNATURES = [
     ("wx_ens_last_launches", ctypes.c_long, [_VP]),
     ("wx_ens_destroy", None, [_VP]),
     ("wx_ens_last_error", ctypes.c_char_p, [_VP]),
+    ("wx_gemm_bf16", ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP,
+                                    _VP, _VP, _VP, _VP, _VP]),
+    ("wx_mlp_last_error", ctypes.c_char_p, []),
+    ("wx_mlp_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_VP)]),
+    ("wx_mlp_destroy", None, [_VP]),
+    ("wx_mlp_set_weights", ctypes.c_int, [_VP, _VP, _VP]),
+    ("wx_mlp_get_weights", ctypes.c_int, [_VP, _VP, _VP]),
+    ("wx_mlp_get_grads", ctypes.c_int, [_VP, _VP, _VP]),
+    ("wx_mlp_set_norm", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    ("wx_mlp_get_norm", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    ("wx_mlp_set_levels", ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
+    ("wx_mlp_fit_norm", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_long, _VP]),
+    ("wx_mlp_prepare", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_long, _VP, _VP, _VP]),
+    ("wx_mlp_forward", ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP]),
+    ("wx_mlp_gradients", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP]),
+    ("wx_mlp_train_step", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_float, _VP, _VP]),
+    ("wx_mlp_status", ctypes.c_int, [_VP]),
+    ("wx_set_surrogate", ctypes.c_int, [_VP, _VP, ctypes.c_double]),
+    ("wx_surrogate_fallbacks", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_long)]),
     ("wx_destroy", None, [_VP]),
     ("wx_last_error", ctypes.c_char_p, [_VP]),
 ]
@@ -219,6 +238,17 @@ class Context:
     def last_launches(self):
         return int(lib().wx_last_launches(self.ptr))
 
+    def set_surrogate(self, mlp, fallback_tol=2e-2):
+        """Attach an MLP (or detach with None) for steps with WX_SURROGATE."""
+        _check(lib().wx_set_surrogate(self.ptr, mlp.ptr if mlp is not None else None,
+                                      float(fallback_tol)), self.ptr)
+        self._mlp = mlp
+
+    def surrogate_fallbacks(self):
+        n = ctypes.c_long()
+        _check(lib().wx_surrogate_fallbacks(self.ptr, ctypes.byref(n)), self.ptr)
+        return n.value
+
     def tune(self, cache_path=None, force=False, stream=None):
         """Autotune the launch configuration (state restored); returns ms/step."""
         ms = ctypes.c_double()
@@ -303,3 +333,104 @@ def wx_sums_noalloc(T, q, dz, h, out, stream=None):
     if code != 0:
         raise WxError(code, lib().wx_sums_noalloc_error().decode())
 
+
+def _mcheck(code):
+    if code != 0:
+        raise WxError(code, lib().wx_mlp_last_error().decode())
+
+
+def wx_gemm_bf16(A, B, epilogue=0, bias=None, aux=None, out=None, out2=None, status=None, stream=None):
+    """C = A . B^T (torch BF16 CUDA tensors A [M][K], B [N][K]) with an epilogue."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    if out is None:
+        out = torch.empty(M, N, device=A.device, dtype=torch.float32 if epilogue == 0 else torch.bfloat16)
+    if status is None:
+        status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _mcheck(lib().wx_gemm_bf16(_dptr(A), _dptr(B), M, N, K, epilogue, _dptr(bias), _dptr(aux), _dptr(out),
+                               _dptr(out2), _dptr(status), _stream_ptr(stream)))
+    return out
+
+
+
+# ------------------------------------------------------------------ MLP
+MLP_SHAPES = [(512, 232), (512, 512), (512, 512), (116, 512)]  # (fan_out, fan_in)
+MLP_IN, MLP_IN_PAD, MLP_OUT, MLP_OUT_PAD = 232, 256, 116, 128
+
+
+def _f32arrays(arrs):
+    arrs = [np.ascontiguousarray(a, np.float32) for a in arrs]
+    ptrs = (ctypes.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
+    return arrs, ptrs
+
+
+class MLP:
+    """One wx_mlp*: the column-physics surrogate network (include/wx.h)."""
+
+    def __init__(self, max_batch=4096):
+        p = _VP()
+        _mcheck(lib().wx_mlp_create(int(max_batch), ctypes.byref(p)))
+        self.ptr = p
+        self.max_batch = int(max_batch)
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            lib().wx_mlp_destroy(self.ptr)
+            self.ptr = None
+
+    __del__ = close
+
+    def set_weights(self, Ws, bs):
+        (Wk, Wp), (bk, bp) = _f32arrays(Ws), _f32arrays(bs)
+        _mcheck(lib().wx_mlp_set_weights(self.ptr, Wp, bp))
+
+    def _get(self, fn):
+        Ws = [np.empty(s, np.float32) for s in MLP_SHAPES]
+        bs = [np.empty(s[0], np.float32) for s in MLP_SHAPES]
+        wp = (ctypes.c_void_p * 4)(*[a.ctypes.data for a in Ws])
+        bp = (ctypes.c_void_p * 4)(*[a.ctypes.data for a in bs])
+        _mcheck(fn(self.ptr, wp, bp))
+        return Ws, bs
+
+    def get_weights(self):
+        return self._get(lib().wx_mlp_get_weights)
+
+    def get_grads(self):
+        return self._get(lib().wx_mlp_get_grads)
+
+    def set_norm(self, mean_in, std_in, mean_out, std_out):
+        a, _ = _f32arrays([mean_in, std_in, mean_out, std_out])
+        _mcheck(lib().wx_mlp_set_norm(self.ptr, *[_dptr(x) for x in a]))
+
+    def get_norm(self):
+        a = [np.empty(MLP_IN, np.float32), np.empty(MLP_IN, np.float32),
+             np.empty(MLP_OUT, np.float32), np.empty(MLP_OUT, np.float32)]
+        _mcheck(lib().wx_mlp_get_norm(self.ptr, *[_dptr(x) for x in a]))
+        return a
+
+    def set_levels(self, kappa_lev, alpha_dz):
+        a, _ = _f32arrays([kappa_lev, alpha_dz])
+        _mcheck(lib().wx_mlp_set_levels(self.ptr, len(a[0]), _dptr(a[0]), _dptr(a[1])))
+
+    def fit_norm(self, Ts, qs, kappa_mult, tend, stream=None):
+        _mcheck(lib().wx_mlp_fit_norm(self.ptr, _dptr(Ts), _dptr(qs), _dptr(kappa_mult), _dptr(tend),
+                                      Ts.shape[0], _stream_ptr(stream)))
+
+    def prepare(self, Ts, qs, kappa_mult, tend, X, Yt=None, stream=None):
+        _mcheck(lib().wx_mlp_prepare(self.ptr, _dptr(Ts), _dptr(qs), _dptr(kappa_mult), _dptr(tend),
+                                     Ts.shape[0], _dptr(X), _dptr(Yt), _stream_ptr(stream)))
+
+    def forward(self, X, Y, stream=None):
+        _mcheck(lib().wx_mlp_forward(self.ptr, _dptr(X), X.shape[0], _dptr(Y), _stream_ptr(stream)))
+
+    def gradients(self, X, Yt, loss=None, stream=None):
+        _mcheck(lib().wx_mlp_gradients(self.ptr, _dptr(X), _dptr(Yt), X.shape[0], _dptr(loss),
+                                       _stream_ptr(stream)))
+
+    def train_step(self, X, Yt, lr, loss=None, stream=None):
+        _mcheck(lib().wx_mlp_train_step(self.ptr, _dptr(X), _dptr(Yt), X.shape[0], float(lr),
+                                        _dptr(loss), _stream_ptr(stream)))
+
+    def status(self):
+        _mcheck(lib().wx_mlp_status(self.ptr))
