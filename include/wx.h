@@ -269,9 +269,11 @@ const char *wx_mlp_last_error(void);
  * alpha_k dz_k] (k = 0..57, bottom first) are normalised per feature;
  * outputs y = [H_k | (T**_k - T*_k)/dt] likewise, where T** is the implicit
  * vertical diffusion's result and H the radiative heating (Sec. 3.1's
- * column physics, Eq. 1).  On the device, normalised inputs are BF16 rows
- * of 256 (232 used, zero padding) and outputs FP32 rows of 128 (116 used);
- * row counts are multiples of 128. */
+ * column physics, Eq. 1).  On the device, a normalised input row is 512
+ * BF16 values: the two-term expansion x = hi + lo of every feature,
+ * hi = bf16(x) in [0, 232) and lo = bf16(x - hi) in [256, 488), zeros
+ * elsewhere; the first layer applies its weights to both halves.  Outputs
+ * are FP32 rows of 128 (116 used).  Row counts are multiples of 128. */
 typedef struct wx_mlp wx_mlp;
 /* Allocate a network whose training and activation buffers hold max_batch
  * rows (multiple of 128); weights zero, normalisation identity. */
@@ -300,13 +302,13 @@ int wx_mlp_set_levels(wx_mlp *m, int nz, const float *kappa_lev,
 int wx_mlp_fit_norm(wx_mlp *m, const float *Ts, const float *qs,
                     const float *kappa_mult, const float *tend, long ncol,
                     void *cuda_stream);
-/* Normalised BF16 input rows X [ceil128(ncol)][256] and, when tend and Yt
+/* Normalised BF16 input rows X [ceil128(ncol)][512] and, when tend and Yt
  * are given, FP32 target rows Yt [ceil128(ncol)][128] of device columns
  * (padding rows zero).  Asynchronous. */
 int wx_mlp_prepare(wx_mlp *m, const float *Ts, const float *qs,
                    const float *kappa_mult, const float *tend, long ncol,
                    void *X, float *Yt, void *cuda_stream);
-/* Normalised outputs Y [M][128] (FP32) of BF16 rows X [M][256]; any M that
+/* Normalised outputs Y [M][128] (FP32) of BF16 rows X [M][512]; any M that
  * is a multiple of 128 (processed in chunks of max_batch). */
 int wx_mlp_forward(wx_mlp *m, const void *X, int M, float *Y,
                    void *cuda_stream);

@@ -16,10 +16,12 @@ with inputs and targets normalised per feature, mean-squared-error loss and
 Adam.  GELU is the exact erf form 0.5 z (1 + erf(z / sqrt 2)), evaluated by
 calling ``scipy.special.erf``.
 
-``forward(..., bf16=True)`` rounds the weights, the normalised inputs and
-each hidden activation to bfloat16 (round to nearest even, as the tensor-core
-path stores them) and accumulates in FP64; ``bf16=False`` is the plain FP64
-network used by the finite-difference pin.  ``backward`` is full FP64.
+``forward(..., bf16=True)`` rounds the weights and each hidden activation to
+bfloat16 (round to nearest even, as the tensor-core path stores them), takes
+each normalised input (held in FP32) as its two-term bfloat16 expansion
+hi + lo, hi = bf16(x), lo = bf16(x - hi), and accumulates in FP64;
+``bf16=False`` is the plain FP64 network used by the finite-difference pin.
+``backward`` is full FP64.
 """
 from __future__ import annotations
 
@@ -46,6 +48,14 @@ def bf16(x) -> np.ndarray:
     return out
 
 
+def bf16_pair(x):
+    """Two-term bfloat16 expansion (hi, lo) of FP32(x): hi = bf16(x),
+    lo = bf16(x - hi); x - hi is exact in FP32."""
+    f = np.asarray(x, dtype=np.float32).astype(np.float64)
+    hi = bf16(f)
+    return hi, bf16(f - hi)
+
+
 # --------------------------------------------------------------- network
 def gelu(z):
     return 0.5 * z * (1.0 + erf(z * SQRT_HALF))
@@ -59,7 +69,11 @@ def gelu_grad(z):
 def forward(Ws, bs, X, bf16_path: bool = True):
     """X [M][232] normalised inputs -> (Y [M][116], cache for backward)."""
     rnd = bf16 if bf16_path else (lambda a: np.asarray(a, dtype=np.float64))
-    h = rnd(X)
+    if bf16_path:
+        hi, lo = bf16_pair(X)
+        h = hi + lo
+    else:
+        h = np.asarray(X, dtype=np.float64)
     cache = {"a": [h], "z": []}
     for l in range(4):
         z = h @ rnd(Ws[l]).T + np.asarray(bs[l], dtype=np.float64)

@@ -328,8 +328,15 @@ extern "C" int wx_gemm_bf16(const void *A, const void *B, int M, int N, int K, i
 namespace wx {
 
 constexpr int kNZ = 58, kIn = 4 * kNZ, kInP = 256, kHid = 512, kOut = 2 * kNZ, kOutP = 128;
+// Input rows carry each normalised feature as a two-term BF16 expansion
+// x ~ hi + lo (hi = bf16(x), lo = bf16(x - hi)): [hi (256) | lo (256)].  The
+// first layer multiplies both halves by the same weights, so its products
+// see the input to ~16 significant bits instead of BF16's 8.
+constexpr int kXW = 2 * kInP;
 constexpr int kLayers = 4;
 __host__ __device__ constexpr int layer_in(int l) { return l == 0 ? kInP : kHid; }
+// K of the layer's forward GEMM (the first layer runs over both halves)
+__host__ __device__ constexpr int layer_k(int l) { return l == 0 ? kXW : kHid; }
 __host__ __device__ constexpr int layer_out(int l) { return l == 3 ? kOutP : kHid; }
 
 }  // namespace wx
@@ -354,12 +361,12 @@ namespace wx {
 
 // ------------------------------------------------------------ small kernels
 __global__ void transpose_bf16_kernel(const __nv_bfloat16 *__restrict__ in, __nv_bfloat16 *__restrict__ out,
-                                      int rows, int cols) {
+                                      int rows, int cols, int ld) {
     __shared__ __nv_bfloat16 t[32][33];
     const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
     for (int y = threadIdx.y; y < 32; y += blockDim.y) {
         const int r = r0 + y, c = c0 + threadIdx.x;
-        if (r < rows && c < cols) t[y][threadIdx.x] = in[(size_t)r * cols + c];
+        if (r < rows && c < cols) t[y][threadIdx.x] = in[(size_t)r * ld + c];
     }
     __syncthreads();
     for (int y = threadIdx.y; y < 32; y += blockDim.y) {
@@ -417,11 +424,27 @@ __global__ void loss_finalize_kernel(const float *__restrict__ part, int n, int 
     out[0] = (float)(s / ((double)M * kOut));
 }
 
-// Adam (beta1, beta2, eps) on FP32 masters, then the BF16 copies [N][K] and
-// [K][N] (the latter feeds the input-gradient GEMM).
+// BF16 copies of master element e = (n, k) of an [N][K] matrix: pb [N][K],
+// or [N][2K] with the row written twice for the first layer (dup); pbT
+// [K][N] (feeds the input-gradient GEMM) unless NULL.
+__device__ __forceinline__ void store_copies(float v, long e, int N, int K, int dup, __nv_bfloat16 *pb,
+                                             __nv_bfloat16 *pbT) {
+    const __nv_bfloat16 q = __float2bfloat16_rn(v);
+    const int nn = (int)(e / K), kk = (int)(e % K);
+    if (dup) {
+        pb[(size_t)nn * 2 * K + kk] = q;
+        pb[(size_t)nn * 2 * K + K + kk] = q;
+    } else {
+        pb[e] = q;
+    }
+    if (pbT) pbT[(size_t)kk * N + nn] = q;
+}
+
+// Adam (beta1, beta2, eps) on FP32 masters, then the BF16 copies.
 __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
                             float *__restrict__ v, long n, int N, int K, float lr, float b1, float b2, float eps,
-                            float c1, float c2, __nv_bfloat16 *__restrict__ pb, __nv_bfloat16 *__restrict__ pbT) {
+                            float c1, float c2, int dup, __nv_bfloat16 *__restrict__ pb,
+                            __nv_bfloat16 *__restrict__ pbT) {
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
         const float gi = g[e];
         const float mi = b1 * m[e] + (1.f - b1) * gi;
@@ -430,22 +453,14 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, 
         v[e] = vi;
         const float pi = p[e] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
         p[e] = pi;
-        if (pb) {
-            const __nv_bfloat16 q = __float2bfloat16_rn(pi);
-            pb[e] = q;
-            const int nn = (int)(e / K), kk = (int)(e % K);
-            pbT[(size_t)kk * N + nn] = q;
-        }
+        if (pb) store_copies(pi, e, N, K, dup, pb, pbT);
     }
 }
 
-__global__ void to_bf16_kernel(const float *__restrict__ p, long n, int N, int K, __nv_bfloat16 *__restrict__ pb,
-                               __nv_bfloat16 *__restrict__ pbT) {
-    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
-        const __nv_bfloat16 q = __float2bfloat16_rn(p[e]);
-        pb[e] = q;
-        pbT[(size_t)(e % K) * N + (e / K)] = q;
-    }
+__global__ void to_bf16_kernel(const float *__restrict__ p, long n, int N, int K, int dup,
+                               __nv_bfloat16 *__restrict__ pb, __nv_bfloat16 *__restrict__ pbT) {
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+        store_copies(p[e], e, N, K, dup, pb, pbT);
 }
 
 // Features of ncol columns given as [ncol][nz] arrays (T*, q*), kappa_mult
@@ -456,9 +471,9 @@ __global__ void features_cols_kernel(const float *__restrict__ Ts, const float *
                                      __nv_bfloat16 *__restrict__ X) {
     const long col = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= ncol_pad) return;
-    __nv_bfloat16 *row = X + col * kInP;
+    __nv_bfloat16 *row = X + col * kXW;
     if (col >= ncol) {
-        for (int f = 0; f < kInP; ++f) row[f] = __float2bfloat16_rn(0.f);
+        for (int f = 0; f < kXW; ++f) row[f] = __float2bfloat16_rn(0.f);
         return;
     }
     const float s = km ? km[col] : 1.f;
@@ -472,7 +487,9 @@ __global__ void features_cols_kernel(const float *__restrict__ Ts, const float *
                                           : lev[kNZ + k];
             x = (raw - norm[f]) / norm[kInP + f];
         }
-        row[f] = __float2bfloat16_rn(x);
+        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+        row[f] = hi;
+        row[kInP + f] = __float2bfloat16_rn(x - __bfloat162float(hi));
     }
 }
 
@@ -583,7 +600,8 @@ extern "C" int wx_mlp_create(int max_batch, wx_mlp **out) {
     for (int l = 0; l < kLayers && ok; ++l) {
         const size_t nk = (size_t)layer_out(l) * layer_in(l), n = layer_out(l);
         ok = alloc((void **)&m->W[l], nk * 4) && alloc((void **)&m->b[l], n * 4) &&
-             alloc((void **)&m->Wb[l], nk * 2) && alloc((void **)&m->WbT[l], nk * 2) &&
+             alloc((void **)&m->Wb[l], (size_t)layer_out(l) * layer_k(l) * 2) &&
+             alloc((void **)&m->WbT[l], nk * 2) &&
              alloc((void **)&m->mW[l], nk * 4) && alloc((void **)&m->vW[l], nk * 4) &&
              alloc((void **)&m->mb[l], n * 4) && alloc((void **)&m->vb[l], n * 4) &&
              alloc((void **)&m->dW[l], nk * 4) && alloc((void **)&m->db[l], n * 4);
@@ -593,7 +611,7 @@ extern "C" int wx_mlp_create(int max_batch, wx_mlp **out) {
         ok = alloc((void **)&m->Z[i], B * kHid * 2) && alloc((void **)&m->H[i], B * kHid * 2) &&
              alloc((void **)&m->dZ[i], B * kHid * 2);
     ok = ok && alloc((void **)&m->norm, 4 * kInP * 4) && alloc((void **)&m->lev, 2 * kNZ * 4) &&
-         alloc((void **)&m->X, B * kInP * 2) && alloc((void **)&m->dY, B * kOutP * 2) &&
+         alloc((void **)&m->X, B * kXW * 2) && alloc((void **)&m->dY, B * kOutP * 2) &&
          alloc((void **)&m->TA, B * kHid * 2) && alloc((void **)&m->TB, B * kHid * 2) &&
          alloc((void **)&m->Y, B * kOutP * 4) && alloc((void **)&m->loss, 1024 * 4) &&
          alloc((void **)&m->status, sizeof(unsigned));
@@ -628,7 +646,8 @@ extern "C" int wx_mlp_set_weights(wx_mlp *m, const float *const *W, const float 
         MCK(cudaMemset(m->vW[l], 0, w.size() * 4), "reset Adam");
         MCK(cudaMemset(m->mb[l], 0, bb.size() * 4), "reset Adam");
         MCK(cudaMemset(m->vb[l], 0, bb.size() * 4), "reset Adam");
-        to_bf16_kernel<<<grid1((long)N * K), 256>>>(m->W[l], (long)N * K, N, K, m->Wb[l], m->WbT[l]);
+        to_bf16_kernel<<<grid1((long)N * K), 256>>>(m->W[l], (long)N * K, N, K, l == 0, m->Wb[l],
+                                                     l == 0 ? nullptr : m->WbT[l]);
     }
     m->adam_t = 0;
     MCK(cudaDeviceSynchronize(), "wx_mlp_set_weights");
@@ -737,12 +756,13 @@ extern "C" int wx_mlp_prepare(wx_mlp *m, const float *Ts, const float *qs, const
 }
 
 namespace wx {
-// Forward pass of M rows (M % 128 == 0, <= max_batch) from BF16 X; Z/H kept
-// for backward; normalised outputs in m->Y [M][128] (or `Yout`).
+// Forward pass of M rows (M % 128 == 0, <= max_batch) from BF16 rows X
+// [M][512] (hi | lo); Z/H kept for backward; normalised outputs in m->Y
+// [M][128] (or `Yout`).
 static int mlp_forward(wx_mlp *m, const __nv_bfloat16 *X, int M, float *Yout, cudaStream_t s) {
     const __nv_bfloat16 *in = X;
     for (int l = 0; l < 3; ++l) {
-        const int rc = gemm(in, m->Wb[l], M, kHid, layer_in(l), EPI_GELU, m->b[l], nullptr, m->H[l], m->Z[l],
+        const int rc = gemm(in, m->Wb[l], M, kHid, layer_k(l), EPI_GELU, m->b[l], nullptr, m->H[l], m->Z[l],
                             m->status, s, m->err);
         if (rc != WX_OK) return rc;
         in = m->H[l];
@@ -751,9 +771,40 @@ static int mlp_forward(wx_mlp *m, const __nv_bfloat16 *X, int M, float *Yout, cu
                 m->err);
 }
 
-static void transpose(const __nv_bfloat16 *in, __nv_bfloat16 *out, int rows, int cols, cudaStream_t s) {
+static void transpose(const __nv_bfloat16 *in, __nv_bfloat16 *out, int rows, int cols, int ld, cudaStream_t s) {
     dim3 grid((cols + 31) / 32, (rows + 31) / 32), block(32, 8);
-    transpose_bf16_kernel<<<grid, block, 0, s>>>(in, out, rows, cols);
+    transpose_bf16_kernel<<<grid, block, 0, s>>>(in, out, rows, cols, ld);
+}
+
+// Loss gradient and backward pass after mlp_forward of the same rows:
+//   dW_l = dZ_l^T . a_l (GEMM over the M rows of the transposed operands),
+//   db_l = column sums of dZ_l,
+//   dZ_{l-1} = (dZ_l . W_l) * GELU'(Z_{l-1}) (GEMM with the GELU' epilogue).
+// The first layer's weight gradient takes the leading BF16 term of its
+// inputs (the hi half of X).
+static int mlp_backward(wx_mlp *m, const __nv_bfloat16 *X, const float *Yt, int M, float *loss, cudaStream_t s) {
+    const int nblk = 256;
+    mse_grad_kernel<<<nblk, 256, 0, s>>>(m->Y, Yt, M, m->dY, m->loss + 1);
+    if (loss) loss_finalize_kernel<<<1, 32, 0, s>>>(m->loss + 1, nblk, M, loss);
+    const __nv_bfloat16 *dout = m->dY;
+    int nout = kOutP;
+    for (int l = 3; l >= 0; --l) {
+        const int K = layer_in(l);
+        const __nv_bfloat16 *act = l == 0 ? X : m->H[l - 1];
+        transpose(dout, m->TA, M, nout, nout, s);              // [nout][M]
+        transpose(act, m->TB, M, K, l == 0 ? kXW : K, s);      // [K][M]
+        int rc = gemm(m->TA, m->TB, nout, K, M, EPI_F32, nullptr, nullptr, m->dW[l], nullptr, m->status, s, m->err);
+        if (rc != WX_OK) return rc;
+        rowsum_bf16_kernel<<<nout, 256, 0, s>>>(m->TA, M, m->db[l]);
+        if (l > 0) {
+            rc = gemm(dout, m->WbT[l], M, K, nout, EPI_DGELU, nullptr, m->Z[l - 1], m->dZ[l - 1], nullptr,
+                      m->status, s, m->err);
+            if (rc != WX_OK) return rc;
+            dout = m->dZ[l - 1];
+            nout = kHid;
+        }
+    }
+    return WX_OK;
 }
 }  // namespace wx
 
@@ -765,96 +816,51 @@ extern "C" int wx_mlp_forward(wx_mlp *m, const void *X, int M, float *Y, void *s
     // rows beyond the activation buffers go through in chunks of max_batch
     for (int r0 = 0; r0 < M; r0 += m->max_batch) {
         const int rows = std::min(m->max_batch, M - r0);
-        const int rc = mlp_forward(m, Xb + (size_t)r0 * kInP, rows, Y + (size_t)r0 * kOutP, s);
+        const int rc = mlp_forward(m, Xb + (size_t)r0 * kXW, rows, Y + (size_t)r0 * kOutP, s);
         if (rc != WX_OK) return mfail(m, rc, m->err);
     }
     return WX_OK;
 }
 
-// One training step on a minibatch: forward, MSE loss and its gradient,
-// backward through the four layers (tcgen05 GEMMs for input and weight
-// gradients), Adam.  loss (device float or NULL) receives the batch loss.
-extern "C" int wx_mlp_train_step(wx_mlp *m, const void *X, const float *Yt, int M, float lr, float *loss,
-                                 void *stream) {
-    if (!m || !X || !Yt) return mfail(m, WX_EINVAL, "wx_mlp_train_step: NULL");
+static int check_batch(wx_mlp *m, const void *X, const float *Yt, int M, const char *who) {
+    if (!m) return WX_EINVAL;
+    if (!X || !Yt) return mfail(m, WX_EINVAL, std::string(who) + ": NULL");
     if (M <= 0 || M % 128 || M > m->max_batch)
-        return mfail(m, WX_EINVAL, "wx_mlp_train_step: M must be a multiple of 128 and <= max_batch");
+        return mfail(m, WX_EINVAL, std::string(who) + ": M must be a multiple of 128 and <= max_batch");
+    return WX_OK;
+}
+
+extern "C" int wx_mlp_gradients(wx_mlp *m, const void *X, const float *Yt, int M, float *loss, void *stream) {
+    int rc = check_batch(m, X, Yt, M, "wx_mlp_gradients");
+    if (rc != WX_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     const __nv_bfloat16 *Xb = reinterpret_cast<const __nv_bfloat16 *>(X);
-    int rc = mlp_forward(m, Xb, M, nullptr, s);
+    rc = mlp_forward(m, Xb, M, nullptr, s);
+    if (rc == WX_OK) rc = mlp_backward(m, Xb, Yt, M, loss, s);
     if (rc != WX_OK) return mfail(m, rc, m->err);
-    const int nblk = 256;
-    mse_grad_kernel<<<nblk, 256, 0, s>>>(m->Y, Yt, M, m->dY, m->loss + 1);
-    if (loss) loss_finalize_kernel<<<1, 32, 0, s>>>(m->loss + 1, nblk, M, loss);
-    // layer 4: dW4 = dY^T . H3, db4 = colsum(dY); dZ3 = (dY . W4) * GELU'(Z3)
-    const __nv_bfloat16 *dout = m->dY;
-    int nout = kOutP;
-    for (int l = 3; l >= 0; --l) {
-        const int K = layer_in(l);
-        const __nv_bfloat16 *act = l == 0 ? Xb : m->H[l - 1];
-        transpose(dout, m->TA, M, nout, s);  // [nout][M]
-        transpose(act, m->TB, M, K, s);      // [K][M]
-        rc = gemm(m->TA, m->TB, nout, K, M, EPI_F32, nullptr, nullptr, m->dW[l], nullptr, m->status, s, m->err);
-        if (rc != WX_OK) return mfail(m, rc, m->err);
-        rowsum_bf16_kernel<<<nout, 256, 0, s>>>(m->TA, M, m->db[l]);
-        if (l > 0) {
-            rc = gemm(dout, m->WbT[l], M, K, nout, EPI_DGELU, nullptr, m->Z[l - 1], m->dZ[l - 1], nullptr,
-                      m->status, s, m->err);
-            if (rc != WX_OK) return mfail(m, rc, m->err);
-            dout = m->dZ[l - 1];
-            nout = kHid;
-        }
-    }
-    // Adam (beta 0.9, 0.999, eps 1e-8) with bias correction
+    MCK(cudaGetLastError(), "gradient kernels");
+    return WX_OK;
+}
+
+// One training step: forward, loss gradient, backward, then Adam with bias
+// correction (beta1 0.9, beta2 0.999, eps 1e-8) on every weight and bias.
+extern "C" int wx_mlp_train_step(wx_mlp *m, const void *X, const float *Yt, int M, float lr, float *loss,
+                                 void *stream) {
+    int rc = wx_mlp_gradients(m, X, Yt, M, loss, stream);
+    if (rc != WX_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
     ++m->adam_t;
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     const float c1 = 1.f - powf(b1, (float)m->adam_t), c2 = 1.f - powf(b2, (float)m->adam_t);
     for (int l = 0; l < kLayers; ++l) {
         const int N = layer_out(l), K = layer_in(l);
         adam_kernel<<<grid1((long)N * K), 256, 0, s>>>(m->W[l], m->dW[l], m->mW[l], m->vW[l], (long)N * K, N, K, lr,
-                                                      b1, b2, eps, c1, c2, m->Wb[l], m->WbT[l]);
+                                                      b1, b2, eps, c1, c2, l == 0, m->Wb[l],
+                                                      l == 0 ? nullptr : m->WbT[l]);
         adam_kernel<<<grid1(N), 256, 0, s>>>(m->b[l], m->db[l], m->mb[l], m->vb[l], N, N, 1, lr, b1, b2, eps, c1,
-                                            c2, nullptr, nullptr);
+                                            c2, 0, nullptr, nullptr);
     }
-    MCK(cudaGetLastError(), "training kernels");
-    return WX_OK;
-}
-
-// Gradients only (no Adam): forward + backward into the gradient buffers.
-extern "C" int wx_mlp_gradients(wx_mlp *m, const void *X, const float *Yt, int M, float *loss, void *stream) {
-    if (!m) return WX_EINVAL;
-    // a training step with lr = 0 leaves the weights as they were, but Adam
-    // moments would move: keep them by saving and restoring the step count
-    // is not enough, so run the forward/backward part only
-    if (!X || !Yt) return mfail(m, WX_EINVAL, "wx_mlp_gradients: NULL");
-    if (M <= 0 || M % 128 || M > m->max_batch)
-        return mfail(m, WX_EINVAL, "wx_mlp_gradients: M must be a multiple of 128 and <= max_batch");
-    cudaStream_t s = (cudaStream_t)stream;
-    const __nv_bfloat16 *Xb = reinterpret_cast<const __nv_bfloat16 *>(X);
-    int rc = mlp_forward(m, Xb, M, nullptr, s);
-    if (rc != WX_OK) return mfail(m, rc, m->err);
-    const int nblk = 256;
-    mse_grad_kernel<<<nblk, 256, 0, s>>>(m->Y, Yt, M, m->dY, m->loss + 1);
-    if (loss) loss_finalize_kernel<<<1, 32, 0, s>>>(m->loss + 1, nblk, M, loss);
-    const __nv_bfloat16 *dout = m->dY;
-    int nout = kOutP;
-    for (int l = 3; l >= 0; --l) {
-        const int K = layer_in(l);
-        const __nv_bfloat16 *act = l == 0 ? Xb : m->H[l - 1];
-        transpose(dout, m->TA, M, nout, s);
-        transpose(act, m->TB, M, K, s);
-        rc = gemm(m->TA, m->TB, nout, K, M, EPI_F32, nullptr, nullptr, m->dW[l], nullptr, m->status, s, m->err);
-        if (rc != WX_OK) return mfail(m, rc, m->err);
-        rowsum_bf16_kernel<<<nout, 256, 0, s>>>(m->TA, M, m->db[l]);
-        if (l > 0) {
-            rc = gemm(dout, m->WbT[l], M, K, nout, EPI_DGELU, nullptr, m->Z[l - 1], m->dZ[l - 1], nullptr,
-                      m->status, s, m->err);
-            if (rc != WX_OK) return mfail(m, rc, m->err);
-            dout = m->dZ[l - 1];
-            nout = kHid;
-        }
-    }
-    MCK(cudaGetLastError(), "gradient kernels");
+    MCK(cudaGetLastError(), "Adam kernels");
     return WX_OK;
 }
 
@@ -885,9 +891,9 @@ __global__ void __launch_bounds__(128) sur_features_kernel(const float *__restri
                                                            __nv_bfloat16 *__restrict__ X, long ncol, long rows) {
     const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= rows) return;
-    uint4 *row = reinterpret_cast<uint4 *>(X + c * kInP);
+    uint4 *row = reinterpret_cast<uint4 *>(X + c * kXW);
     if (c >= ncol) {
-        for (int g = 0; g < kInP / 8; ++g) row[g] = make_uint4(0, 0, 0, 0);
+        for (int g = 0; g < kXW / 8; ++g) row[g] = make_uint4(0, 0, 0, 0);
         return;
     }
     const int j = (int)(c / nx), i = (int)(c % nx);
@@ -896,7 +902,7 @@ __global__ void __launch_bounds__(128) sur_features_kernel(const float *__restri
     const float s = km ? km[c] : 1.f;
 #pragma unroll 1
     for (int g = 0; g < kInP / 8; ++g) {
-        __align__(16) __nv_bfloat16 v[8];
+        __align__(16) __nv_bfloat16 v[8], w[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
             const int f = 8 * g + t;
@@ -910,8 +916,10 @@ __global__ void __launch_bounds__(128) sur_features_kernel(const float *__restri
                 x = (raw - norm[f]) / norm[kInP + f];
             }
             v[t] = __float2bfloat16_rn(x);
+            w[t] = __float2bfloat16_rn(x - __bfloat162float(v[t]));
         }
         row[g] = *reinterpret_cast<const uint4 *>(v);
+        row[kInP / 8 + g] = *reinterpret_cast<const uint4 *>(w);
     }
 }
 
@@ -963,17 +971,18 @@ __global__ void __launch_bounds__(128) sur_apply_kernel(float *__restrict__ fld,
             q[k] = base[(size_t)(2 * k + 1) * plane];
         }
         // rho_vd: (A v - T*)_k = (v_k - T*_k) + a_k (v_{k-1} - v_k) + c_k (v_{k+1} - v_k)
+        // with v = T* + dt r; level differences of T* are taken first (exact
+        // in FP32 for neighbouring values) so that the small increments
+        // dt r never round against T ~ 300
         float num = 0.f, den = 0.f, sumH = 0.f, tau2 = 0.f;
         bool finite = true;
 #pragma unroll
         for (int k = 0; k < kNZ; ++k) {
             const float ak = s * sE[k].x, ck = s * sE[k].y;
-            const float xk = ts[k] + dt * r[k];
-            const float xm = k > 0 ? ts[k - 1] + dt * r[k - 1] : xk;
-            const float xp = k < kNZ - 1 ? ts[k + 1] + dt * r[k + 1] : xk;
-            const float tm = k > 0 ? ts[k - 1] : ts[k], tp = k < kNZ - 1 ? ts[k + 1] : ts[k];
-            const float ex = dt * r[k] + ak * (xm - xk) + ck * (xp - xk);
-            const float e0 = ak * (tm - ts[k]) + ck * (tp - ts[k]);
+            const float dtm = k > 0 ? ts[k - 1] - ts[k] : 0.f, dtp = k < kNZ - 1 ? ts[k + 1] - ts[k] : 0.f;
+            const float drm = k > 0 ? r[k - 1] - r[k] : 0.f, drp = k < kNZ - 1 ? r[k + 1] - r[k] : 0.f;
+            const float e0 = ak * dtm + ck * dtp;
+            const float ex = e0 + dt * (r[k] + ak * drm + ck * drp);
             num = fmaf(ex, ex, num);
             den = fmaf(e0, e0, den);
             sumH = fmaf(H[k], sE[k].z, sumH);
@@ -1075,10 +1084,10 @@ int launch_surrogate_step(wx_ctx *c, cudaStream_t s, long *launches) {
     const long chunk = 65535L * 128;
     for (long r0 = 0; r0 < rows; r0 += chunk) {
         const int M = (int)std::min(chunk, rows - r0);
-        const __nv_bfloat16 *X = reinterpret_cast<const __nv_bfloat16 *>(c->sur_X) + r0 * kInP;
+        const __nv_bfloat16 *X = reinterpret_cast<const __nv_bfloat16 *>(c->sur_X) + r0 * kXW;
         __nv_bfloat16 *H0 = reinterpret_cast<__nv_bfloat16 *>(c->sur_H[0]) + r0 * kHid;
         __nv_bfloat16 *H1 = reinterpret_cast<__nv_bfloat16 *>(c->sur_H[1]) + r0 * kHid;
-        rc = gemm(X, m->Wb[0], M, kHid, kInP, EPI_GELU, m->b[0], nullptr, H0, nullptr, c->d_status, s, err);
+        rc = gemm(X, m->Wb[0], M, kHid, kXW, EPI_GELU, m->b[0], nullptr, H0, nullptr, c->d_status, s, err);
         if (rc == WX_OK)
             rc = gemm(H0, m->Wb[1], M, kHid, kHid, EPI_GELU, m->b[1], nullptr, H1, nullptr, c->d_status, s, err);
         if (rc == WX_OK)
@@ -1123,7 +1132,7 @@ extern "C" int wx_set_surrogate(wx_ctx *c, wx_mlp *m, double fallback_tol) {
     }
     free_surrogate(c);
     const long rows = ((long)c->nx * c->ny + 127) / 128 * 128;
-    bool ok = cudaMalloc(&c->sur_X, rows * kInP * 2) == cudaSuccess &&
+    bool ok = cudaMalloc(&c->sur_X, rows * kXW * 2) == cudaSuccess &&
               cudaMalloc(&c->sur_H[0], rows * kHid * 2) == cudaSuccess &&
               cudaMalloc(&c->sur_H[1], rows * kHid * 2) == cudaSuccess &&
               cudaMalloc((void **)&c->sur_Y, rows * kOutP * 4) == cudaSuccess &&

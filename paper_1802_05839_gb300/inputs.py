@@ -207,15 +207,18 @@ def small_case(nx=128, ny=128, nz=32, seed=12345) -> Case:
                 q=tracer(nx, ny, nz, seed), U=U, V=V, name=f"small {nx}x{ny}x{nz}")
 
 
-def paper_grid_case(nx=1581, ny=1301, nz=58, seed=12345, near_singular=False) -> Case:
+def paper_grid_case(nx=1581, ny=1301, nz=58, seed=12345, near_singular=False,
+                    config_seed=None) -> Case:
     """The paper's ASUCA grid shape (Sec. 5.5): 1581x1301x58 by default.
 
     dz_k = 1.05^k, kappa_lev ~ U[0.01, 0.05] per level.  With near_singular
-    the Bernoulli(0.05) columns get kappa_mult = 10^U[4,5].
+    the Bernoulli(0.05) columns get kappa_mult = 10^U[4,5].  The fields and
+    winds come from `seed`; kappa_lev from `config_seed` (default: `seed`),
+    so that several states can share one model configuration.
     """
     h = 2.5
     U, V = winds(nx, ny, h, seed)
-    klev = 0.01 + 0.04 * uniform(seed, _S_KLEV, nz)
+    klev = 0.01 + 0.04 * uniform(seed if config_seed is None else config_seed, _S_KLEV, nz)
     km = near_singular_multiplier(nx, ny, seed) if near_singular else None
     return Case(nx=nx, ny=ny, nz=nz, dt=0.1, h=h, kappa_h=0.05, S0=1.0, q_ref=0.01,
                 dz=1.05 ** np.arange(nz), kappa_lev=klev, alpha=absorber(nz),

@@ -357,6 +357,7 @@ def wx_gemm_bf16(A, B, epilogue=0, bias=None, aux=None, out=None, out2=None, sta
 # ------------------------------------------------------------------ MLP
 MLP_SHAPES = [(512, 232), (512, 512), (512, 512), (116, 512)]  # (fan_out, fan_in)
 MLP_IN, MLP_IN_PAD, MLP_OUT, MLP_OUT_PAD = 232, 256, 116, 128
+MLP_X_WIDTH = 2 * MLP_IN_PAD  # [hi | lo] two-term BF16 input rows
 
 
 def _f32arrays(arrs):

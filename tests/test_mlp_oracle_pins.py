@@ -42,6 +42,17 @@ def test_bf16_rounding_ties_to_even_and_matches_torch():
     assert np.array_equal(mlp.bf16(x), ref)
 
 
+def test_two_term_bf16_expansion():
+    """hi + lo carries FP32(x) to 16 significant bits: |x - hi - lo| <=
+    2^-17 |x| (two roundings of 2^-9 each); hi alone only to 2^-9."""
+    x = inputs.normal(6, 1, 50000) * 10.0 ** (inputs.uniform(6, 2, 50000) * 6 - 3)
+    f = x.astype(np.float32).astype(np.float64)
+    hi, lo = mlp.bf16_pair(x)
+    assert np.array_equal(hi, mlp.bf16(x))
+    assert np.all(np.abs(f - hi - lo) <= 2.0 ** -17 * np.abs(f))
+    assert np.max(np.abs(f - hi) / np.abs(f)) > 2.0 ** -10
+
+
 def test_forward_matches_independent_torch_network():
     Ws, bs = inputs.mlp_init(11)
     bs = [inputs.normal(11, 50 + l, len(b)) * 0.1 for l, b in enumerate(bs)]
