@@ -12,7 +12,13 @@ field buffers exceed the 129 MB L2, so no flush is needed); `e2e` is the same
 metric through the C ABI with host buffers (load + step + read back every
 step); `roofline` relates the step kernel's algorithmic bytes to the measured
 HBM copy bandwidth; `cpu_baseline` times the FP64 CPU oracle on a bounded
-sample of the same workload on this host's cores.
+sample of the same workload on this host's cores.  `variants` holds the
+other measured configurations of the same hot path: the FP64 step, the
+mixed-precision step with FP64 sums, the 16-member ensemble replayed from a
+CUDA graph, and the residual-checked MLP-surrogate step (network trained in
+this run by the library's kernels) against the plain step.
+
+  python bench.py --only f64|mixed|ensemble|surrogate [--nx --ny]   one variant
 """
 from __future__ import annotations
 
@@ -200,6 +206,155 @@ def e2e_measure(case, dtype, iters=3):
             "path": "wx_load_fields(host) + wx_step(1) + wx_read_fields(host)"}
 
 
+def _events(n):
+    import torch
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def _time_steps(step, n, stream, warmup=3):
+    """Mean ms per call of step() over n calls after `warmup`, CUDA events on
+    `stream` with a synchronize on both sides."""
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = _events(2)
+    torch.cuda.nvtx.range_push("timed")   # ncu --nvtx --nvtx-include timed/
+    e0.record(stream)
+    for _ in range(n):
+        step()
+    e1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / n
+
+
+def variant_plain(dtype, steps, nx=1581, ny=1301, nz=58):
+    """FP64 (C2) or mixed precision with FP64 sums (C3) at the paper grid."""
+    import torch
+    from paper_1802_05839_gb300 import wx
+    case = make_case(dtype, nx, ny, nz)
+    ctx = wx.Context(nx, ny, nz, dtype)
+    flags = wx.WX_ADVECTION | wx.WX_PHYSICS | (wx.WX_SUMS if dtype == "mixed" else 0)
+    ctx.set_params(case, flags=flags)
+    ctx.load_fields(case.T, case.q, case.U, case.V)
+    st = torch.cuda.Stream()
+    ms = _time_steps(lambda: ctx.step(1, stream=st), steps, st)
+    ctx.sync()
+    out = {"ms_per_step": ms, "value": case.cells / (ms * 1e-3), "unit": "cell-steps/s", "steps": steps,
+           "workload": f"paper grid {nx}x{ny}x{nz} ({dtype})", "gpu_launches_per_step": ctx.last_launches()}
+    peak, kind = peaks()
+    alg = case.cells * CELL_BYTES[dtype] + nx * ny * COL_BYTES[dtype]
+    out["hbm_frac"] = alg / (ms * 1e-3) / 1e9 / peak
+    if dtype == "mixed":
+        out["flagged_fp64_columns"] = ctx.flagged_columns()
+        out["sums_recorded"] = len(ctx.sums()[0])
+    if dtype == "f64":
+        out["bound"] = "fp64 alu (one FP64 divide and exp2 per T cell; GB300 FP64 rate)"
+    ctx.close()
+    return out
+
+
+def variant_ensemble(steps):
+    """16 uneven members (C4), one persistent launch per step, graph-replayed."""
+    import torch
+    from paper_1802_05839_gb300 import inputs, wx
+    sizes = inputs.ensemble_sizes()
+    ens = wx.Ensemble(sizes, "f32")
+    cells = 0
+    for m, (mem, (nx, ny, nz)) in enumerate(zip(ens.members, sizes)):
+        c = inputs.round_to_f32(inputs.ensemble_member(m, nx, ny, nz))
+        mem.set_params(c)
+        mem.load_fields(c.T, c.q, c.U, c.V)
+        cells += nx * ny * nz
+    st = torch.cuda.Stream()
+    tuned_ms = ens.tune(stream=st)
+    ens.step(steps, graph=True, stream=st)   # capture + warm-up replay
+    ens.sync()
+    torch.cuda.synchronize()
+    e0, e1 = _events(2)
+    e0.record(st)
+    ens.step(steps, graph=True, stream=st)
+    e1.record(st)
+    ens.sync()
+    ms = e0.elapsed_time(e1) / steps
+    peak, _ = peaks()
+    alg = sum(nx * ny * nz * CELL_BYTES["f32"] + nx * ny * COL_BYTES["f32"] for nx, ny, nz in sizes)
+    out = {"ms_per_step": ms, "value": cells / (ms * 1e-3), "unit": "cell-steps/s (all members)",
+           "steps": steps, "members": len(sizes), "cells": cells, "hbm_frac": alg / (ms * 1e-3) / 1e9 / peak,
+           "graph": True, "tuned_config": ens.step_config(), "tune_ms": tuned_ms,
+           "gpu_launches_per_step": ens.last_launches() / steps}
+    ens.close()
+    return out
+
+
+def variant_surrogate(steps, nx=1581, ny=1301, plain_ms=None, train_epochs=32):
+    """C5: train the MLP on 2M columns with the library's kernels, then step
+    the paper grid with the residual-checked surrogate."""
+    import torch
+    from paper_1802_05839_gb300 import inputs, surrogate as S, wx
+    t0 = time.perf_counter()
+    # train_epochs = 0: an untrained network (kernel timing and profiling only)
+    Ts, qs, km, tend = S.dataset(range(1, 9), 512, 512) if train_epochs else S.dataset([1], 128, 128)
+    net = wx.MLP(4096)
+    Ws, bs = inputs.mlp_init(2024)
+    net.set_weights(Ws, bs)
+    S.set_levels_from_case(net, inputs.paper_grid_case(8, 8, 58, seed=1, config_seed=S.CONFIG_SEED))
+    net.fit_norm(Ts, qs, km, tend)
+    X, Yt = S.rows(net, Ts, qs, km, tend)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    hist = S.train(net, X, Yt, Ts.shape[0], epochs=train_epochs, batch=4096, lr0=3e-3, seed=0) \
+        if train_epochs else [float("nan")]
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    n_train = Ts.shape[0]
+    del X, Yt, Ts, qs, km, tend
+    val = S.dataset([101], 256, 256)
+    err = S.tendency_error(net, *val)
+    del val
+    case = make_case("f32", nx, ny, 58)
+    ctx = wx.Context(nx, ny, 58, "f32")
+    ctx.set_params(case, flags=wx.WX_ADVECTION | wx.WX_PHYSICS | wx.WX_SURROGATE)
+    ctx.load_fields(case.T, case.q, case.U, case.V)
+    ctx.set_surrogate(net, 2e-2)
+    st = torch.cuda.Stream()
+    ms = _time_steps(lambda: ctx.step(1, stream=st), steps, st)
+    torch.cuda.nvtx.range_push("surrogate_step")
+    ctx.step(1, stream=st)
+    torch.cuda.nvtx.range_pop()
+    ctx.sync()
+    fb = ctx.surrogate_fallbacks()
+    launches = ctx.last_launches()
+    ctx.close()
+    # the network alone on every column of the grid (tensor-core roofline)
+    rows = (nx * ny + 127) // 128 * 128
+    Xf = torch.zeros(rows, wx.MLP_X_WIDTH, dtype=torch.bfloat16, device="cuda")
+    Yf = torch.empty(rows, wx.MLP_OUT_PAD, dtype=torch.float32, device="cuda")
+    big = wx.MLP(rows)
+    big.set_weights(*net.get_weights())
+    fwd_ms = _time_steps(lambda: big.forward(Xf, Yf, stream=st), 5, st)
+    big.close()
+    net.close()
+    flop_col = 2 * (512 * 512 + 2 * 512 * 512 + 512 * 128)   # padded GEMM shapes actually run
+    flop_alg = 2 * (232 * 512 + 2 * 512 * 512 + 512 * 116)   # the network's own
+    tflops = nx * ny * flop_col / (fwd_ms * 1e-3) / 1e12
+    tpk = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
+    out = {"ms_per_step": ms, "value": nx * ny * 58 / (ms * 1e-3), "unit": "cell-steps/s",
+           "steps": steps, "workload": f"paper grid {nx}x{ny}x58, surrogate physics, fallback tol 2e-2",
+           "fallback_columns_last_step": fb, "fallback_frac": fb / (nx * ny),
+           "val_tendency_rel_l2": {"all": err[0], "heating": err[1], "vdiff": err[2]},
+           "train": {"columns": n_train, "epochs": train_epochs, "batch": 4096, "loss_first": hist[0],
+                     "loss_last": hist[-1], "seconds": t2 - t1, "setup_seconds": t1 - t0},
+           "network_forward": {"ms": fwd_ms, "tflops": tflops, "peak_tflops": tpk, "frac": tflops / tpk,
+                               "flop_per_column_run": flop_col, "flop_per_column_alg": flop_alg},
+           "gpu_launches_per_step": launches}
+    if plain_ms:
+        out["vs_plain_step"] = ms / plain_ms
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -233,10 +388,12 @@ def run_ours(args):
     time.sleep(0.3)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")   # ncu --nvtx --nvtx-include timed/
     ev[0].record(stream)
     for s in range(args.steps):
         ctx.step(1, stream=stream)
         ev[s + 1].record(stream)
+    torch.cuda.nvtx.range_pop()
     stream.synchronize()
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -284,6 +441,13 @@ def run_ours(args):
         out["e2e"] = e2e_measure(case, dtype)
     if not args.skip_cpu:
         out["cpu_baseline"] = cpu_baseline(case if dtype == "f64" else make_case("f64"))
+    if not args.no_variants and dtype == "f32" and (case.nx, case.ny, case.nz) == (1581, 1301, 58):
+        out["variants"] = {
+            "f64": variant_plain("f64", 100),
+            "mixed": variant_plain("mixed", 500),
+            "ensemble": variant_ensemble(200),
+            "surrogate": variant_surrogate(100, plain_ms=ms, train_epochs=args.epochs),
+        }
     print(json.dumps(out))
 
 
@@ -299,11 +463,25 @@ def main():
     ap.add_argument("--nx", type=int, default=1581, help="grid override (profiling captures only)")
     ap.add_argument("--ny", type=int, default=1301, help="grid override (profiling captures only)")
     ap.add_argument("--nz", type=int, default=58, help="grid override (profiling captures only)")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--epochs", type=int, default=32, help="surrogate training epochs")
+    ap.add_argument("--only", choices=["f64", "mixed", "ensemble", "surrogate"],
+                    help="run one variant alone and print its record (profiling captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    args.metric = "cell-steps/s at 1581x1301x58 (FP32 vs FP64), % HBM peak"
+    args.metric = "cell-steps/s at 1581x1301x58 (FP32 vs FP64), % HBM peak; surrogate vs plain"
     if args.impl == "reference":
         run_reference(args)
+    elif args.only:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        if args.only in ("f64", "mixed"):
+            rec = variant_plain(args.only, args.steps, args.nx, args.ny, args.nz)
+        elif args.only == "ensemble":
+            rec = variant_ensemble(args.steps)
+        else:
+            rec = variant_surrogate(args.steps, args.nx, args.ny, train_epochs=args.epochs)
+        print(json.dumps({"variant": args.only, **rec}))
     else:
         run_ours(args)
 
