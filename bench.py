@@ -1,6 +1,6 @@
 """Benchmark of the fused weather step on GB300.
 
-Default workload: the paper's grid 1581 x 1301 x 58 (Sec. 5.5), FP32 fields,
+Default workload: the paper's grid 1581 x 1301 x 58 (Sec. 5.4), FP32 fields,
 dynamics + column physics, seeded synthetic state (the paper's JMA inputs are
 not public).  One step = one pass of the whole hot path over the grid.
 

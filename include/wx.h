@@ -12,7 +12,7 @@
  *             periodic in x and y (Sec. 3.1: "cyclic" KI/KJ boundaries), plus
  *             flux-form first-order upwind advection by C-grid face winds;
  *   physics   per column (Sec. 3.1: one thread per K column, K sequential,
- *             Sec. 2.2): implicit vertical diffusion (I - dt L_v) T** = T*
+ *             Sec. 2.1): implicit vertical diffusion (I - dt L_v) T** = T*
  *             by the Thomas algorithm, optical depth dtau_k =
  *             alpha_k dz_k q*_k / q_ref scanned from the top, heating
  *             H_k = S0 (exp(-tau_top,k) - exp(-tau_bot,k)) / dz_k,
@@ -206,7 +206,7 @@ int wx_tune(wx_ctx *c, const char *cache_path, int force, void *cuda_stream,
  * members' sums kernels when enabled.  Members are ordinary contexts owned
  * by the ensemble: set their parameters, load and read their fields with
  * the wx_* calls on wx_ens_member(e, i).  (The paper's ensemble context is
- * its many-GPU strong-scaling runs, Sec. 5.5; this batches independent
+ * its many-GPU strong-scaling runs, Sec. 5.4; this batches independent
  * grids on one GPU.) */
 typedef struct wx_ens wx_ens;
 

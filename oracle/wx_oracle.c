@@ -12,7 +12,7 @@
  *   zero-flux vertical ends (1-5d rows)    paper appendix, diffusion listing
  *   periodic horizontal boundaries         paper Sec. 3.1 ("cyclic")
  *   out-of-place update, then swap         paper appendix, time-loop listing
- *   one column per thread for physics      paper Sec. 3.1 and Sec. 2.2
+ *   one column per thread for physics      paper Sec. 3.1 and Sec. 2.1
  *   advection, Thomas solve, k-scan        the step definition in the
  *                                          header comment (the paper names
  *                                          C-grid finite-volume dynamics and

@@ -16,7 +16,7 @@
 //     implicit vertical diffusion (I - dt L_v) x = T*: the Thomas elimination
 //       run from the top, f_k = (T*_k - c_k f_{k+1}) / m_k, m_k = b_k -
 //       c_k e_{k+1}, e_k = a_k / m_k (the K recurrence the paper keeps
-//       sequential, Sec. 2.2);
+//       sequential, Sec. 2.1);
 //     the heating is folded into the back substitution: with T^{n+1}_k =
 //       x_k + dt H_k and x_k = f_k - e_k x_{k-1},
 //         T^{n+1}_k = F_k - e_k T^{n+1}_{k-1},  F_k = f_k + h_k + e_k h_{k-1},

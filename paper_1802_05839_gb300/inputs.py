@@ -209,7 +209,7 @@ def small_case(nx=128, ny=128, nz=32, seed=12345) -> Case:
 
 def paper_grid_case(nx=1581, ny=1301, nz=58, seed=12345, near_singular=False,
                     config_seed=None) -> Case:
-    """The paper's ASUCA grid shape (Sec. 5.5): 1581x1301x58 by default.
+    """The paper's ASUCA grid shape (Sec. 5.4): 1581x1301x58 by default.
 
     dz_k = 1.05^k, kappa_lev ~ U[0.01, 0.05] per level.  With near_singular
     the Bernoulli(0.05) columns get kappa_mult = 10^U[4,5].  The fields and
