@@ -2,13 +2,19 @@
 // physics: forward, backward, Adam, the residual-checked surrogate step.
 //
 // GEMM: C[M][N] = A[M][K] . B[N][K]^T, A and B BF16 and K-major in global
-// memory, FP32 accumulation in tensor memory.  One CTA (4 warps) per 128 x BN
-// output tile: thread 0 streams 128 x 64 and BN x 64 K-slabs of A and B
-// through a 4-slot shared-memory ring with TMA (128-byte swizzle); thread 32
-// issues tcgen05.mma (M = 128, N = BN, K = 16, four per slab) and commits
-// each slab back to its ring slot; when the last slab's MMAs complete, the
-// four warps drain their 32 TMEM lanes each with tcgen05.ld and apply the
-// epilogue (bias, GELU, GELU' for backward) on the way to global memory.
+// memory, FP32 accumulation in tensor memory.  A persistent kernel, one CTA
+// per SM, walks the 128 x BN output tiles (n fastest, so that the CTAs
+// running at the same time share each A tile in L2) with three roles:
+//   warp 0 (one lane): streams 128 x 64 and BN x 64 K-slabs of A and B
+//     through a shared-memory ring with TMA (128-byte swizzle);
+//   warp 1 (one lane): issues tcgen05.mma (M = 128, N = BN, K = 16, four per
+//     slab) into one of two TMEM accumulators, commits each slab back to its
+//     ring slot and each finished tile to the epilogue;
+//   warps 2..17: drain the other accumulator with tcgen05.ld and apply the
+//     epilogue (bias, GELU, GELU' for backward) on the way to global memory,
+//     then hand the accumulator back -- so the epilogue of tile i runs under
+//     the MMAs of tile i+1.
+// Every wait is bounded; a timeout sets a status bit and all roles stop.
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
@@ -42,11 +48,11 @@ struct GemmArgs {
     unsigned *status;
 };
 
-constexpr int kGemmBK = 64;  // BF16 K per slab: one 128-byte swizzle row
-// Ring depth: two slots of 48 KB for 256-column tiles, three of 32 KB for
-// 128-column tiles, so that two CTAs share an SM and one's epilogue runs
-// under the other's MMAs.
-__host__ __device__ constexpr int gemm_stages(int BN) { return BN == 256 ? 2 : 3; }
+constexpr int kGemmBK = 64;   // BF16 K per slab: one 128-byte swizzle row
+constexpr int kEpiWarps = 16;  // epilogue warps: 4 per TMEM lane quarter
+constexpr int kGemmThreads = 32 * (2 + kEpiWarps);
+// Ring depth: 4 slots of 48 KB for 256-column tiles, 6 of 32 KB for 128.
+__host__ __device__ constexpr int gemm_stages(int BN) { return BN == 256 ? 4 : 6; }
 __host__ __device__ constexpr int gemm_smem(int BN) {
     return gemm_stages(BN) * (128 * kGemmBK * 2 + BN * kGemmBK * 2) + 1024 + 256;
 }
@@ -60,35 +66,41 @@ __device__ __forceinline__ float gelu_grad(float z) {
 }
 
 template <int BN, int EPI>
-__global__ void __launch_bounds__(256, 2) gemm_kernel(const __grid_constant__ CUtensorMap ta,
-                                                   const __grid_constant__ CUtensorMap tb, const GemmArgs g) {
+__global__ void __launch_bounds__(kGemmThreads, 1) gemm_kernel(const __grid_constant__ CUtensorMap ta,
+                                                            const __grid_constant__ CUtensorMap tb,
+                                                            const GemmArgs g) {
     constexpr int BM = 128;
-    constexpr int kGemmStages = gemm_stages(BN);
+    constexpr int S = gemm_stages(BN);
     constexpr uint32_t A_BYTES = BM * kGemmBK * 2, B_BYTES = BN * kGemmBK * 2;
     constexpr uint32_t STAGE = A_BYTES + B_BYTES;
+    constexpr int CPW = BN / 4;  // accumulator columns per epilogue warp
     extern __shared__ __align__(1024) unsigned char gsm[];
     unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(gsm) + 1023) & ~uintptr_t(1023));
-    uint64_t *full = reinterpret_cast<uint64_t *>(base + kGemmStages * STAGE);
-    uint64_t *empty = full + kGemmStages;
-    uint64_t *done = empty + kGemmStages;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    uint64_t *full = reinterpret_cast<uint64_t *>(base + S * STAGE);
+    uint64_t *empty = full + S;
+    uint64_t *acc_full = empty + S;     // [2] MMA -> epilogue
+    uint64_t *acc_empty = acc_full + 2; // [2] epilogue -> MMA
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int nk = g.K / kGemmBK;
+    const int nk = g.K / kGemmBK, nN = g.N / BN;
+    const long ntiles = (long)(g.M / BM) * nN;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kGemmStages; ++s) {
+        for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], kEpiWarps);
+        }
         *abort_flag = 0;
         fence_mbar_init();
     }
     if (warp == 0) {
-        tmem_alloc(tmem_slot, BN);
+        tmem_alloc(tmem_slot, 2 * BN);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -96,109 +108,157 @@ __global__ void __launch_bounds__(256, 2) gemm_kernel(const __grid_constant__ CU
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (threadIdx.x == 0) {
-        // producer: K-slabs of A and B into the ring
-        prefetch_tmap(&ta);
-        prefetch_tmap(&tb);
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % kGemmStages;
-            if (kb >= kGemmStages && !mbar_wait_bounded(&empty[s], ((kb / kGemmStages) - 1) & 1)) {
-                *abort_flag = 1;
-                break;
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer: (tile, slab) in order through the ring; a slot is
+            // refilled once the MMAs that read it have completed
+            prefetch_tmap(&ta);
+            prefetch_tmap(&tb);
+            long issued = 0;
+            for (long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+                const int m0 = (int)(t / nN) * BM, n0 = (int)(t % nN) * BN;
+                for (int kb = 0; kb < nk; ++kb, ++issued) {
+                    const int s = (int)(issued % S);
+                    const uint32_t ph = (uint32_t)((issued / S) & 1);
+                    if (*abort_flag || !mbar_wait_bounded(&empty[s], ph ^ 1u)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    unsigned char *sa = base + s * STAGE;
+                    mbar_arrive_expect_tx(&full[s], STAGE);
+                    tma_load_2d(sa, &ta, &full[s], kb * kGemmBK, m0);
+                    tma_load_2d(sa + A_BYTES, &tb, &full[s], kb * kGemmBK, n0);
+                }
             }
-            unsigned char *sa = base + s * STAGE;
-            mbar_arrive_expect_tx(&full[s], STAGE);
-            tma_load_2d(sa, &ta, &full[s], kb * kGemmBK, m0);
-            tma_load_2d(sa + A_BYTES, &tb, &full[s], kb * kGemmBK, n0);
+            // the ring's last copies have landed before the CTA may exit
+            for (long q = issued - 1; q >= 0 && q >= issued - S; --q)
+                (void)mbar_wait_bounded(&full[q % S], (uint32_t)((q / S) & 1));
         }
-    } else if (threadIdx.x == 32) {
-        // MMA issuer
-        constexpr uint32_t idesc = idesc_bf16(BM, BN);
-        bool ok = true;
-        for (int kb = 0; kb < nk && ok; ++kb) {
-            const int s = kb % kGemmStages;
-            if (!mbar_wait_bounded(&full[s], (kb / kGemmStages) & 1)) {
-                ok = false;
-                *abort_flag = 1;
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(BM, BN);
+            long used = 0;
+            int it = 0;
+            for (long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++it) {
+                const int b = it & 1;
+                const uint32_t use = (uint32_t)(it >> 1);
+                if (!mbar_wait_bounded(&acc_empty[b], (use & 1u) ^ 1u)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * BN);
+                bool ok = true;
+                for (int kb = 0; kb < nk; ++kb, ++used) {
+                    const int s = (int)(used % S);
+                    if (*abort_flag || !mbar_wait_bounded(&full[s], (uint32_t)((used / S) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const unsigned char *sa = base + s * STAGE;
+                    const uint64_t ad = smem_desc_sw128(sa), bd = smem_desc_sw128(sa + A_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < kGemmBK / 16; ++kk)
+                        // +32 bytes per K = 16 step inside the 128-byte swizzle row
+                        tc_mma_bf16(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, (kb | kk) != 0);
+                    tc_commit(&empty[s]);
+                }
+                if (!ok) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc_commit(&acc_full[b]);  // arrives when every MMA of the tile has completed
+            }
+        }
+    } else {
+        // epilogue: warp w drains TMEM lanes 32 (w % 4) .. +31 (rows
+        // m0 + 32 (w % 4) + lane), columns [CPW p, CPW (p + 1)), p = (w - 2) / 4
+        const int quarter = warp & 3, part = (warp - 2) >> 2;
+        int it = 0;
+        for (long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+            const int b = it & 1;
+            const uint32_t use = (uint32_t)(it >> 1);
+            bool ok = !*abort_flag && mbar_wait_bounded(&acc_full[b], use & 1u);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                if (lane == 0) *abort_flag = 1;
                 break;
             }
             tc_fence_after();
-            const unsigned char *sa = base + s * STAGE;
-            const uint64_t ad = smem_desc_sw128(sa), bd = smem_desc_sw128(sa + A_BYTES);
-#pragma unroll
-            for (int kk = 0; kk < kGemmBK / 16; ++kk) {
-                // +32 bytes per K = 16 step inside the 128-byte swizzle row
-                tc_mma_bf16(tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, (kb | kk) != 0);
-            }
-            tc_commit(&empty[s]);
-        }
-        tc_commit(done);  // arrives once every MMA issued above has completed
-    }
-
-    // epilogue: warp w drains TMEM lanes 32(w%4)..+31 (rows m0+32(w%4)+lane),
-    // columns [BN/2 (w/4), BN/2 (w/4 + 1))
-    __syncwarp();
-    const bool ok = mbar_wait_bounded(done, 0);
-    __syncwarp();
-    tc_fence_after();
-    if (!ok || *abort_flag) {
-        if (threadIdx.x == 0) atomicOr(g.status, ST_TIMEOUT);
-    } else {
-        const int quarter = warp & 3, half = warp >> 2;
-        const int row = m0 + quarter * 32 + lane;
-        const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
+            const int m0 = (int)(t / nN) * BM, n0 = (int)(t % nN) * BN;
+            const int row = m0 + quarter * 32 + lane;
+            const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN);
 #pragma unroll 1
-        for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 16) {
-            float v[16];
-            tmem_ld16(trow + c0, v);
-            const int col = n0 + c0;
-            const size_t o = (size_t)row * g.N + col;
-            if (EPI == EPI_F32) {
-                float *out = reinterpret_cast<float *>(g.out) + o;
+            for (int c0 = part * CPW; c0 < (part + 1) * CPW; c0 += 16) {
+                float v[16];
+                tmem_ld16(trow + c0, v);
+                const int col = n0 + c0;
+                float bias[16];
+                if (g.bias) {
+                    const float4 *bp = reinterpret_cast<const float4 *>(g.bias + col);
 #pragma unroll
-                for (int i = 0; i < 16; i += 4) {
-                    float4 w4;
-                    w4.x = v[i] + (g.bias ? g.bias[col + i] : 0.f);
-                    w4.y = v[i + 1] + (g.bias ? g.bias[col + i + 1] : 0.f);
-                    w4.z = v[i + 2] + (g.bias ? g.bias[col + i + 2] : 0.f);
-                    w4.w = v[i + 3] + (g.bias ? g.bias[col + i + 3] : 0.f);
-                    *reinterpret_cast<float4 *>(out + i) = w4;
-                }
-            } else {
-                __align__(16) __nv_bfloat16 o1[16];
-                __align__(16) __nv_bfloat16 o2[16];
-                __align__(16) __nv_bfloat16 zin[16];
-                if (EPI == EPI_DGELU) {
-                    const uint4 *zp = reinterpret_cast<const uint4 *>(g.aux + o);
-                    *reinterpret_cast<uint4 *>(zin) = zp[0];
-                    *reinterpret_cast<uint4 *>(zin + 8) = zp[1];
-                }
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 b4 = bp[q];
+                        bias[4 * q] = b4.x;
+                        bias[4 * q + 1] = b4.y;
+                        bias[4 * q + 2] = b4.z;
+                        bias[4 * q + 3] = b4.w;
+                    }
+                } else {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    if (EPI == EPI_GELU) {
-                        const float z = v[i] + g.bias[col + i];
-                        o1[i] = __float2bfloat16_rn(gelu(z));
-                        o2[i] = __float2bfloat16_rn(z);
-                    } else if (EPI == EPI_DGELU) {
-                        o1[i] = __float2bfloat16_rn(v[i] * gelu_grad(__bfloat162float(zin[i])));
-                    } else {
-                        o1[i] = __float2bfloat16_rn(v[i] + (g.bias ? g.bias[col + i] : 0.f));
+                    for (int q = 0; q < 16; ++q) bias[q] = 0.f;
+                }
+                const size_t o = (size_t)row * g.N + col;
+                if (EPI == EPI_F32) {
+                    float *out = reinterpret_cast<float *>(g.out) + o;
+#pragma unroll
+                    for (int q = 0; q < 16; q += 4)
+                        *reinterpret_cast<float4 *>(out + q) =
+                            make_float4(v[q] + bias[q], v[q + 1] + bias[q + 1], v[q + 2] + bias[q + 2],
+                                        v[q + 3] + bias[q + 3]);
+                } else {
+                    __align__(16) __nv_bfloat162 o1[8];
+                    __align__(16) __nv_bfloat162 o2[8];
+                    __align__(16) __nv_bfloat16 zin[16];
+                    if (EPI == EPI_DGELU) {
+                        const uint4 *zp = reinterpret_cast<const uint4 *>(g.aux + o);
+                        *reinterpret_cast<uint4 *>(zin) = zp[0];
+                        *reinterpret_cast<uint4 *>(zin + 8) = zp[1];
+                    }
+#pragma unroll
+                    for (int q = 0; q < 16; q += 2) {
+                        if (EPI == EPI_GELU) {
+                            const float z0 = v[q] + bias[q], z1 = v[q + 1] + bias[q + 1];
+                            o1[q / 2] = __floats2bfloat162_rn(gelu(z0), gelu(z1));
+                            o2[q / 2] = __floats2bfloat162_rn(z0, z1);
+                        } else if (EPI == EPI_DGELU) {
+                            o1[q / 2] = __floats2bfloat162_rn(v[q] * gelu_grad(__bfloat162float(zin[q])),
+                                                              v[q + 1] * gelu_grad(__bfloat162float(zin[q + 1])));
+                        } else {
+                            o1[q / 2] = __floats2bfloat162_rn(v[q] + bias[q], v[q + 1] + bias[q + 1]);
+                        }
+                    }
+                    __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(g.out) + o;
+                    reinterpret_cast<uint4 *>(out)[0] = *reinterpret_cast<uint4 *>(o1);
+                    reinterpret_cast<uint4 *>(out)[1] = *reinterpret_cast<uint4 *>(o1 + 4);
+                    if (EPI == EPI_GELU && g.out2) {
+                        __nv_bfloat16 *out2 = g.out2 + o;
+                        reinterpret_cast<uint4 *>(out2)[0] = *reinterpret_cast<uint4 *>(o2);
+                        reinterpret_cast<uint4 *>(out2)[1] = *reinterpret_cast<uint4 *>(o2 + 4);
                     }
                 }
-                __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(g.out) + o;
-                reinterpret_cast<uint4 *>(out)[0] = *reinterpret_cast<uint4 *>(o1);
-                reinterpret_cast<uint4 *>(out)[1] = *reinterpret_cast<uint4 *>(o1 + 8);
-                if (EPI == EPI_GELU && g.out2) {
-                    __nv_bfloat16 *out2 = g.out2 + o;
-                    reinterpret_cast<uint4 *>(out2)[0] = *reinterpret_cast<uint4 *>(o2);
-                    reinterpret_cast<uint4 *>(out2)[1] = *reinterpret_cast<uint4 *>(o2 + 8);
-                }
             }
+            // the accumulator may be overwritten once every warp's loads are done
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, BN);
+    if (threadIdx.x == 0 && *abort_flag) atomicOr(g.status, ST_TIMEOUT);
+    if (warp == 0) tmem_dealloc(tmem, 2 * BN);
 }
 
 // ------------------------------------------------------------ launcher
@@ -251,10 +311,14 @@ template <int BN, int EPI> static cudaError_t gemm_launch(const CUtensorMap &a, 
     const int smem = gemm_smem(BN);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    // n fastest: the CTAs of one 128-row block run together and share its A
-    // tile in L2
-    dim3 grid(g.N / BN, g.M / 128);
-    k<<<grid, 256, smem, s>>>(a, b, g);
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const long tiles = (long)(g.M / 128) * (g.N / BN);
+    k<<<(unsigned)std::min<long>(tiles, sms), kGemmThreads, smem, s>>>(a, b, g);
     return cudaGetLastError();
 }
 
@@ -264,10 +328,6 @@ int gemm(const void *A, const void *B, int M, int N, int K, int epi, const float
          void *out2, unsigned *status, cudaStream_t s, std::string &err) {
     if (M <= 0 || N <= 0 || K <= 0 || M % 128 || N % 128 || K % kGemmBK) {
         err = "gemm: M and N must be multiples of 128 and K of 64";
-        return WX_EINVAL;
-    }
-    if (M / 128 > 65535) {
-        err = "gemm: M above 65535 x 128 rows";
         return WX_EINVAL;
     }
     const int BN = (N % 256 == 0) ? 256 : 128;
@@ -485,7 +545,7 @@ __global__ void features_cols_kernel(const float *__restrict__ Ts, const float *
                               : kind == 1 ? qs[col * kNZ + k]
                               : kind == 2 ? s * lev[k]
                                           : lev[kNZ + k];
-            x = (raw - norm[f]) / norm[kInP + f];
+            x = (raw - norm[f]) * (1.f / norm[kInP + f]);
         }
         const __nv_bfloat16 hi = __float2bfloat16_rn(x);
         row[f] = hi;
@@ -759,11 +819,12 @@ namespace wx {
 // Forward pass of M rows (M % 128 == 0, <= max_batch) from BF16 rows X
 // [M][512] (hi | lo); Z/H kept for backward; normalised outputs in m->Y
 // [M][128] (or `Yout`).
-static int mlp_forward(wx_mlp *m, const __nv_bfloat16 *X, int M, float *Yout, cudaStream_t s) {
+static int mlp_forward(wx_mlp *m, const __nv_bfloat16 *X, int M, float *Yout, cudaStream_t s,
+                       bool keep_z = true) {
     const __nv_bfloat16 *in = X;
     for (int l = 0; l < 3; ++l) {
-        const int rc = gemm(in, m->Wb[l], M, kHid, layer_k(l), EPI_GELU, m->b[l], nullptr, m->H[l], m->Z[l],
-                            m->status, s, m->err);
+        const int rc = gemm(in, m->Wb[l], M, kHid, layer_k(l), EPI_GELU, m->b[l], nullptr, m->H[l],
+                            keep_z ? m->Z[l] : nullptr, m->status, s, m->err);
         if (rc != WX_OK) return rc;
         in = m->H[l];
     }
@@ -816,7 +877,7 @@ extern "C" int wx_mlp_forward(wx_mlp *m, const void *X, int M, float *Y, void *s
     // rows beyond the activation buffers go through in chunks of max_batch
     for (int r0 = 0; r0 < M; r0 += m->max_batch) {
         const int rows = std::min(m->max_batch, M - r0);
-        const int rc = mlp_forward(m, Xb + (size_t)r0 * kXW, rows, Y + (size_t)r0 * kOutP, s);
+        const int rc = mlp_forward(m, Xb + (size_t)r0 * kXW, rows, Y + (size_t)r0 * kOutP, s, false);
         if (rc != WX_OK) return mfail(m, rc, m->err);
     }
     return WX_OK;
@@ -882,51 +943,110 @@ extern "C" int wx_mlp_status(wx_mlp *m) {
 // =====================================================================
 namespace wx {
 
-// Normalised BF16 feature rows [rows][256] of all nx*ny columns (raster
-// order j*nx + i) straight from the planar T*, q* planes.
-__global__ void __launch_bounds__(128) sur_features_kernel(const float *__restrict__ fld, int nx, int P, int R,
-                                                           const float *__restrict__ km,
-                                                           const float *__restrict__ lev,
-                                                           const float *__restrict__ norm,
-                                                           __nv_bfloat16 *__restrict__ X, long ncol, long rows) {
-    const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= rows) return;
-    uint4 *row = reinterpret_cast<uint4 *>(X + c * kXW);
-    if (c >= ncol) {
-        for (int g = 0; g < kXW / 8; ++g) row[g] = make_uint4(0, 0, 0, 0);
-        return;
-    }
-    const int j = (int)(c / nx), i = (int)(c % nx);
-    const size_t plane = (size_t)R * P;
-    const float *base = fld + (size_t)(j + 1) * P + i + kGhostX;
-    const float s = km ? km[c] : 1.f;
-#pragma unroll 1
-    for (int g = 0; g < kInP / 8; ++g) {
-        __align__(16) __nv_bfloat16 v[8], w[8];
+// Columns of a block of kSB consecutive raster columns staged in shared
+// memory, row-major [column][CS] = [T*_0..57 | q*_0..57 | pad], by
+// coalesced plane reads: thread t serves column t % kSB and every
+// (NTH / kSB)-th plane, its column's address computed once, all its loads
+// issued back to back (an unrolled loop with no dependence between them).
+constexpr int kSB = 64;          // columns per block of the feature / apply kernels
+constexpr int kCS = 2 * kNZ;     // staged values per column
+template <int NTH, int CS>
+__device__ __forceinline__ void stage_columns(float *tile, const float *__restrict__ fld, long r0, long ncol,
+                                              int nx, int P, size_t plane) {
+    static_assert(NTH % kSB == 0 && kCS % (NTH / kSB) == 0, "plane split");
+    constexpr int G = NTH / kSB, PER = kCS / G;
+    const int u = threadIdx.x % kSB, g = threadIdx.x / kSB;
+    const long c = r0 + u;
+    if (c < ncol) {
+        const int j = (int)(c / nx), i = (int)(c - (long)j * nx);
+        const float *src = fld + (size_t)(j + 1) * P + i + kGhostX;
+        float v[PER];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const int f = 8 * g + t;
-            float x = 0.f;
-            if (f < kIn) {
-                const int kind = f / kNZ, k = f % kNZ;
-                const float raw = kind == 0   ? base[(size_t)(2 * k) * plane]
-                                  : kind == 1 ? base[(size_t)(2 * k + 1) * plane]
-                                  : kind == 2 ? s * lev[k]
-                                              : lev[kNZ + k];
-                x = (raw - norm[f]) / norm[kInP + f];
-            }
-            v[t] = __float2bfloat16_rn(x);
-            w[t] = __float2bfloat16_rn(x - __bfloat162float(v[t]));
+        for (int n = 0; n < PER; ++n) v[n] = src[(size_t)(g + n * G) * plane];
+#pragma unroll
+        for (int n = 0; n < PER; ++n) {
+            const int p = g + n * G;                 // plane (k, f), f = p & 1
+            tile[u * CS + (p & 1) * kNZ + (p >> 1)] = v[n];
         }
-        row[g] = *reinterpret_cast<const uint4 *>(v);
-        row[kInP / 8 + g] = *reinterpret_cast<const uint4 *>(w);
+    } else {
+#pragma unroll 4
+        for (int n = 0; n < PER; ++n) {
+            const int p = g + n * G;
+            tile[u * CS + (p & 1) * kNZ + (p >> 1)] = 0.f;
+        }
     }
 }
 
-// One thread per column: denormalise the prediction, run the two residual
-// checks, write T^{n+1} (the prediction, or the exact column physics when a
-// check fails) over T* with the periodic ghost copies.
-__global__ void __launch_bounds__(128) sur_apply_kernel(float *__restrict__ fld, int nx, int ny, int P, int R,
+// Normalised feature rows [rows][512] ([hi | lo], see kXW) of all nx*ny
+// columns (raster order j*nx + i), straight from the planar T*, q* planes:
+// staged columns, then one thread per (row, 8-feature chunk) so that a warp
+// writes 512 contiguous bytes of a row.
+constexpr int kFeatThreads = 256;
+__global__ void __launch_bounds__(kFeatThreads) sur_features_kernel(const float *__restrict__ fld, int nx, int P,
+                                                                    int R, const float *__restrict__ km,
+                                                                    const float *__restrict__ lev,
+                                                                    const float *__restrict__ norm,
+                                                                    __nv_bfloat16 *__restrict__ X, long ncol,
+                                                                    long rows) {
+    __shared__ __align__(16) float tile[kSB * kCS];
+    __shared__ float smean[kInP], sinv[kInP], slev[2 * kNZ], skm[kSB];
+    const long r0 = (long)blockIdx.x * kSB;
+    for (int e = threadIdx.x; e < kInP; e += blockDim.x) {
+        smean[e] = norm[e];
+        sinv[e] = 1.f / norm[kInP + e];
+    }
+    for (int e = threadIdx.x; e < 2 * kNZ; e += blockDim.x) slev[e] = lev[e];
+    for (int e = threadIdx.x; e < kSB; e += blockDim.x) skm[e] = (km && r0 + e < ncol) ? km[r0 + e] : 1.f;
+    stage_columns<kFeatThreads, kCS>(tile, fld, r0, ncol, nx, P, (size_t)R * P);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kSB * (kInP / 8); e += blockDim.x) {
+        const int r = e / (kInP / 8), g = e % (kInP / 8);
+        const long row = r0 + r;
+        if (row >= rows) continue;
+        const bool live = row < ncol;
+        float raw[8];
+        if (8 * g + 8 <= kCS) {  // T*, q*: two 16-byte reads of the staged row
+            const float4 a = *reinterpret_cast<const float4 *>(&tile[r * kCS + 8 * g]);
+            const float4 b = *reinterpret_cast<const float4 *>(&tile[r * kCS + 8 * g + 4]);
+            raw[0] = a.x; raw[1] = a.y; raw[2] = a.z; raw[3] = a.w;
+            raw[4] = b.x; raw[5] = b.y; raw[6] = b.z; raw[7] = b.w;
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int f = 8 * g + u;
+                raw[u] = f < kCS ? tile[r * kCS + f]
+                         : f < 3 * kNZ ? skm[r] * slev[f - kCS]
+                         : f < kIn ? slev[kNZ + f - 3 * kNZ] : 0.f;
+            }
+        }
+        __align__(16) __nv_bfloat162 hi[4], lo[4];
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+            const int f = 8 * g + u;
+            const float x0 = (live && f < kIn) ? (raw[u] - smean[f]) * sinv[f] : 0.f;
+            const float x1 = (live && f + 1 < kIn) ? (raw[u + 1] - smean[f + 1]) * sinv[f + 1] : 0.f;
+            const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+            hi[u / 2] = h;
+            lo[u / 2] = __floats2bfloat162_rn(x0 - __low2float(h), x1 - __high2float(h));
+        }
+        __nv_bfloat16 *dst = X + row * kXW + 8 * g;
+        *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(hi);
+        *reinterpret_cast<uint4 *>(dst + kInP) = *reinterpret_cast<const uint4 *>(lo);
+    }
+}
+
+// Residual checks, fallback and T^{n+1} for a block of kSB columns: the
+// columns' T*, q* and their output rows are staged in shared memory; one
+// thread per column then runs the checks (and, for a rejected column, the
+// exact elimination, back substitution and scan) on shared data only, and
+// writes its new T column back with the periodic ghost copies (a warp's
+// stores to one plane are coalesced).  Row strides are odd, so a thread
+// walking its own row hits distinct banks.  Two threads per column share
+// the loads and stores; the first kSB threads do the per-column work.
+constexpr int kYS = kOut + 1;   // row stride of the staged outputs
+constexpr int kTS = kCS + 1;    // row stride of the staged columns
+constexpr int kApplyThreads = 2 * kSB;
+__global__ void __launch_bounds__(kApplyThreads) sur_apply_kernel(float *__restrict__ fld, int nx, int ny, int P, int R,
                                                         const float *__restrict__ km,
                                                         const Q4<float> *__restrict__ gtab,
                                                         const float *__restrict__ Y,
@@ -934,74 +1054,86 @@ __global__ void __launch_bounds__(128) sur_apply_kernel(float *__restrict__ fld,
                                                         float tol, long ncol,
                                                         unsigned long long *__restrict__ n_fallback,
                                                         unsigned *__restrict__ status) {
+    extern __shared__ __align__(16) float dsm[];
+    float *tile = dsm;                  // [kSB][kTS] T* | q*; T* is overwritten by T^{n+1}
+    float *ysm = dsm + kSB * kTS;       // [kSB][kYS] outputs, then scratch
     __shared__ Q4<float> sB[kNZ], sC[kNZ], sE[kNZ];
-    for (int e = threadIdx.x; e < kNZ; e += blockDim.x) {
+    __shared__ float smo[kOut], sso[kOut];
+    const int t = threadIdx.x;
+    const long r0 = (long)blockIdx.x * kSB;
+    const size_t plane = (size_t)R * P;
+    for (int e = t; e < kNZ; e += blockDim.x) {
         sB[e] = gtab[REC_B * kNZ + e];
         sC[e] = gtab[REC_C * kNZ + e];
         sE[e] = gtab[REC_E * kNZ + e];
     }
-    __syncthreads();
-    const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    bool reject = false;
-    if (c < ncol) {
-        const int j = (int)(c / nx), i = (int)(c % nx);
-        const size_t plane = (size_t)R * P;
-        float *base = fld + (size_t)(j + 1) * P + i + kGhostX;
-        const float s = km ? km[c] : 1.f;
-        const float *mo = norm + 2 * kInP, *so = norm + 3 * kInP;
-        const float4 *yr = reinterpret_cast<const float4 *>(Y + c * kOutP);
-        float ts[kNZ], q[kNZ], H[kNZ], r[kNZ];
+    for (int e = t; e < kOut; e += blockDim.x) {
+        smo[e] = norm[2 * kInP + e];
+        sso[e] = norm[3 * kInP + e];
+    }
+    {   // output rows: warp w reads rows 16 w .. 16 w + 15, one 464-byte row
+        // (29 lanes x 16 bytes) per load, all 16 loads in flight
+        constexpr int RPW = kSB / (kApplyThreads / 32);
+        const int w = t / 32, lane = t % 32;
+        float4 buf[RPW];
 #pragma unroll
-        for (int g = 0; g < kOut / 4; ++g) {
-            const float4 y4 = yr[g];
-            const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+        for (int n = 0; n < RPW; ++n) {
+            const long row = r0 + w * RPW + n;
+            buf[n] = (lane < kOut / 4 && row < ncol)
+                         ? reinterpret_cast<const float4 *>(Y + row * kOutP)[lane]
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int o = 4 * g + t;
-                const float v = fmaf(yv[t], so[o], mo[o]);
-                if (o < kNZ)
-                    H[o] = v;
-                else
-                    r[o - kNZ] = v;
+        for (int n = 0; n < RPW; ++n) {
+            if (lane < kOut / 4) {
+                float *d = ysm + (w * RPW + n) * kYS + 4 * lane;
+                d[0] = buf[n].x;
+                d[1] = buf[n].y;
+                d[2] = buf[n].z;
+                d[3] = buf[n].w;
             }
         }
-#pragma unroll
-        for (int k = 0; k < kNZ; ++k) {
-            ts[k] = base[(size_t)(2 * k) * plane];
-            q[k] = base[(size_t)(2 * k + 1) * plane];
-        }
+    }
+    stage_columns<kApplyThreads, kTS>(tile, fld, r0, ncol, nx, P, plane);
+    __syncthreads();
+    const long c = r0 + t;
+    bool reject = false, ok = true;
+    if (t < kSB && c < ncol) {
+        float *yr = ysm + t * kYS;
+        float *ts = tile + t * kTS, *qs = ts + kNZ;
+        for (int o = 0; o < kOut; ++o) yr[o] = fmaf(yr[o], sso[o], smo[o]);  // H_k | r_k
+        const float s = km ? km[c] : 1.f;
         // rho_vd: (A v - T*)_k = (v_k - T*_k) + a_k (v_{k-1} - v_k) + c_k (v_{k+1} - v_k)
-        // with v = T* + dt r; level differences of T* are taken first (exact
-        // in FP32 for neighbouring values) so that the small increments
-        // dt r never round against T ~ 300
+        // with v = T* + dt r; level differences of T* first (exact in FP32
+        // for neighbouring values) so that dt r never rounds against T ~ 300
         float num = 0.f, den = 0.f, sumH = 0.f, tau2 = 0.f;
         bool finite = true;
-#pragma unroll
+#pragma unroll 2
         for (int k = 0; k < kNZ; ++k) {
             const float ak = s * sE[k].x, ck = s * sE[k].y;
-            const float dtm = k > 0 ? ts[k - 1] - ts[k] : 0.f, dtp = k < kNZ - 1 ? ts[k + 1] - ts[k] : 0.f;
-            const float drm = k > 0 ? r[k - 1] - r[k] : 0.f, drp = k < kNZ - 1 ? r[k + 1] - r[k] : 0.f;
+            const float tk = ts[k], rk = yr[kNZ + k];
+            const float dtm = k > 0 ? ts[k - 1] - tk : 0.f, dtp = k < kNZ - 1 ? ts[k + 1] - tk : 0.f;
+            const float drm = k > 0 ? yr[kNZ + k - 1] - rk : 0.f, drp = k < kNZ - 1 ? yr[kNZ + k + 1] - rk : 0.f;
             const float e0 = ak * dtm + ck * dtp;
-            const float ex = e0 + dt * (r[k] + ak * drm + ck * drp);
+            const float ex = e0 + dt * (rk + ak * drm + ck * drp);
             num = fmaf(ex, ex, num);
             den = fmaf(e0, e0, den);
-            sumH = fmaf(H[k], sE[k].z, sumH);
-            tau2 = fmaf(sB[k].z, q[k], tau2);
-            finite = finite && isfinite(H[k]) && isfinite(r[k]);
+            sumH = fmaf(yr[k], sE[k].z, sumH);
+            tau2 = fmaf(sB[k].z, qs[k], tau2);
+            finite = finite && isfinite(yr[k]) && isfinite(rk);
         }
         const float absorbed = S0 * (1.f - exp2f(-tau2));
         const float rvd = den > 0.f ? sqrtf(num / den) : (num == 0.f ? 0.f : INFINITY);
         const float rH = absorbed > 0.f ? fabsf(sumH - absorbed) / absorbed : (sumH == 0.f ? 0.f : INFINITY);
         reject = !(finite && rvd <= tol && rH <= tol);
-        float tn[kNZ];
         if (!reject) {
-#pragma unroll
-            for (int k = 0; k < kNZ; ++k) tn[k] = ts[k] + dt * (r[k] + H[k]);
+            for (int k = 0; k < kNZ; ++k) ts[k] = ts[k] + dt * (yr[kNZ + k] + yr[k]);
         } else {
-            // exact column: forward elimination, back substitution with the
-            // heating of the optical-depth scan from the top
-            float cp[kNZ], dp[kNZ], cpp = 0.f, dpp = 0.f;
-#pragma unroll
+            // exact column: forward elimination (c'_k, d'_k in the row's
+            // scratch), back substitution with the heating of the
+            // optical-depth scan from the top
+            float *cp = yr, *dp = yr + kNZ;
+            float cpp = 0.f, dpp = 0.f;
             for (int k = 0; k < kNZ; ++k) {
                 const float ak = s * sE[k].x, ck = s * sE[k].y;
                 const float m = ((1.f - ak) - ck) - ak * cpp;
@@ -1012,32 +1144,37 @@ __global__ void __launch_bounds__(128) sur_apply_kernel(float *__restrict__ fld,
                 dp[k] = dpp;
             }
             float x = 0.f, tau = 0.f, Etop = 1.f;
-#pragma unroll
             for (int k = kNZ - 1; k >= 0; --k) {
                 x = dp[k] - cp[k] * x;
-                const float taub = tau + sB[k].z * q[k];
+                const float taub = tau + sB[k].z * qs[k];
                 const float Eb = exp2f(-taub);
-                tn[k] = x + sC[k].x * (Etop - Eb);
+                ts[k] = x + sC[k].x * (Etop - Eb);
                 Etop = Eb;
                 tau = taub;
             }
         }
-        bool ok = true;
-#pragma unroll
-        for (int k = 0; k < kNZ; ++k) {
-            const float v = tn[k];
-            ok = ok && isfinite(v);
-            float *row = base + (size_t)(2 * k) * plane;
-            row[0] = v;
-            if (i == 0) row[nx] = v;            // -> right ghost column
-            if (i == nx - 1) row[-nx] = v;      // -> left ghost column
-            if (j == 0) row[(size_t)ny * P] = v;          // -> top ghost row
-            if (j == ny - 1) row[-(long)ny * P] = v;      // -> bottom ghost row
-        }
-        if (!ok) atomicOr(status, ST_NONFINITE);
+        for (int k = 0; k < kNZ; ++k) ok = ok && isfinite(ts[k]);
     }
     const int nrej = __syncthreads_count(reject);
-    if (threadIdx.x == 0 && nrej) atomicAdd(n_fallback, (unsigned long long)nrej);
+    if (!__syncthreads_and(ok) && t == 0) atomicOr(status, ST_NONFINITE);
+    if (t == 0 && nrej) atomicAdd(n_fallback, (unsigned long long)nrej);
+    const int u = t % kSB, half = t / kSB;
+    const long cu = r0 + u;
+    if (cu < ncol) {
+        const int j = (int)(cu / nx), i = (int)(cu - (long)j * nx);
+        float *col = fld + (size_t)(j + 1) * P + i + kGhostX;
+        const float *ts = tile + u * kTS;
+#pragma unroll 4
+        for (int k = half; k < kNZ; k += kApplyThreads / kSB) {
+            const float v = ts[k];
+            float *row = col + (size_t)(2 * k) * plane;
+            row[0] = v;
+            if (i == 0) row[nx] = v;                   // -> right ghost column
+            if (i == nx - 1) row[-nx] = v;             // -> left ghost column
+            if (j == 0) row[(size_t)ny * P] = v;       // -> top ghost row
+            if (j == ny - 1) row[-(long)ny * P] = v;   // -> bottom ghost row
+        }
+    }
 }
 
 void free_surrogate(wx_ctx *c) {
@@ -1076,12 +1213,12 @@ int launch_surrogate_step(wx_ctx *c, cudaStream_t s, long *launches) {
     const long ncol = (long)c->nx * c->ny, rows = c->sur_rows;
     cudaMemsetAsync(c->sur_nfb, 0, sizeof(unsigned long long), s);
     // 2. features
-    sur_features_kernel<<<(unsigned)(rows / 128), 128, 0, s>>>(f, c->nx, c->P, c->R, (const float *)c->kmult,
+    sur_features_kernel<<<(unsigned)((rows + kSB - 1) / kSB), kFeatThreads, 0, s>>>(f, c->nx, c->P, c->R, (const float *)c->kmult,
                                                                c->sur_lev, m->norm,
                                                                reinterpret_cast<__nv_bfloat16 *>(c->sur_X), ncol, rows);
-    // 3. the network, in chunks of at most 65535 row tiles
+    // 3. the network (persistent GEMMs over all rows)
     std::string err;
-    const long chunk = 65535L * 128;
+    const long chunk = rows;
     for (long r0 = 0; r0 < rows; r0 += chunk) {
         const int M = (int)std::min(chunk, rows - r0);
         const __nv_bfloat16 *X = reinterpret_cast<const __nv_bfloat16 *>(c->sur_X) + r0 * kXW;
@@ -1102,7 +1239,13 @@ int launch_surrogate_step(wx_ctx *c, cudaStream_t s, long *launches) {
         *launches += 4;
     }
     // 4. residual checks, fallback, T^{n+1}
-    sur_apply_kernel<<<(unsigned)((ncol + 127) / 128), 128, 0, s>>>(
+    constexpr int apply_smem = kSB * (kTS + kYS) * (int)sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(sur_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, apply_smem);
+        attr = true;
+    }
+    sur_apply_kernel<<<(unsigned)((ncol + kSB - 1) / kSB), kApplyThreads, apply_smem, s>>>(
         f, c->nx, c->ny, c->P, c->R, (const float *)c->kmult, (const Q4<float> *)c->tab, c->sur_Y, m->norm,
         (float)c->dt, (float)c->S0, (float)c->sur_tol, ncol, c->sur_nfb, c->d_status);
     *launches += 2;

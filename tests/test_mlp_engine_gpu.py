@@ -177,7 +177,7 @@ def test_fit_norm_and_prepare_match_oracle(net):
     net.prepare(Tsd, qsd, kmd, td, X, Yt)
     Xg = X.float().cpu().numpy().astype(np.float64)
     # the same FP32 normalisation on both sides, then the two-term expansion
-    hi, lo = omlp.bf16_pair((F.astype(np.float32) - mi) / si)
+    hi, lo = omlp.bf16_pair((F.astype(np.float32) - mi) * (np.float32(1) / si))
     assert np.array_equal(Xg[:n, :232], hi) and np.array_equal(Xg[:n, 256:488], lo)
     assert np.all(Xg[n:] == 0) and np.all(Xg[:, 232:256] == 0) and np.all(Xg[:, 488:] == 0)
     Yo = (f32(tend).reshape(n, -1) - mo) / so

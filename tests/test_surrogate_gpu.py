@@ -78,7 +78,7 @@ def test_accepted_predictions_match_the_mlp_oracle():
     F = omlp.raw_features(f32(Tc), f32(qc), None, f32(c.kappa_lev), 1.0,
                           f32(np.asarray(c.alpha) * np.asarray(c.dz)))
     mi, si, mo, so = net.get_norm()
-    X = ((F.astype(np.float32) - mi) / si).astype(np.float64)  # FP32 values; split by forward
+    X = ((F.astype(np.float32) - mi) * (np.float32(1) / si)).astype(np.float64)  # FP32; split by forward
     Ws, bs = net.get_weights()
     Y, _ = omlp.forward([W.astype(np.float64) for W in Ws], [b.astype(np.float64) for b in bs], X)
     y = Y * so + mo

@@ -1,7 +1,7 @@
 """Training the column-physics surrogate with the library's own kernels and
 what the trained network gains.
 
-Training data: 1M columns of four seeded paper-grid-generator states that
+Training data: 2M columns of eight seeded paper-grid-generator states that
 share the served model configuration, with FP64 tendencies; validation on
 a held-out state.  The target is a relative L2 tendency error of at most
 2e-2 in physical units (heating and vertical-diffusion rate together); the
@@ -22,7 +22,7 @@ torch = pytest.importorskip("torch")
 
 @pytest.fixture(scope="module")
 def trained():
-    Ts, qs, km, tend = S.dataset(range(1, 5), 512, 512)
+    Ts, qs, km, tend = S.dataset(range(1, 9), 512, 512)
     m = wx.MLP(4096)
     Ws, bs = inputs.mlp_init(2024)
     m.set_weights(Ws, bs)
