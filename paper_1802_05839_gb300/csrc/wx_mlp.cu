@@ -943,13 +943,94 @@ extern "C" int wx_mlp_status(wx_mlp *m) {
 // =====================================================================
 namespace wx {
 
+constexpr int kSB = 64;          // columns per block of the feature and apply kernels
+constexpr int kCS = 2 * kNZ;     // T* and q* values per column
+constexpr int kCH = kInP / 8;    // 8-feature chunks per input row (32)
+constexpr int kSC = (kCS + 7) / 8;  // chunks holding staged T*, q* (15)
+constexpr int kFS = 8 * kSC + 1;    // staged row stride (odd)
+
+// Normalised feature rows [rows][512] ([hi | lo], see kXW) of all nx*ny
+// columns (raster order j*nx + i), straight from the planar T*, q* planes.
+// Staging: thread t serves column t % kSB and every (threads / kSB)-th
+// plane, its column's address computed once and all its loads issued back
+// to back; value f of a column lands at (f % 8) kSC + f / 8 of its row, so
+// that in the second phase -- one thread per (row, 8-feature chunk), a
+// warp covering one row and writing its 512 contiguous bytes -- lanes read
+// consecutive words.  Per-feature constants use the same [f % 8][f / 8]
+// order; the inputs past T*, q* are s fa_f + fb_f (s = kappa_mult).
+constexpr int kFeatThreads = 256;
+__global__ void __launch_bounds__(kFeatThreads) sur_features_kernel(const float *__restrict__ fld, int nx, int P,
+                                                                    int R, const float *__restrict__ km,
+                                                                    const float *__restrict__ lev,
+                                                                    const float *__restrict__ norm,
+                                                                    __nv_bfloat16 *__restrict__ X, long ncol,
+                                                                    long rows) {
+    __shared__ float tile[kSB * kFS];
+    __shared__ float smean[kInP], sinv[kInP], sfa[kInP], sfb[kInP], skm[kSB];
+    const long r0 = (long)blockIdx.x * kSB;
+    for (int f = threadIdx.x; f < kInP; f += blockDim.x) {
+        const int d = (f % 8) * kCH + f / 8;
+        smean[d] = f < kIn ? norm[f] : 0.f;
+        sinv[d] = f < kIn ? 1.f / norm[kInP + f] : 0.f;
+        sfa[d] = (f >= kCS && f < 3 * kNZ) ? lev[f - kCS] : 0.f;
+        sfb[d] = (f >= 3 * kNZ && f < kIn) ? lev[kNZ + f - 3 * kNZ] : 0.f;
+    }
+    for (int e = threadIdx.x; e < kSB; e += blockDim.x) skm[e] = (km && r0 + e < ncol) ? km[r0 + e] : 1.f;
+    {
+        constexpr int G = kFeatThreads / kSB, PER = kCS / G;
+        static_assert(kFeatThreads % kSB == 0 && kCS % G == 0, "plane split");
+        const int u = threadIdx.x % kSB, g = threadIdx.x / kSB;
+        const long c = r0 + u;
+        const size_t plane = (size_t)R * P;
+        float v[PER];
+        if (c < ncol) {
+            const int j = (int)(c / nx), i = (int)(c - (long)j * nx);
+            const float *src = fld + (size_t)(j + 1) * P + i + kGhostX;
+#pragma unroll
+            for (int n = 0; n < PER; ++n) v[n] = src[(size_t)(g + n * G) * plane];
+        } else {
+#pragma unroll
+            for (int n = 0; n < PER; ++n) v[n] = 0.f;
+        }
+#pragma unroll
+        for (int n = 0; n < PER; ++n) {
+            const int p = g + n * G, f = (p & 1) * kNZ + (p >> 1);  // plane (k, field) -> feature
+            tile[u * kFS + (f % 8) * kSC + f / 8] = v[n];
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kSB * kCH; e += blockDim.x) {
+        const int r = e / kCH, g = e % kCH;
+        const long row = r0 + r;
+        if (row >= rows) continue;
+        const float live = row < ncol ? 1.f : 0.f;
+        const float s = skm[r];
+        __align__(16) __nv_bfloat162 hi[4], lo[4];
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+            float x[2];
+#pragma unroll
+            for (int w = 0; w < 2; ++w) {
+                const int d = (u + w) * kCH + g;
+                const float staged = 8 * g + u + w < kCS ? tile[r * kFS + (u + w) * kSC + g] : 0.f;
+                const float raw = staged + s * sfa[d] + sfb[d];
+                x[w] = live * ((raw - smean[d]) * sinv[d]);
+            }
+            const __nv_bfloat162 h = __floats2bfloat162_rn(x[0], x[1]);
+            hi[u / 2] = h;
+            lo[u / 2] = __floats2bfloat162_rn(x[0] - __low2float(h), x[1] - __high2float(h));
+        }
+        __nv_bfloat16 *dst = X + row * kXW + 8 * g;
+        *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(hi);
+        *reinterpret_cast<uint4 *>(dst + kInP) = *reinterpret_cast<const uint4 *>(lo);
+    }
+}
+
 // Columns of a block of kSB consecutive raster columns staged in shared
-// memory, row-major [column][CS] = [T*_0..57 | q*_0..57 | pad], by
+// memory for the apply kernel, row-major [column][CS] = [T*_0..57 | q*_0..57 | pad], by
 // coalesced plane reads: thread t serves column t % kSB and every
 // (NTH / kSB)-th plane, its column's address computed once, all its loads
 // issued back to back (an unrolled loop with no dependence between them).
-constexpr int kSB = 64;          // columns per block of the feature / apply kernels
-constexpr int kCS = 2 * kNZ;     // staged values per column
 template <int NTH, int CS>
 __device__ __forceinline__ void stage_columns(float *tile, const float *__restrict__ fld, long r0, long ncol,
                                               int nx, int P, size_t plane) {
@@ -974,64 +1055,6 @@ __device__ __forceinline__ void stage_columns(float *tile, const float *__restri
             const int p = g + n * G;
             tile[u * CS + (p & 1) * kNZ + (p >> 1)] = 0.f;
         }
-    }
-}
-
-// Normalised feature rows [rows][512] ([hi | lo], see kXW) of all nx*ny
-// columns (raster order j*nx + i), straight from the planar T*, q* planes:
-// staged columns, then one thread per (row, 8-feature chunk) so that a warp
-// writes 512 contiguous bytes of a row.
-constexpr int kFeatThreads = 256;
-__global__ void __launch_bounds__(kFeatThreads) sur_features_kernel(const float *__restrict__ fld, int nx, int P,
-                                                                    int R, const float *__restrict__ km,
-                                                                    const float *__restrict__ lev,
-                                                                    const float *__restrict__ norm,
-                                                                    __nv_bfloat16 *__restrict__ X, long ncol,
-                                                                    long rows) {
-    __shared__ __align__(16) float tile[kSB * kCS];
-    __shared__ float smean[kInP], sinv[kInP], slev[2 * kNZ], skm[kSB];
-    const long r0 = (long)blockIdx.x * kSB;
-    for (int e = threadIdx.x; e < kInP; e += blockDim.x) {
-        smean[e] = norm[e];
-        sinv[e] = 1.f / norm[kInP + e];
-    }
-    for (int e = threadIdx.x; e < 2 * kNZ; e += blockDim.x) slev[e] = lev[e];
-    for (int e = threadIdx.x; e < kSB; e += blockDim.x) skm[e] = (km && r0 + e < ncol) ? km[r0 + e] : 1.f;
-    stage_columns<kFeatThreads, kCS>(tile, fld, r0, ncol, nx, P, (size_t)R * P);
-    __syncthreads();
-    for (int e = threadIdx.x; e < kSB * (kInP / 8); e += blockDim.x) {
-        const int r = e / (kInP / 8), g = e % (kInP / 8);
-        const long row = r0 + r;
-        if (row >= rows) continue;
-        const bool live = row < ncol;
-        float raw[8];
-        if (8 * g + 8 <= kCS) {  // T*, q*: two 16-byte reads of the staged row
-            const float4 a = *reinterpret_cast<const float4 *>(&tile[r * kCS + 8 * g]);
-            const float4 b = *reinterpret_cast<const float4 *>(&tile[r * kCS + 8 * g + 4]);
-            raw[0] = a.x; raw[1] = a.y; raw[2] = a.z; raw[3] = a.w;
-            raw[4] = b.x; raw[5] = b.y; raw[6] = b.z; raw[7] = b.w;
-        } else {
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int f = 8 * g + u;
-                raw[u] = f < kCS ? tile[r * kCS + f]
-                         : f < 3 * kNZ ? skm[r] * slev[f - kCS]
-                         : f < kIn ? slev[kNZ + f - 3 * kNZ] : 0.f;
-            }
-        }
-        __align__(16) __nv_bfloat162 hi[4], lo[4];
-#pragma unroll
-        for (int u = 0; u < 8; u += 2) {
-            const int f = 8 * g + u;
-            const float x0 = (live && f < kIn) ? (raw[u] - smean[f]) * sinv[f] : 0.f;
-            const float x1 = (live && f + 1 < kIn) ? (raw[u + 1] - smean[f + 1]) * sinv[f + 1] : 0.f;
-            const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
-            hi[u / 2] = h;
-            lo[u / 2] = __floats2bfloat162_rn(x0 - __low2float(h), x1 - __high2float(h));
-        }
-        __nv_bfloat16 *dst = X + row * kXW + 8 * g;
-        *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(hi);
-        *reinterpret_cast<uint4 *>(dst + kInP) = *reinterpret_cast<const uint4 *>(lo);
     }
 }
 
