@@ -81,6 +81,9 @@ def lib():
         L.wxo_column_weighted_sum.restype = ctypes.c_double
         L.wxo_threads.restype = ctypes.c_int
         L.wxo_set_threads.argtypes = [ctypes.c_int]
+        PP = ctypes.POINTER(PFParams)
+        L.wxo_pf_step.argtypes = [PP, _D, _D]
+        L.wxo_pf_run.argtypes = [PP, ctypes.c_int, _D]
         _lib = L
     return _lib
 
@@ -209,3 +212,31 @@ def physics_columns(nz, dt, dz, kappa_lev, kappa_mult, alpha, S0, q_ref, Ts, qs,
                               float(S0), float(q_ref), _ptr(Ts), _ptr(qs),
                               _ptr(Tout), _ptr(tend))
     return (Tout, tend) if with_tend else Tout
+
+
+# ------------------------------------------------------------------
+# The paper's reduced weather application (wxo_pf_* in wx_oracle.h)
+class PFParams(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("d", ctypes.c_double), ("radiation", ctypes.c_double),
+                ("transfer", ctypes.c_double), ("T_surf", ctypes.c_double),
+                ("T_pbl", ctypes.c_double)]
+
+
+def pf_params(nx, ny, nz, d=0.1, radiation=0.1, transfer=0.01, T_surf=330.0, T_pbl=200.0):
+    return PFParams(int(nx), int(ny), int(nz), float(d), float(radiation), float(transfer),
+                    float(T_surf), float(T_pbl))
+
+
+def pf_step(p, E):
+    """One step of the reduced application; E is [nz][ny+2][nx+2]."""
+    E = _f64(E)
+    En = np.empty_like(E)
+    lib().wxo_pf_step(ctypes.byref(p), _ptr(E), _ptr(En))
+    return En
+
+
+def pf_run(p, n_steps, E):
+    E = _f64(E).copy()
+    lib().wxo_pf_run(ctypes.byref(p), int(n_steps), _ptr(E))
+    return E

@@ -294,3 +294,97 @@ void wxo_run(const wxo_params *p, int n_steps, double *T, double *q,
         free(qn);
     }
 }
+
+/* ---------------------------------------------------------------------
+ * The paper's reduced weather application (appendix listings), step by
+ * step in the listings' order: physics in place on every column, then the
+ * four diffusion regions into the new array.
+ * ------------------------------------------------------------------- */
+#define PF_AT(p, E, i, j, k) (E)[((size_t)(k) * ((p)->ny + 2) + (size_t)(j)) * ((p)->nx + 2) + (size_t)(i)]
+
+static void pf_physics(const wxo_pf_params *p, double *E) {
+    const int nx = p->nx, ny = p->ny, nz = p->nz;
+    long col;
+    const long ncol = (long)(nx + 2) * (ny + 2);
+#pragma omp parallel for num_threads(wxo_threads()) schedule(static)
+    for (col = 0; col < ncol; ++col) {
+        const int i = (int)(col % (nx + 2)), j = (int)(col / (nx + 2));
+        /* radiate: uniform heat input on every level */
+        for (int k = 0; k < nz; ++k) PF_AT(p, E, i, j, k) = PF_AT(p, E, i, j, k) + p->radiation;
+        /* exchange_heat_with_boundary at the surface, then at the top */
+        {
+            const double x = PF_AT(p, E, i, j, 0);
+            const double flux = p->transfer * (x - p->T_surf);
+            PF_AT(p, E, i, j, 0) = x - flux;
+        }
+        {
+            const double x = PF_AT(p, E, i, j, nz - 1);
+            const double flux = p->transfer * (x - p->T_pbl);
+            PF_AT(p, E, i, j, nz - 1) = x - flux;
+        }
+    }
+}
+
+static void pf_diffuse(const wxo_pf_params *p, const double *E, double *En) {
+    const int nx = p->nx, ny = p->ny, nz = p->nz;
+    const double d = p->d;
+    int j;
+    /* inner region */
+#pragma omp parallel for num_threads(wxo_threads()) schedule(static)
+    for (j = 1; j <= ny; ++j)
+        for (int i = 1; i <= nx; ++i)
+            for (int k = 1; k < nz - 1; ++k)
+                PF_AT(p, En, i, j, k) = PF_AT(p, E, i, j, k) * (1.0 - 6 * d) +
+                                        d * (PF_AT(p, E, i - 1, j, k) + PF_AT(p, E, i + 1, j, k) +
+                                             PF_AT(p, E, i, j - 1, k) + PF_AT(p, E, i, j + 1, k) +
+                                             PF_AT(p, E, i, j, k - 1) + PF_AT(p, E, i, j, k + 1));
+    /* bottom and top levels: one vertical neighbour */
+#pragma omp parallel for num_threads(wxo_threads()) schedule(static)
+    for (j = 1; j <= ny; ++j)
+        for (int i = 1; i <= nx; ++i) {
+            PF_AT(p, En, i, j, 0) = (1.0 - 5 * d) * PF_AT(p, E, i, j, 0) +
+                                    d * (PF_AT(p, E, i - 1, j, 0) + PF_AT(p, E, i + 1, j, 0) +
+                                         PF_AT(p, E, i, j - 1, 0) + PF_AT(p, E, i, j + 1, 0) +
+                                         PF_AT(p, E, i, j, 1));
+            PF_AT(p, En, i, j, nz - 1) = (1.0 - 5 * d) * PF_AT(p, E, i, j, nz - 1) +
+                                         d * (PF_AT(p, E, i - 1, j, nz - 1) + PF_AT(p, E, i + 1, j, nz - 1) +
+                                              PF_AT(p, E, i, j - 1, nz - 1) + PF_AT(p, E, i, j + 1, nz - 1) +
+                                              PF_AT(p, E, i, j, nz - 2));
+        }
+    /* ghost rows j = 0 and j = ny+1 */
+    for (int i = 0; i <= nx + 1; ++i)
+        for (int k = 0; k < nz; ++k) {
+            PF_AT(p, En, i, 0, k) = (1.0 - 2 * d) * PF_AT(p, E, i, 0, k) +
+                                    d * (PF_AT(p, E, i, 1, k) + PF_AT(p, E, i, ny + 1, k));
+            PF_AT(p, En, i, ny + 1, k) = (1.0 - 2 * d) * PF_AT(p, E, i, ny + 1, k) +
+                                         d * (PF_AT(p, E, i, ny, k) + PF_AT(p, E, i, 0, k));
+        }
+    /* ghost columns i = 0 and i = nx+1 (the corners end with this rule) */
+    for (j = 0; j <= ny + 1; ++j)
+        for (int k = 0; k < nz; ++k) {
+            PF_AT(p, En, 0, j, k) = (1.0 - 2 * d) * PF_AT(p, E, 0, j, k) +
+                                    d * (PF_AT(p, E, 1, j, k) + PF_AT(p, E, nx + 1, j, k));
+            PF_AT(p, En, nx + 1, j, k) = (1.0 - 2 * d) * PF_AT(p, E, nx + 1, j, k) +
+                                         d * (PF_AT(p, E, nx, j, k) + PF_AT(p, E, 0, j, k));
+        }
+}
+
+void wxo_pf_step(const wxo_pf_params *p, const double *E, double *En) {
+    const size_t n = (size_t)(p->nx + 2) * (p->ny + 2) * p->nz;
+    double *W = (double *)malloc(sizeof(double) * n);
+    memcpy(W, E, sizeof(double) * n);
+    pf_physics(p, W);
+    pf_diffuse(p, W, En);
+    free(W);
+}
+
+void wxo_pf_run(const wxo_pf_params *p, int n_steps, double *E) {
+    const size_t n = (size_t)(p->nx + 2) * (p->ny + 2) * p->nz;
+    double *En = (double *)malloc(sizeof(double) * n);
+    for (int s = 0; s < n_steps; ++s) {
+        pf_physics(p, E);
+        pf_diffuse(p, E, En);
+        memcpy(E, En, sizeof(double) * n);
+    }
+    free(En);
+}

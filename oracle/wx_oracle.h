@@ -105,6 +105,44 @@ void wxo_run(const wxo_params *p, int n_steps, double *T, double *q,
 double wxo_column_weighted_sum(const wxo_params *p, const double *phi);
 
 /* Threads the oracle's parallel loops use (1 when built without OpenMP). */
+
+/* ---------------------------------------------------------------------
+ * The paper's reduced weather application, as its listings state it
+ * (Sec. 3.1, Eq. 1; appendix: diffusion, physical processes, radiation,
+ * heat exchange, time integration).  The field E has a ghost ring that is
+ * state of its own: E[k][j][i] with i in [0, nx+2), j in [0, ny+2), k in
+ * [0, nz) (k = 0 is the listing's level 1), nz >= 2.  One step:
+ *   physics on every column (i, j) of the whole (nx+2) x (ny+2) plane:
+ *     E(k) += radiation                                   (radiate)
+ *     E(0)    -= transfer (E(0)    - T_surf)              (surface well)
+ *     E(nz-1) -= transfer (E(nz-1) - T_pbl)               (planetary well)
+ *   then diffusion into a new array (d = diffusion_velocity):
+ *     interior i in 1..nx, j in 1..ny, 0 < k < nz-1:
+ *       (1 - 6d) E + d (E_i-1 + E_i+1 + E_j-1 + E_j+1 + E_k-1 + E_k+1)
+ *     k = 0 and k = nz-1, same i, j: (1 - 5d) E + d (4 horizontal + the
+ *       one vertical neighbour)
+ *     ghost rows j = 0, ny+1 for i in 0..nx+1, every k:
+ *       (1 - 2d) E(i,0) + d (E(i,1) + E(i,ny+1)),
+ *       (1 - 2d) E(i,ny+1) + d (E(i,ny) + E(i,0))
+ *     ghost columns i = 0, nx+1 for j in 0..ny+1, every k (written last,
+ *       so the four corner columns take this rule):
+ *       (1 - 2d) E(0,j) + d (E(1,j) + E(nx+1,j)),
+ *       (1 - 2d) E(nx+1,j) + d (E(nx,j) + E(0,j))
+ * ------------------------------------------------------------------- */
+typedef struct {
+    int nx, ny, nz;
+    double d;          /* diffusion_velocity */
+    double radiation;  /* radiation_intensity, added every step */
+    double transfer;   /* transfer_velocity of the two heat wells */
+    double T_surf;     /* surface heat well (level 0) */
+    double T_pbl;      /* planetary-boundary heat well (level nz-1) */
+} wxo_pf_params;
+
+/* One step E -> En (arrays of (nx+2)(ny+2)nz doubles, layout above). */
+void wxo_pf_step(const wxo_pf_params *p, const double *E, double *En);
+/* n steps in place (ping-pong through a scratch copy). */
+void wxo_pf_run(const wxo_pf_params *p, int n_steps, double *E);
+
 int wxo_threads(void);
 void wxo_set_threads(int n);
 

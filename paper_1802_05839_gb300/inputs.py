@@ -286,3 +286,14 @@ def mlp_init(seed: int = 2024):
 def column_sample(ncol_total: int, n: int, seed: int, stream: int = 200) -> np.ndarray:
     """n distinct-ish column indices drawn uniformly from [0, ncol_total)."""
     return np.minimum((uniform(seed, stream, n) * ncol_total).astype(np.int64), ncol_total - 1)
+
+
+# ------------------------------------------------- reduced application
+def paper_box_state(nx: int, ny: int, nz: int, T_box: float = 300.0) -> np.ndarray:
+    """The reduced application's initial state (Sec. 3.1): 0 K everywhere and
+    T_box inside the box from one quarter to three quarters of each
+    dimension, read as the interior indices [n/4, 3n/4) (0-based) of each
+    axis; the ghost ring starts at 0 K.  Layout [nz][ny+2][nx+2]."""
+    E = np.zeros((nz, ny + 2, nx + 2))
+    E[nz // 4:(3 * nz) // 4, 1 + ny // 4:1 + (3 * ny) // 4, 1 + nx // 4:1 + (3 * nx) // 4] = T_box
+    return E
