@@ -15,10 +15,11 @@ HBM copy bandwidth; `cpu_baseline` times the FP64 CPU oracle on a bounded
 sample of the same workload on this host's cores.  `variants` holds the
 other measured configurations of the same hot path: the FP64 step, the
 mixed-precision step with FP64 sums, the 16-member ensemble replayed from a
-CUDA graph, and the residual-checked MLP-surrogate step (network trained in
-this run by the library's kernels) against the plain step.
+CUDA graph, the residual-checked MLP-surrogate step (network trained in this
+run by the library's kernels) against the plain step, and the paper's own
+reduced weather application on its three grids beside the paper's timings.
 
-  python bench.py --only f64|mixed|ensemble|surrogate [--nx --ny]   one variant
+  python bench.py --only f64|mixed|ensemble|surrogate|reduced_app [--nx --ny]   one variant
 """
 from __future__ import annotations
 
@@ -355,6 +356,49 @@ def variant_surrogate(steps, nx=1581, ny=1301, plain_ms=None, train_epochs=32):
     return out
 
 
+# The paper's own timings of its reduced weather application, 100 steps,
+# FP64 (Sec. 5.1, block-size and performance tables): Tesla K20x with the
+# Hybrid Fortran default 32 x 16 blocks, and a 6-core Xeon X5670.
+PAPER_REDUCED_S = {(128, 128, 128): {"k20x_s": 0.10, "x5670_6core_s": 0.40},
+                   (256, 256, 256): {"k20x_s": 0.55, "x5670_6core_s": 4.25},
+                   (256, 256, 512): {"k20x_s": 2.16}}
+
+
+def variant_reduced_app(steps=100):
+    """The paper's reduced application (wx_pf_*) on its three grids, 100
+    steps from the 300 K box state; device-resident time and the time with
+    the state copied in and out (the paper's GPU times include the copies)."""
+    import torch
+    from paper_1802_05839_gb300 import inputs, wx
+    out = {}
+    for (nx, ny, nz), ref in PAPER_REDUCED_S.items():
+        E = inputs.paper_box_state(nx, ny, nz)
+        rec = {"paper": ref}
+        for dtype in ("f64", "f32"):
+            app = wx.ReducedApp(nx, ny, nz, dtype)
+            app.set_params()
+            app.load(E)
+            st = torch.cuda.Stream()
+            ms = _time_steps(lambda: app.step(steps, stream=st), 1, st) / steps
+            app.sync()
+            t0 = time.perf_counter()
+            app.load(E)
+            app.step(steps, stream=st)
+            app.sync()
+            app.read()
+            e2e_s = time.perf_counter() - t0
+            app.close()
+            cells = nx * ny * nz
+            r = {"ms_per_step": ms, "value": cells / (ms * 1e-3), "unit": "cell-steps/s",
+                 "s_per_100_steps_device": ms * 0.1, "s_per_100_steps_with_copies": e2e_s,
+                 "hbm_frac": cells * (16 if dtype == "f64" else 8) / (ms * 1e-3) / 1e9 / peaks()[0]}
+            if dtype == "f64":
+                r["vs_paper_k20x"] = ref["k20x_s"] / e2e_s
+            rec[dtype] = r
+        out[f"{nx}x{ny}x{nz}"] = rec
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -447,6 +491,7 @@ def run_ours(args):
             "mixed": variant_plain("mixed", 500),
             "ensemble": variant_ensemble(200),
             "surrogate": variant_surrogate(100, plain_ms=ms, train_epochs=args.epochs),
+            "reduced_app": variant_reduced_app(100),
         }
     print(json.dumps(out))
 
@@ -465,7 +510,7 @@ def main():
     ap.add_argument("--nz", type=int, default=58, help="grid override (profiling captures only)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--epochs", type=int, default=32, help="surrogate training epochs")
-    ap.add_argument("--only", choices=["f64", "mixed", "ensemble", "surrogate"],
+    ap.add_argument("--only", choices=["f64", "mixed", "ensemble", "surrogate", "reduced_app"],
                     help="run one variant alone and print its record (profiling captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -479,6 +524,8 @@ def main():
             rec = variant_plain(args.only, args.steps, args.nx, args.ny, args.nz)
         elif args.only == "ensemble":
             rec = variant_ensemble(args.steps)
+        elif args.only == "reduced_app":
+            rec = variant_reduced_app(args.steps)
         else:
             rec = variant_surrogate(args.steps, args.nx, args.ny, train_epochs=args.epochs)
         print(json.dumps({"variant": args.only, **rec}))

@@ -188,6 +188,40 @@ int wx_sums_noalloc(const void *T, const void *q, int dtype, int nx, int ny,
 /* Message of the last failing wx_sums_noalloc call on this host thread. */
 const char *wx_sums_noalloc_error(void);
 
+/* ------------------------------------------- the paper's reduced application
+ * The reduced weather application of Sec. 3.1 (Eq. 1, explicit Euler) with
+ * the semantics of its appendix listings, for comparison with the paper's
+ * own timings (Sec. 5.1): the state E[k][j][i], i in [0, nx+2), j in
+ * [0, ny+2), k in [0, nz), includes a ghost ring that evolves by its own
+ * two-neighbour rule; each step applies the physics (radiation added to
+ * every level; Newtonian heat wells at the bottom and top levels) to every
+ * column, then the diffusion (7-point interior rule, 1 - 5d at the bottom
+ * and top levels, 1 - 2d two-neighbour rule on ghost rows and columns, the
+ * corner columns taking the column rule), then swaps buffers. */
+typedef struct wx_pf wx_pf;
+/* nx, ny >= 1, nz >= 2; dtype WX_F64 (the paper's real(8)) or WX_F32.
+ * The state starts at 0 K.  Parameters default to d = 0.1, radiation 0.1,
+ * transfer 0.01, wells 330 K / 200 K.  WX_EINVAL, WX_EUNSUPPORTED,
+ * WX_ENOMEM. */
+int wx_pf_create(int nx, int ny, int nz, int dtype, wx_pf **out);
+/* d = diffusion_velocity in [0, 1/6], transfer in [0, 1] (WX_ECFL
+ * otherwise: the update stops being a convex combination). */
+int wx_pf_set_params(wx_pf *p, double d, double radiation, double transfer,
+                     double T_surf, double T_pbl);
+/* Copy the whole state in: FP64 [nz][ny+2][nx+2], host (src_is_device = 0)
+ * or device memory; synchronous. */
+int wx_pf_load(wx_pf *p, const double *E, int src_is_device);
+/* Copy the state out to a host FP64 [nz][ny+2][nx+2] array (synchronises). */
+int wx_pf_read(wx_pf *p, double *E);
+/* n_steps >= 0 steps on the stream, one kernel launch each. */
+int wx_pf_step(wx_pf *p, int n_steps, void *cuda_stream);
+/* Wait for the last stream; WX_ENONFINITE if a step produced a non-finite
+ * value since the last call. */
+int wx_pf_sync(wx_pf *p);
+long wx_pf_last_launches(const wx_pf *p);
+void wx_pf_destroy(wx_pf *p);               /* NULL-safe */
+const char *wx_pf_last_error(const wx_pf *p);
+
 /* Autotune the step kernel's launch configuration for this context (grid,
  * dtype, options): candidate tile rows x planes per TMA box x ring slots x
  * CTAs per SM are each timed with CUDA events over a few steps on the

@@ -1,0 +1,297 @@
+// wx_pf.cu -- the paper's reduced weather application on the GPU.
+//
+// State: E[k][j][i] over i in [0, nx+2), j in [0, ny+2), k in [0, nz): the
+// listings' arrays with their ghost ring, which is state of its own (it
+// evolves by a two-neighbour rule, not by copying).  One step is the time
+// loop of the appendix listings: the physics (uniform radiation on every
+// level, Newtonian heat wells at the bottom and top levels) in place on
+// every column, then diffusion into the other buffer, then the swap.
+//
+// The physics is pointwise and affine per level,
+//   P_k(x) = a_k x + b_k,   a_k = 1, b_k = r for 0 < k < nz-1,
+//   a_k = 1 - tau, b_k = (1 - tau) r + tau T_well at k = 0 (T_surf) and
+//   k = nz-1 (T_pbl),
+// so one kernel applies it to every value it reads: a sum of n neighbours
+// at one level is P applied to their raw sum, a_k S + n b_k.  Each thread
+// owns kPfChunk levels of one (i, j) column and walks them bottom to top,
+// keeping the physics result of levels k-1, k, k+1 of its own column in
+// registers; the four horizontal neighbours come from L1/L2 (a warp reads
+// 32 consecutive i).  Splitting columns into chunks (grid z) keeps enough
+// independent loads in flight: a whole column per thread leaves too few
+// threads, each waiting on one level at a time.
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <string>
+
+#include "../../include/wx.h"
+
+struct wx_pf {
+    int nx = 0, ny = 0, nz = 0, dtype = 0;
+    int W = 0, H = 0, P = 0;      // row width nx+2, rows ny+2, row pitch (cells)
+    size_t cells = 0, bytes = 0;  // per buffer (pitched)
+    int tb = 0;                   // bytes per value
+    void *buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    double *staging = nullptr;    // FP64 [nz][H][W] for load / read
+    unsigned *status = nullptr;
+    double d = 0.1, r = 0.1, tau = 0.01, Ts = 330.0, Tp = 200.0;
+    bool loaded = false;
+    cudaStream_t last = nullptr;
+    long launches = 0;
+    std::string err;
+};
+
+namespace wxpf {
+
+constexpr int kPfChunk = 8;  // levels per thread
+
+template <typename T> struct PfArgs {
+    const T *E;
+    T *En;
+    int nx, ny, nz, W, H, P;
+    T d, c6, c5, c2;                 // d, 1-6d, 1-5d, 1-2d
+    T a_mid, b_mid, a_bot, b_bot, a_top, b_top;
+    unsigned *status;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) pf_step_kernel(const PfArgs<T> g) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k0 = blockIdx.z * kPfChunk, k1 = min(k0 + kPfChunk, g.nz);
+    if (i >= g.W || j >= g.H) return;
+    const size_t plane = (size_t)g.H * g.P;
+    const T *col = g.E + (size_t)j * g.P + i;
+    T *out = g.En + (size_t)j * g.P + i;
+    const bool ghost_col = (i == 0 || i == g.nx + 1);
+    const bool ghost_row = !ghost_col && (j == 0 || j == g.ny + 1);
+    auto aff_a = [&](int k) { return k == 0 ? g.a_bot : (k == g.nz - 1 ? g.a_top : g.a_mid); };
+    auto aff_b = [&](int k) { return k == 0 ? g.b_bot : (k == g.nz - 1 ? g.b_top : g.b_mid); };
+    bool finite = true;
+    if (ghost_col || ghost_row) {
+        // two neighbours on the same level: the row's (or column's) other end
+        // and the adjacent interior cell
+        const T *na, *nb;
+        if (ghost_col) {
+            na = g.E + (size_t)j * g.P + (i == 0 ? 1 : g.nx);
+            nb = g.E + (size_t)j * g.P + (i == 0 ? g.nx + 1 : 0);
+        } else {
+            na = g.E + (size_t)(j == 0 ? 1 : g.ny) * g.P + i;
+            nb = g.E + (size_t)(j == 0 ? g.ny + 1 : 0) * g.P + i;
+        }
+#pragma unroll 4
+        for (int k = k0; k < k1; ++k) {
+            const size_t o = (size_t)k * plane;
+            const T a = aff_a(k), b = aff_b(k);
+            const T pc = a * col[o] + b;
+            const T ps = a * (na[o] + nb[o]) + 2 * b;
+            const T v = g.c2 * pc + g.d * ps;
+            finite = finite && isfinite(v);
+            out[o] = v;
+        }
+    } else {
+        // interior column: 7-point rule, one-sided at the bottom and top
+        T pm = k0 > 0 ? aff_a(k0 - 1) * col[(size_t)(k0 - 1) * plane] + aff_b(k0 - 1) : T(0);
+        T pc = aff_a(k0) * col[(size_t)k0 * plane] + aff_b(k0);
+#pragma unroll 4
+        for (int k = k0; k < k1; ++k) {
+            const size_t o = (size_t)k * plane;
+            const T a = aff_a(k), b = aff_b(k);
+            const T pu = k + 1 < g.nz ? aff_a(k + 1) * col[o + plane] + aff_b(k + 1) : T(0);
+            const T hs = (col[o - 1] + col[o + 1]) + (col[o - g.P] + col[o + g.P]);
+            const T ph = a * hs + 4 * b;
+            T v;
+            if (k == 0)
+                v = g.c5 * pc + g.d * (ph + pu);
+            else if (k == g.nz - 1)
+                v = g.c5 * pc + g.d * (ph + pm);
+            else
+                v = g.c6 * pc + g.d * (ph + (pm + pu));
+            finite = finite && isfinite(v);
+            out[o] = v;
+            pm = pc;
+            pc = pu;
+        }
+    }
+    if (!finite) atomicOr(g.status, 1u);
+}
+
+template <typename T> __global__ void pf_pack_kernel(const double *__restrict__ src, T *__restrict__ dst, int W,
+                                                     int H, int nz, int P) {
+    const size_t n = (size_t)W * H * nz;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = e / W;
+        dst[row * P + e % W] = (T)src[e];
+    }
+}
+
+template <typename T> __global__ void pf_unpack_kernel(const T *__restrict__ src, double *__restrict__ dst, int W,
+                                                       int H, int nz, int P) {
+    const size_t n = (size_t)W * H * nz;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = e / W;
+        dst[e] = (double)src[row * P + e % W];
+    }
+}
+
+template <typename T> static PfArgs<T> args(const wx_pf *p) {
+    PfArgs<T> g;
+    g.E = (const T *)p->buf[p->cur];
+    g.En = (T *)p->buf[1 - p->cur];
+    g.nx = p->nx;
+    g.ny = p->ny;
+    g.nz = p->nz;
+    g.W = p->W;
+    g.H = p->H;
+    g.P = p->P;
+    g.d = (T)p->d;
+    g.c6 = (T)(1.0 - 6 * p->d);
+    g.c5 = (T)(1.0 - 5 * p->d);
+    g.c2 = (T)(1.0 - 2 * p->d);
+    g.a_mid = (T)1.0;
+    g.b_mid = (T)p->r;
+    g.a_bot = (T)(1.0 - p->tau);
+    g.b_bot = (T)((1.0 - p->tau) * p->r + p->tau * p->Ts);
+    g.a_top = (T)(1.0 - p->tau);
+    g.b_top = (T)((1.0 - p->tau) * p->r + p->tau * p->Tp);
+    g.status = p->status;
+    return g;
+}
+
+static int grid1(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 65535 * 8); }
+
+}  // namespace wxpf
+
+using namespace wxpf;
+
+static int pfail(wx_pf *p, int code, const std::string &m) {
+    if (p) p->err = m;
+    return code;
+}
+
+#define PCK(call, what)                                                                                \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) return pfail(p, WX_ECUDA, std::string(what) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+extern "C" void wx_pf_destroy(wx_pf *p) {
+    if (!p) return;
+    for (void *q : {p->buf[0], p->buf[1], (void *)p->staging, (void *)p->status})
+        if (q) cudaFree(q);
+    delete p;
+}
+
+extern "C" int wx_pf_create(int nx, int ny, int nz, int dtype, wx_pf **out) {
+    if (!out) return WX_EINVAL;
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 2 || (dtype != WX_F32 && dtype != WX_F64)) return WX_EINVAL;
+    if ((size_t)(nx + 2) * (ny + 2) * nz > (size_t)1 << 34) return WX_EUNSUPPORTED;
+    wx_pf *p = new (std::nothrow) wx_pf();
+    if (!p) return WX_ENOMEM;
+    p->nx = nx;
+    p->ny = ny;
+    p->nz = nz;
+    p->dtype = dtype;
+    p->tb = dtype == WX_F64 ? 8 : 4;
+    p->W = nx + 2;
+    p->H = ny + 2;
+    p->P = (p->W + 31) / 32 * 32;
+    p->cells = (size_t)p->P * p->H * nz;
+    p->bytes = p->cells * p->tb;
+    bool ok = cudaMalloc(&p->buf[0], p->bytes) == cudaSuccess && cudaMalloc(&p->buf[1], p->bytes) == cudaSuccess &&
+              cudaMalloc((void **)&p->staging, (size_t)p->W * p->H * nz * sizeof(double)) == cudaSuccess &&
+              cudaMalloc((void **)&p->status, sizeof(unsigned)) == cudaSuccess &&
+              cudaMemset(p->status, 0, sizeof(unsigned)) == cudaSuccess &&
+              cudaMemset(p->buf[0], 0, p->bytes) == cudaSuccess && cudaMemset(p->buf[1], 0, p->bytes) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        wx_pf_destroy(p);
+        return WX_ENOMEM;
+    }
+    *out = p;
+    return WX_OK;
+}
+
+extern "C" int wx_pf_set_params(wx_pf *p, double d, double radiation, double transfer, double T_surf,
+                                double T_pbl) {
+    if (!p) return WX_EINVAL;
+    if (!std::isfinite(d) || !std::isfinite(radiation) || !std::isfinite(transfer) || !std::isfinite(T_surf) ||
+        !std::isfinite(T_pbl))
+        return pfail(p, WX_EINVAL, "wx_pf_set_params: non-finite parameter");
+    // the explicit update is a convex combination only for these ranges
+    if (d < 0 || d > 1.0 / 6.0 || transfer < 0 || transfer > 1)
+        return pfail(p, WX_ECFL, "wx_pf_set_params: need 0 <= d <= 1/6 and 0 <= transfer <= 1");
+    p->d = d;
+    p->r = radiation;
+    p->tau = transfer;
+    p->Ts = T_surf;
+    p->Tp = T_pbl;
+    return WX_OK;
+}
+
+extern "C" int wx_pf_load(wx_pf *p, const double *E, int src_is_device) {
+    if (!p || !E) return pfail(p, WX_EINVAL, "wx_pf_load: NULL");
+    const size_t n = (size_t)p->W * p->H * p->nz;
+    PCK(cudaMemcpy(p->staging, E, n * sizeof(double), src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice),
+        "wx_pf_load copy");
+    if (p->dtype == WX_F64)
+        pf_pack_kernel<double><<<grid1(n), 256>>>(p->staging, (double *)p->buf[0], p->W, p->H, p->nz, p->P);
+    else
+        pf_pack_kernel<float><<<grid1(n), 256>>>(p->staging, (float *)p->buf[0], p->W, p->H, p->nz, p->P);
+    PCK(cudaGetLastError(), "wx_pf_load pack");
+    PCK(cudaDeviceSynchronize(), "wx_pf_load");
+    p->cur = 0;
+    p->loaded = true;
+    return WX_OK;
+}
+
+extern "C" int wx_pf_read(wx_pf *p, double *E) {
+    if (!p || !E) return pfail(p, WX_EINVAL, "wx_pf_read: NULL");
+    if (!p->loaded) return pfail(p, WX_ESTATE, "wx_pf_read: nothing loaded");
+    PCK(cudaDeviceSynchronize(), "wx_pf_read");
+    const size_t n = (size_t)p->W * p->H * p->nz;
+    if (p->dtype == WX_F64)
+        pf_unpack_kernel<double><<<grid1(n), 256>>>((const double *)p->buf[p->cur], p->staging, p->W, p->H, p->nz, p->P);
+    else
+        pf_unpack_kernel<float><<<grid1(n), 256>>>((const float *)p->buf[p->cur], p->staging, p->W, p->H, p->nz, p->P);
+    PCK(cudaGetLastError(), "wx_pf_read unpack");
+    PCK(cudaMemcpy(E, p->staging, n * sizeof(double), cudaMemcpyDeviceToHost), "wx_pf_read copy");
+    return WX_OK;
+}
+
+extern "C" int wx_pf_step(wx_pf *p, int n_steps, void *stream) {
+    if (!p) return WX_EINVAL;
+    if (n_steps < 0) return pfail(p, WX_EINVAL, "wx_pf_step: n_steps < 0");
+    if (!p->loaded) return pfail(p, WX_ESTATE, "wx_pf_step: load a state first");
+    cudaStream_t s = (cudaStream_t)stream;
+    const dim3 block(32, 8), grid((p->W + 31) / 32, (p->H + 7) / 8, (p->nz + kPfChunk - 1) / kPfChunk);
+    for (int n = 0; n < n_steps; ++n) {
+        if (p->dtype == WX_F64)
+            pf_step_kernel<double><<<grid, block, 0, s>>>(args<double>(p));
+        else
+            pf_step_kernel<float><<<grid, block, 0, s>>>(args<float>(p));
+        PCK(cudaGetLastError(), "wx_pf_step");
+        p->cur = 1 - p->cur;
+    }
+    p->last = s;
+    p->launches = n_steps;
+    return WX_OK;
+}
+
+extern "C" int wx_pf_sync(wx_pf *p) {
+    if (!p) return WX_EINVAL;
+    PCK(cudaStreamSynchronize(p->last), "wx_pf_sync");
+    unsigned st = 0;
+    PCK(cudaMemcpy(&st, p->status, sizeof st, cudaMemcpyDeviceToHost), "wx_pf_sync status");
+    if (st) {
+        cudaMemset(p->status, 0, sizeof st);
+        return pfail(p, WX_ENONFINITE, "a step produced a non-finite value");
+    }
+    return WX_OK;
+}
+
+extern "C" long wx_pf_last_launches(const wx_pf *p) { return p ? p->launches : 0; }
+
+extern "C" const char *wx_pf_last_error(const wx_pf *p) { return p ? p->err.c_str() : "NULL handle"; }

@@ -94,6 +94,16 @@ SIGNATURES = [
     ("wx_mlp_train_step", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_float, _VP, _VP]),
     ("wx_mlp_status", ctypes.c_int, [_VP]),
     ("wx_set_surrogate", ctypes.c_int, [_VP, _VP, ctypes.c_double]),
+    ("wx_pf_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(_VP)]),
+    ("wx_pf_set_params", ctypes.c_int, [_VP] + [ctypes.c_double] * 5),
+    ("wx_pf_load", ctypes.c_int, [_VP, _VP, ctypes.c_int]),
+    ("wx_pf_read", ctypes.c_int, [_VP, _VP]),
+    ("wx_pf_step", ctypes.c_int, [_VP, ctypes.c_int, _VP]),
+    ("wx_pf_sync", ctypes.c_int, [_VP]),
+    ("wx_pf_last_launches", ctypes.c_long, [_VP]),
+    ("wx_pf_destroy", None, [_VP]),
+    ("wx_pf_last_error", ctypes.c_char_p, [_VP]),
     ("wx_surrogate_fallbacks", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_long)]),
     ("wx_destroy", None, [_VP]),
     ("wx_last_error", ctypes.c_char_p, [_VP]),
@@ -435,3 +445,51 @@ class MLP:
 
     def status(self):
         _mcheck(lib().wx_mlp_status(self.ptr))
+
+
+# ------------------------------------------------ reduced application
+class ReducedApp:
+    """One wx_pf*: the paper's reduced weather application (include/wx.h)."""
+
+    def __init__(self, nx, ny, nz, dtype="f64"):
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        p = _VP()
+        code = lib().wx_pf_create(self.nx, self.ny, self.nz, DTYPES[dtype], ctypes.byref(p))
+        if code != 0:
+            raise WxError(code, "wx_pf_create")
+        self.ptr = p
+
+    def _check(self, code):
+        if code != 0:
+            raise WxError(code, lib().wx_pf_last_error(self.ptr).decode())
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            lib().wx_pf_destroy(self.ptr)
+            self.ptr = None
+
+    __del__ = close
+
+    def set_params(self, d=0.1, radiation=0.1, transfer=0.01, T_surf=330.0, T_pbl=200.0):
+        self._check(lib().wx_pf_set_params(self.ptr, d, radiation, transfer, T_surf, T_pbl))
+
+    def load(self, E):
+        dev = hasattr(E, "data_ptr")
+        if not dev:
+            E = np.ascontiguousarray(E, np.float64)
+        self._keep = E
+        self._check(lib().wx_pf_load(self.ptr, _dptr(E), int(dev)))
+
+    def read(self):
+        E = np.empty((self.nz, self.ny + 2, self.nx + 2))
+        self._check(lib().wx_pf_read(self.ptr, _dptr(E)))
+        return E
+
+    def step(self, n_steps=1, stream=None):
+        self._check(lib().wx_pf_step(self.ptr, int(n_steps), _stream_ptr(stream)))
+
+    def sync(self):
+        self._check(lib().wx_pf_sync(self.ptr))
+
+    def last_launches(self):
+        return int(lib().wx_pf_last_launches(self.ptr))
