@@ -188,6 +188,15 @@ int wx_sums_noalloc(const void *T, const void *q, int dtype, int nx, int ny,
 /* Message of the last failing wx_sums_noalloc call on this host thread. */
 const char *wx_sums_noalloc_error(void);
 
+/* Failure-detection self test: one kernel waits on a barrier that nothing
+ * will complete, with the same bounded wait every kernel of the library
+ * uses, limited to limit_ns (1 .. 2e9).  Returns WX_ETIMEOUT when the wait
+ * gave up and reported it (the expected outcome), WX_OK if it completed;
+ * waited_ns receives the device time spent waiting.  The CUDA context
+ * stays usable either way.  WX_EINVAL for a zero or larger limit. */
+int wx_selftest_wait_timeout(unsigned long long limit_ns,
+                             unsigned long long *waited_ns);
+
 /* ------------------------------------------- the paper's reduced application
  * The reduced weather application of Sec. 3.1 (Eq. 1, explicit Euler) with
  * the semantics of its appendix listings, for comparison with the paper's

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 
+#include "ptx.cuh"
 #include "wx_internal.cuh"
 
 using namespace wx;
@@ -478,4 +479,47 @@ extern "C" int wx_physics_columns(wx_ctx *c, const void *Ts, const void *qs, con
     int rc = launch_columns(c, Ts, qs, km, Tout, tend, ncol, (cudaStream_t)stream);
     c->last_stream = (cudaStream_t)stream;
     return rc;
+}
+
+
+// ------------------------------------------------------------ self test
+// A wait on an mbarrier that no thread will ever arrive on: the bounded
+// wait every kernel of the library uses must give up after limit_ns, report
+// it through the status word, and leave the context usable.
+namespace wx {
+__global__ void selftest_wait_kernel(uint64_t limit_ns, unsigned *status, unsigned long long *waited_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint64_t t0 = globaltimer_ns();
+        const bool ok = mbar_wait_bounded(&bar, 0, limit_ns);
+        *waited_ns = globaltimer_ns() - t0;
+        if (!ok) atomicOr(status, ST_TIMEOUT);
+    }
+}
+}  // namespace wx
+
+extern "C" int wx_selftest_wait_timeout(unsigned long long limit_ns, unsigned long long *waited_ns) {
+    if (!waited_ns || limit_ns == 0 || limit_ns > WX_SPIN_NS) return WX_EINVAL;
+    unsigned *st = nullptr;
+    unsigned long long *w = nullptr;
+    if (cudaMalloc(&st, sizeof *st) != cudaSuccess || cudaMalloc(&w, sizeof *w) != cudaSuccess) {
+        cudaFree(st);
+        cudaGetLastError();
+        return WX_ENOMEM;
+    }
+    cudaMemset(st, 0, sizeof *st);
+    wx::selftest_wait_kernel<<<1, 32>>>(limit_ns, st, w);
+    unsigned s = 0;
+    const bool ok = cudaGetLastError() == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess &&
+                    cudaMemcpy(&s, st, sizeof s, cudaMemcpyDeviceToHost) == cudaSuccess &&
+                    cudaMemcpy(waited_ns, w, sizeof *w, cudaMemcpyDeviceToHost) == cudaSuccess;
+    cudaFree(st);
+    cudaFree(w);
+    if (!ok) return WX_ECUDA;
+    return (s & ST_TIMEOUT) ? WX_ETIMEOUT : WX_OK;
 }

@@ -94,6 +94,7 @@ SIGNATURES = [
     ("wx_mlp_train_step", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_float, _VP, _VP]),
     ("wx_mlp_status", ctypes.c_int, [_VP]),
     ("wx_set_surrogate", ctypes.c_int, [_VP, _VP, ctypes.c_double]),
+    ("wx_selftest_wait_timeout", ctypes.c_int, [ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_ulonglong)]),
     ("wx_pf_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.POINTER(_VP)]),
     ("wx_pf_set_params", ctypes.c_int, [_VP] + [ctypes.c_double] * 5),
@@ -493,3 +494,10 @@ class ReducedApp:
 
     def last_launches(self):
         return int(lib().wx_pf_last_launches(self.ptr))
+
+
+def wx_selftest_wait_timeout(limit_ns):
+    """(status code, device ns waited) of the bounded-wait self test."""
+    w = ctypes.c_ulonglong()
+    code = lib().wx_selftest_wait_timeout(int(limit_ns), ctypes.byref(w))
+    return code, w.value

@@ -271,3 +271,23 @@ def test_cfl_violation_is_refused():
         wx.Context(8, 8, 4, "f32").step(1)
     assert ei.value.code == -7
     ctx.close()
+
+
+def test_bounded_wait_gives_up_and_context_survives():
+    """A wait that nothing will end returns WX_ETIMEOUT after its limit (the
+    failure-detection path every kernel's waits share), and the context can
+    still step afterwards."""
+    code, waited = wx.wx_selftest_wait_timeout(20_000_000)  # 20 ms
+    assert code == -6
+    assert 20_000_000 <= waited < 2_000_000_000
+    case = inputs.round_to_f32(inputs.small_case(40, 30, 8))
+    ctx = wx.Context(40, 30, 8, "f32")
+    ctx.set_params(case)
+    ctx.load_fields(case.T, case.q, case.U, case.V)
+    ctx.step(2)
+    ctx.sync()
+    T, _ = ctx.read_fields()
+    To, _ = oracle.run(case, 2, case.T, case.q, case.U, case.V)
+    assert np.max(np.abs(T - To)) / np.max(np.abs(To)) <= 1e-5
+    ctx.close()
+    assert wx.wx_selftest_wait_timeout(0)[0] == -1
