@@ -19,7 +19,7 @@ CUDA graph, the residual-checked MLP-surrogate step (network trained in this
 run by the library's kernels) against the plain step, and the paper's own
 reduced weather application on its three grids beside the paper's timings.
 
-  python bench.py --only f64|mixed|ensemble|surrogate|reduced_app [--nx --ny]   one variant
+  python bench.py --only f64|mixed|ensemble|surrogate|reduced_app|ablation [--nx --ny]   one variant
 """
 from __future__ import annotations
 
@@ -399,6 +399,50 @@ def variant_reduced_app(steps=100):
     return out
 
 
+# The paper's storage-order (128^3, Sec. 5.1.1) and block-size (Sec. 5.1.4)
+# tables, 100 steps, FP64.
+PAPER_ORDER_S = {"ijk": {"k20x_openacc_s": 0.10, "x5670_1core_s": 1.73},
+                 "kij": {"k20x_openacc_s": 0.77, "x5670_1core_s": 1.28}}
+PAPER_BLOCK_S = {"128x1": {"128": 0.095, "256": 0.63, "256x512": 2.99},
+                 "32x16": {"128": 0.10, "256": 0.55, "256x512": 2.16}}
+
+
+def variant_ablation(steps=100):
+    """The paper's storage-order and block-size experiments on GB300: the
+    reduced application (box state, 100 steps, device-resident) in IJK and
+    KIJ order at 128^3 and 256^3, and four block shapes in IJK order on the
+    three grids; FP64 as in the paper (FP64-ALU-bound here) and FP32
+    (memory-bound)."""
+    import torch
+    from paper_1802_05839_gb300 import inputs, wx
+    st = torch.cuda.Stream()
+
+    def run(nx, ny, nz, layout, block, dtype):
+        app = wx.ReducedApp(nx, ny, nz, dtype)
+        app.set_params()
+        app.set_launch(layout, block)
+        app.load(inputs.paper_box_state(nx, ny, nz))
+        ms = _time_steps(lambda: app.step(steps, stream=st), 1, st)
+        app.sync()
+        app.close()
+        return ms * 1e-3
+
+    out = {"paper": {"storage_order_128": PAPER_ORDER_S, "block_k20x": PAPER_BLOCK_S}}
+    for dtype in ("f64", "f32"):
+        order = {}
+        for n in (128, 256):
+            r = {lay: run(n, n, n, lay, (32, 8), dtype) for lay in ("ijk", "kij")}
+            r["kij_over_ijk"] = r["kij"] / r["ijk"]
+            order[str(n)] = r
+        blocks = {}
+        for b in ((128, 1), (32, 16), (32, 8), (64, 4)):
+            blocks[f"{b[0]}x{b[1]}"] = {g: run(*dims, "ijk", b, dtype) for g, dims in
+                                        (("128", (128, 128, 128)), ("256", (256, 256, 256)),
+                                         ("256x512", (256, 256, 512)))}
+        out[dtype] = {"storage_order_s_per_100_steps": order, "block_shape_s_per_100_steps": blocks}
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -492,6 +536,7 @@ def run_ours(args):
             "ensemble": variant_ensemble(200),
             "surrogate": variant_surrogate(100, plain_ms=ms, train_epochs=args.epochs),
             "reduced_app": variant_reduced_app(100),
+            "ablation": variant_ablation(100),
         }
     print(json.dumps(out))
 
@@ -510,7 +555,7 @@ def main():
     ap.add_argument("--nz", type=int, default=58, help="grid override (profiling captures only)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--epochs", type=int, default=32, help="surrogate training epochs")
-    ap.add_argument("--only", choices=["f64", "mixed", "ensemble", "surrogate", "reduced_app"],
+    ap.add_argument("--only", choices=["f64", "mixed", "ensemble", "surrogate", "reduced_app", "ablation"],
                     help="run one variant alone and print its record (profiling captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -526,6 +571,8 @@ def main():
             rec = variant_ensemble(args.steps)
         elif args.only == "reduced_app":
             rec = variant_reduced_app(args.steps)
+        elif args.only == "ablation":
+            rec = variant_ablation(args.steps)
         else:
             rec = variant_surrogate(args.steps, args.nx, args.ny, train_epochs=args.epochs)
         print(json.dumps({"variant": args.only, **rec}))

@@ -217,6 +217,13 @@ int wx_pf_create(int nx, int ny, int nz, int dtype, wx_pf **out);
  * otherwise: the update stops being a convex combination). */
 int wx_pf_set_params(wx_pf *p, double d, double radiation, double transfer,
                      double T_surf, double T_pbl);
+/* Storage order on the device (WX_PF_IJK: i fastest, the default; WX_PF_KIJ:
+ * k fastest, the paper's CPU order) and thread-block shape (block_x *
+ * block_y threads, 32..512, a multiple of 32; default 32 x 8), for the
+ * paper's storage-order and block-size experiments (Sec. 5.1.1, 5.1.4).
+ * A loaded state is converted.  WX_EINVAL otherwise. */
+enum { WX_PF_IJK = 0, WX_PF_KIJ = 1 };
+int wx_pf_set_launch(wx_pf *p, int layout, int block_x, int block_y);
 /* Copy the whole state in: FP64 [nz][ny+2][nx+2], host (src_is_device = 0)
  * or device memory; synchronous. */
 int wx_pf_load(wx_pf *p, const double *E, int src_is_device);

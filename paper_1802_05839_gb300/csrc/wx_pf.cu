@@ -19,6 +19,13 @@
 // 32 consecutive i).  Splitting columns into chunks (grid z) keeps enough
 // independent loads in flight: a whole column per thread leaves too few
 // threads, each waiting on one level at a time.
+//
+// Two storage orders are kept for the paper's storage-order experiment
+// (Sec. 2.4.3, Sec. 5.1.1): IJK (i fastest, the default: a warp's loads of
+// one level are contiguous) and KIJ (k fastest, the CPU order: a warp's
+// loads are nz cells apart).  The kernel is written once in terms of the
+// strides (si, sj, sk) of the chosen order; the block shape is a launch
+// parameter (the paper's block-size experiment, Sec. 5.1.4).
 #include <algorithm>
 #include <cmath>
 #include <new>
@@ -28,7 +35,9 @@
 
 struct wx_pf {
     int nx = 0, ny = 0, nz = 0, dtype = 0;
-    int W = 0, H = 0, P = 0;      // row width nx+2, rows ny+2, row pitch (cells)
+    int W = 0, H = 0, P = 0;      // row width nx+2, rows ny+2, row pitch (cells, IJK)
+    int layout = 0;               // WX_PF_IJK or WX_PF_KIJ
+    int bx = 32, by = 8;          // thread-block shape
     size_t cells = 0, bytes = 0;  // per buffer (pitched)
     int tb = 0;                   // bytes per value
     void *buf[2] = {nullptr, nullptr};
@@ -49,21 +58,22 @@ constexpr int kPfChunk = 8;  // levels per thread
 template <typename T> struct PfArgs {
     const T *E;
     T *En;
-    int nx, ny, nz, W, H, P;
+    int nx, ny, nz, W, H;
+    long si, sj, sk;                 // strides of i, j, k in the storage order
     T d, c6, c5, c2;                 // d, 1-6d, 1-5d, 1-2d
     T a_mid, b_mid, a_bot, b_bot, a_top, b_top;
     unsigned *status;
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256) pf_step_kernel(const PfArgs<T> g) {
+__global__ void __launch_bounds__(512) pf_step_kernel(const PfArgs<T> g) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k0 = blockIdx.z * kPfChunk, k1 = min(k0 + kPfChunk, g.nz);
     if (i >= g.W || j >= g.H) return;
-    const size_t plane = (size_t)g.H * g.P;
-    const T *col = g.E + (size_t)j * g.P + i;
-    T *out = g.En + (size_t)j * g.P + i;
+    const long plane = g.sk;
+    const T *col = g.E + j * g.sj + i * g.si;
+    T *out = g.En + j * g.sj + i * g.si;
     const bool ghost_col = (i == 0 || i == g.nx + 1);
     const bool ghost_row = !ghost_col && (j == 0 || j == g.ny + 1);
     auto aff_a = [&](int k) { return k == 0 ? g.a_bot : (k == g.nz - 1 ? g.a_top : g.a_mid); };
@@ -74,15 +84,15 @@ __global__ void __launch_bounds__(256) pf_step_kernel(const PfArgs<T> g) {
         // and the adjacent interior cell
         const T *na, *nb;
         if (ghost_col) {
-            na = g.E + (size_t)j * g.P + (i == 0 ? 1 : g.nx);
-            nb = g.E + (size_t)j * g.P + (i == 0 ? g.nx + 1 : 0);
+            na = g.E + j * g.sj + (i == 0 ? 1 : g.nx) * g.si;
+            nb = g.E + j * g.sj + (i == 0 ? g.nx + 1 : 0) * g.si;
         } else {
-            na = g.E + (size_t)(j == 0 ? 1 : g.ny) * g.P + i;
-            nb = g.E + (size_t)(j == 0 ? g.ny + 1 : 0) * g.P + i;
+            na = g.E + (j == 0 ? 1 : g.ny) * g.sj + i * g.si;
+            nb = g.E + (j == 0 ? g.ny + 1 : 0) * g.sj + i * g.si;
         }
 #pragma unroll 4
         for (int k = k0; k < k1; ++k) {
-            const size_t o = (size_t)k * plane;
+            const long o = k * plane;
             const T a = aff_a(k), b = aff_b(k);
             const T pc = a * col[o] + b;
             const T ps = a * (na[o] + nb[o]) + 2 * b;
@@ -92,14 +102,14 @@ __global__ void __launch_bounds__(256) pf_step_kernel(const PfArgs<T> g) {
         }
     } else {
         // interior column: 7-point rule, one-sided at the bottom and top
-        T pm = k0 > 0 ? aff_a(k0 - 1) * col[(size_t)(k0 - 1) * plane] + aff_b(k0 - 1) : T(0);
-        T pc = aff_a(k0) * col[(size_t)k0 * plane] + aff_b(k0);
+        T pm = k0 > 0 ? aff_a(k0 - 1) * col[(k0 - 1) * plane] + aff_b(k0 - 1) : T(0);
+        T pc = aff_a(k0) * col[k0 * plane] + aff_b(k0);
 #pragma unroll 4
         for (int k = k0; k < k1; ++k) {
-            const size_t o = (size_t)k * plane;
+            const long o = k * plane;
             const T a = aff_a(k), b = aff_b(k);
             const T pu = k + 1 < g.nz ? aff_a(k + 1) * col[o + plane] + aff_b(k + 1) : T(0);
-            const T hs = (col[o - 1] + col[o + 1]) + (col[o - g.P] + col[o + g.P]);
+            const T hs = (col[o - g.si] + col[o + g.si]) + (col[o - g.sj] + col[o + g.sj]);
             const T ph = a * hs + 4 * b;
             T v;
             if (k == 0)
@@ -117,21 +127,36 @@ __global__ void __launch_bounds__(256) pf_step_kernel(const PfArgs<T> g) {
     if (!finite) atomicOr(g.status, 1u);
 }
 
+// element e of the [nz][H][W] exchange order -> its offset in the storage order
+__device__ __forceinline__ long pf_offset(size_t e, int W, int H, long si, long sj, long sk) {
+    const long i = (long)(e % W), j = (long)((e / W) % H), k = (long)(e / ((size_t)W * H));
+    return i * si + j * sj + k * sk;
+}
+
 template <typename T> __global__ void pf_pack_kernel(const double *__restrict__ src, T *__restrict__ dst, int W,
-                                                     int H, int nz, int P) {
+                                                     int H, int nz, long si, long sj, long sk) {
     const size_t n = (size_t)W * H * nz;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        const size_t row = e / W;
-        dst[row * P + e % W] = (T)src[e];
-    }
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        dst[pf_offset(e, W, H, si, sj, sk)] = (T)src[e];
 }
 
 template <typename T> __global__ void pf_unpack_kernel(const T *__restrict__ src, double *__restrict__ dst, int W,
-                                                       int H, int nz, int P) {
+                                                       int H, int nz, long si, long sj, long sk) {
     const size_t n = (size_t)W * H * nz;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        const size_t row = e / W;
-        dst[e] = (double)src[row * P + e % W];
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        dst[e] = (double)src[pf_offset(e, W, H, si, sj, sk)];
+}
+
+// strides of the storage order: IJK [k][j][P], KIJ [j][i][nz]
+static void strides(const wx_pf *p, long *si, long *sj, long *sk) {
+    if (p->layout == WX_PF_KIJ) {
+        *sk = 1;
+        *si = p->nz;
+        *sj = (long)p->W * p->nz;
+    } else {
+        *si = 1;
+        *sj = p->P;
+        *sk = (long)p->H * p->P;
     }
 }
 
@@ -144,7 +169,7 @@ template <typename T> static PfArgs<T> args(const wx_pf *p) {
     g.nz = p->nz;
     g.W = p->W;
     g.H = p->H;
-    g.P = p->P;
+    strides(p, &g.si, &g.sj, &g.sk);
     g.d = (T)p->d;
     g.c6 = (T)(1.0 - 6 * p->d);
     g.c5 = (T)(1.0 - 5 * p->d);
@@ -198,7 +223,7 @@ extern "C" int wx_pf_create(int nx, int ny, int nz, int dtype, wx_pf **out) {
     p->W = nx + 2;
     p->H = ny + 2;
     p->P = (p->W + 31) / 32 * 32;
-    p->cells = (size_t)p->P * p->H * nz;
+    p->cells = std::max((size_t)p->P * p->H * nz, (size_t)p->W * p->H * nz);
     p->bytes = p->cells * p->tb;
     bool ok = cudaMalloc(&p->buf[0], p->bytes) == cudaSuccess && cudaMalloc(&p->buf[1], p->bytes) == cudaSuccess &&
               cudaMalloc((void **)&p->staging, (size_t)p->W * p->H * nz * sizeof(double)) == cudaSuccess &&
@@ -236,10 +261,12 @@ extern "C" int wx_pf_load(wx_pf *p, const double *E, int src_is_device) {
     const size_t n = (size_t)p->W * p->H * p->nz;
     PCK(cudaMemcpy(p->staging, E, n * sizeof(double), src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice),
         "wx_pf_load copy");
+    long si, sj, sk;
+    strides(p, &si, &sj, &sk);
     if (p->dtype == WX_F64)
-        pf_pack_kernel<double><<<grid1(n), 256>>>(p->staging, (double *)p->buf[0], p->W, p->H, p->nz, p->P);
+        pf_pack_kernel<double><<<grid1(n), 256>>>(p->staging, (double *)p->buf[0], p->W, p->H, p->nz, si, sj, sk);
     else
-        pf_pack_kernel<float><<<grid1(n), 256>>>(p->staging, (float *)p->buf[0], p->W, p->H, p->nz, p->P);
+        pf_pack_kernel<float><<<grid1(n), 256>>>(p->staging, (float *)p->buf[0], p->W, p->H, p->nz, si, sj, sk);
     PCK(cudaGetLastError(), "wx_pf_load pack");
     PCK(cudaDeviceSynchronize(), "wx_pf_load");
     p->cur = 0;
@@ -252,10 +279,14 @@ extern "C" int wx_pf_read(wx_pf *p, double *E) {
     if (!p->loaded) return pfail(p, WX_ESTATE, "wx_pf_read: nothing loaded");
     PCK(cudaDeviceSynchronize(), "wx_pf_read");
     const size_t n = (size_t)p->W * p->H * p->nz;
+    long si, sj, sk;
+    strides(p, &si, &sj, &sk);
     if (p->dtype == WX_F64)
-        pf_unpack_kernel<double><<<grid1(n), 256>>>((const double *)p->buf[p->cur], p->staging, p->W, p->H, p->nz, p->P);
+        pf_unpack_kernel<double><<<grid1(n), 256>>>((const double *)p->buf[p->cur], p->staging, p->W, p->H, p->nz, si,
+                                                    sj, sk);
     else
-        pf_unpack_kernel<float><<<grid1(n), 256>>>((const float *)p->buf[p->cur], p->staging, p->W, p->H, p->nz, p->P);
+        pf_unpack_kernel<float><<<grid1(n), 256>>>((const float *)p->buf[p->cur], p->staging, p->W, p->H, p->nz, si,
+                                                   sj, sk);
     PCK(cudaGetLastError(), "wx_pf_read unpack");
     PCK(cudaMemcpy(E, p->staging, n * sizeof(double), cudaMemcpyDeviceToHost), "wx_pf_read copy");
     return WX_OK;
@@ -266,7 +297,8 @@ extern "C" int wx_pf_step(wx_pf *p, int n_steps, void *stream) {
     if (n_steps < 0) return pfail(p, WX_EINVAL, "wx_pf_step: n_steps < 0");
     if (!p->loaded) return pfail(p, WX_ESTATE, "wx_pf_step: load a state first");
     cudaStream_t s = (cudaStream_t)stream;
-    const dim3 block(32, 8), grid((p->W + 31) / 32, (p->H + 7) / 8, (p->nz + kPfChunk - 1) / kPfChunk);
+    const dim3 block(p->bx, p->by),
+        grid((p->W + p->bx - 1) / p->bx, (p->H + p->by - 1) / p->by, (p->nz + kPfChunk - 1) / kPfChunk);
     for (int n = 0; n < n_steps; ++n) {
         if (p->dtype == WX_F64)
             pf_step_kernel<double><<<grid, block, 0, s>>>(args<double>(p));
@@ -289,6 +321,40 @@ extern "C" int wx_pf_sync(wx_pf *p) {
         cudaMemset(p->status, 0, sizeof st);
         return pfail(p, WX_ENONFINITE, "a step produced a non-finite value");
     }
+    return WX_OK;
+}
+
+// Storage order and block shape; a loaded state is carried over.
+extern "C" int wx_pf_set_launch(wx_pf *p, int layout, int block_x, int block_y) {
+    if (!p) return WX_EINVAL;
+    if ((layout != WX_PF_IJK && layout != WX_PF_KIJ) || block_x < 1 || block_y < 1 || block_x * block_y > 512 ||
+        block_x * block_y % 32)
+        return pfail(p, WX_EINVAL, "wx_pf_set_launch: layout IJK/KIJ, block of 32..512 threads (multiple of 32)");
+    if (p->loaded && layout != p->layout) {
+        PCK(cudaDeviceSynchronize(), "wx_pf_set_launch");
+        const size_t n = (size_t)p->W * p->H * p->nz;
+        long si, sj, sk;
+        strides(p, &si, &sj, &sk);
+        if (p->dtype == WX_F64)
+            pf_unpack_kernel<double><<<grid1(n), 256>>>((const double *)p->buf[p->cur], p->staging, p->W, p->H,
+                                                        p->nz, si, sj, sk);
+        else
+            pf_unpack_kernel<float><<<grid1(n), 256>>>((const float *)p->buf[p->cur], p->staging, p->W, p->H, p->nz,
+                                                       si, sj, sk);
+        p->layout = layout;
+        strides(p, &si, &sj, &sk);
+        if (p->dtype == WX_F64)
+            pf_pack_kernel<double><<<grid1(n), 256>>>(p->staging, (double *)p->buf[p->cur], p->W, p->H, p->nz, si,
+                                                      sj, sk);
+        else
+            pf_pack_kernel<float><<<grid1(n), 256>>>(p->staging, (float *)p->buf[p->cur], p->W, p->H, p->nz, si,
+                                                     sj, sk);
+        PCK(cudaGetLastError(), "wx_pf_set_launch re-layout");
+        PCK(cudaDeviceSynchronize(), "wx_pf_set_launch");
+    }
+    p->layout = layout;
+    p->bx = block_x;
+    p->by = block_y;
     return WX_OK;
 }
 

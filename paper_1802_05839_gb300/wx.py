@@ -98,6 +98,7 @@ SIGNATURES = [
     ("wx_pf_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.POINTER(_VP)]),
     ("wx_pf_set_params", ctypes.c_int, [_VP] + [ctypes.c_double] * 5),
+    ("wx_pf_set_launch", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     ("wx_pf_load", ctypes.c_int, [_VP, _VP, ctypes.c_int]),
     ("wx_pf_read", ctypes.c_int, [_VP, _VP]),
     ("wx_pf_step", ctypes.c_int, [_VP, ctypes.c_int, _VP]),
@@ -473,6 +474,9 @@ class ReducedApp:
 
     def set_params(self, d=0.1, radiation=0.1, transfer=0.01, T_surf=330.0, T_pbl=200.0):
         self._check(lib().wx_pf_set_params(self.ptr, d, radiation, transfer, T_surf, T_pbl))
+
+    def set_launch(self, layout="ijk", block=(32, 8)):
+        self._check(lib().wx_pf_set_launch(self.ptr, {"ijk": 0, "kij": 1}[layout], int(block[0]), int(block[1])))
 
     def load(self, E):
         dev = hasattr(E, "data_ptr")
