@@ -274,9 +274,11 @@ def variant_ensemble(steps):
     ens.sync()
     torch.cuda.synchronize()
     e0, e1 = _events(2)
+    torch.cuda.nvtx.range_push("timed")   # ncu --nvtx --nvtx-include timed/
     e0.record(st)
     ens.step(steps, graph=True, stream=st)
     e1.record(st)
+    torch.cuda.nvtx.range_pop()
     ens.sync()
     ms = e0.elapsed_time(e1) / steps
     peak, _ = peaks()

@@ -82,3 +82,38 @@ def test_mixed_sums_each_step():
     w = case.h ** 2 * case.dz[:, None, None]
     assert abs(e[-1] - np.sum(Tg * w)) / abs(e[-1]) < 1e-12
     assert abs(m[-1] - np.sum(qg * w)) / abs(m[-1]) < 1e-12
+
+
+def test_error_against_the_oracle_at_steps_1_100_500():
+    """The mixed-precision configuration's error per field against the FP64
+    oracle after 1, 100 and 500 steps (near-singular columns seeded), beside
+    the all-FP32 path.  Bounds: relative L2 1e-5 / 1e-4 / 5e-4."""
+    case = inputs.round_to_f32(inputs.paper_grid_case(192, 160, 58, seed=11, near_singular=True))
+    marks = (1, 100, 500)
+    got = {}
+    for dtype in ("mixed", "f32"):
+        ctx = wx.Context(case.nx, case.ny, case.nz, dtype)
+        ctx.set_params(case)
+        ctx.load_fields(case.T, case.q, case.U, case.V)
+        done, out = 0, []
+        for m in marks:
+            ctx.step(m - done)
+            done = m
+            ctx.sync()
+            out.append(ctx.read_fields())
+        ctx.close()
+        got[dtype] = out
+    T, q = case.T.copy(), case.q.copy()
+    done = 0
+    for idx, m in enumerate(marks):
+        T, q = oracle.run(case, m - done, T, q, case.U, case.V)
+        done = m
+        for dtype in ("mixed", "f32"):
+            Tg, qg = got[dtype][idx]
+            eT = np.linalg.norm(Tg - T) / np.linalg.norm(T)
+            eq = np.linalg.norm(qg - q) / np.linalg.norm(q)
+            print(f"step {m:3d} {dtype:5s}: rel L2 T {eT:.3e} q {eq:.3e}; "
+                  f"max rel T {maxrel(Tg, T):.3e} q {maxrel(qg, q):.3e}")
+            if dtype == "mixed":
+                bound = {1: 1e-5, 100: 1e-4, 500: 5e-4}[m]
+                assert eT <= bound and eq <= bound
