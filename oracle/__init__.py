@@ -81,6 +81,8 @@ def lib():
         L.wxo_column_weighted_sum.restype = ctypes.c_double
         L.wxo_threads.restype = ctypes.c_int
         L.wxo_set_threads.argtypes = [ctypes.c_int]
+        L.wxo_step_rk3.argtypes = [P, _D, _D, _D, _D, _D, _D]
+        L.wxo_run_rk3.argtypes = [P, ctypes.c_int, _D, _D, _D, _D]
         PP = ctypes.POINTER(PFParams)
         L.wxo_pf_step.argtypes = [PP, _D, _D]
         L.wxo_pf_run.argtypes = [PP, ctypes.c_int, _D]
@@ -165,6 +167,23 @@ def run(case, n_steps, T, q, U, V, sums=False):
     lib().wxo_run(b.ref(), int(n_steps), _ptr(T), _ptr(q), _ptr(U), _ptr(V), _ptr(m), _ptr(e))
     if sums:
         return T, q, m[:n_steps], e[:n_steps]
+    return T, q
+
+
+def step_rk3(case, T, q, U, V):
+    """One step with RK3 dynamics (wxo_step_rk3)."""
+    b = _Bound(case)
+    T, q, U, V = map(_f64, (T, q, U, V))
+    Tn, qn = np.empty_like(T), np.empty_like(q)
+    lib().wxo_step_rk3(b.ref(), _ptr(T), _ptr(q), _ptr(U), _ptr(V), _ptr(Tn), _ptr(qn))
+    return Tn, qn
+
+
+def run_rk3(case, n_steps, T, q, U, V):
+    b = _Bound(case)
+    T, q = _f64(T).copy(), _f64(q).copy()
+    U, V = _f64(U), _f64(V)
+    lib().wxo_run_rk3(b.ref(), int(n_steps), _ptr(T), _ptr(q), _ptr(U), _ptr(V))
     return T, q
 
 

@@ -49,9 +49,10 @@ static double upwind(double u, double phiL, double phiR) {
     return (u >= 0.0) ? phiL : phiR;
 }
 
-/* phi* for one field at one cell: Dh, Dz and Adv as defined in the header. */
-static double dyn_cell(const wxo_params *p, const double *phi, const double *U,
-                       const double *V, int i, int j, int k) {
+/* The dynamics tendency Dh + Dz + Adv of one field at one cell, as
+ * defined in the header; phi* = phi + dt * tendency. */
+static double dyn_tendency(const wxo_params *p, const double *phi, const double *U,
+                           const double *V, int i, int j, int k) {
     const int nx = p->nx, ny = p->ny, nz = p->nz;
     const int ie = (i + 1) % nx, iw = (i - 1 + nx) % nx;
     const int jn = (j + 1) % ny, js = (j - 1 + ny) % ny;
@@ -91,7 +92,13 @@ static double dyn_cell(const wxo_params *p, const double *phi, const double *U,
         Adv = -(1.0 / p->h) * (fe - fw + fn - fs);
     }
 
-    return c + p->dt * (Dh + Dz + Adv);
+    return Dh + Dz + Adv;
+}
+
+/* phi* for one field at one cell. */
+static double dyn_cell(const wxo_params *p, const double *phi, const double *U,
+                       const double *V, int i, int j, int k) {
+    return phi[IDX3(p, i, j, k)] + p->dt * dyn_tendency(p, phi, U, V, i, j, k);
 }
 
 void wxo_dynamics(const wxo_params *p, const double *T, const double *q,
@@ -199,15 +206,24 @@ void wxo_physics_columns(int nz, long ncol, double dt, const double *dz,
     }
 }
 
+static void physics_all(const wxo_params *p, const double *Ts, const double *qn, double *Tn);
+
 void wxo_step(const wxo_params *p, const double *T, const double *q,
               const double *U, const double *V, double *Tn, double *qn) {
     const int nx = p->nx, ny = p->ny, nz = p->nz;
     const size_t n = (size_t)nx * ny * nz;
     double *Ts = (double *)malloc(sizeof(double) * n);
     wxo_dynamics(p, T, q, U, V, Ts, qn);
+    physics_all(p, Ts, qn, Tn);
+    free(Ts);
+}
+
+/* Column physics of every column: Tn from T* and q* (T^{n+1} = T* when the
+ * physics is off). */
+static void physics_all(const wxo_params *p, const double *Ts, const double *qn, double *Tn) {
+    const int nx = p->nx, ny = p->ny, nz = p->nz;
     if (!p->physics) {
-        memcpy(Tn, Ts, sizeof(double) * n);
-        free(Ts);
+        memcpy(Tn, Ts, sizeof(double) * (size_t)nx * ny * nz);
         return;
     }
     int j;
@@ -229,7 +245,47 @@ void wxo_step(const wxo_params *p, const double *T, const double *q,
             }
         free(work);
     }
-    free(Ts);
+}
+
+/* One stage of the three-stage Runge-Kutta scheme: phi_out = phi_n +
+ * c dt L(phi_s) for T and q. */
+static void rk3_stage(const wxo_params *p, const double *Tn0, const double *qn0, const double *Ts,
+                      const double *qs, const double *U, const double *V, double cdt, double *To,
+                      double *qo) {
+    const int nx = p->nx, ny = p->ny, nz = p->nz;
+    int j;
+#pragma omp parallel for schedule(static) num_threads(wxo_threads())
+    for (j = 0; j < ny; ++j)
+        for (int k = 0; k < nz; ++k)
+            for (int i = 0; i < nx; ++i) {
+                To[IDX3(p, i, j, k)] = Tn0[IDX3(p, i, j, k)] + cdt * dyn_tendency(p, Ts, U, V, i, j, k);
+                qo[IDX3(p, i, j, k)] = qn0[IDX3(p, i, j, k)] + cdt * dyn_tendency(p, qs, U, V, i, j, k);
+            }
+}
+
+void wxo_step_rk3(const wxo_params *p, const double *T, const double *q,
+                  const double *U, const double *V, double *Tn, double *qn) {
+    const size_t n = (size_t)p->nx * p->ny * p->nz;
+    double *w = (double *)malloc(sizeof(double) * 5 * n);
+    double *T1 = w, *q1 = w + n, *T2 = w + 2 * n, *q2 = w + 3 * n, *T3 = w + 4 * n;
+    rk3_stage(p, T, q, T, q, U, V, p->dt / 3.0, T1, q1);
+    rk3_stage(p, T, q, T1, q1, U, V, p->dt / 2.0, T2, q2);
+    rk3_stage(p, T, q, T2, q2, U, V, p->dt, T3, qn);
+    physics_all(p, T3, qn, Tn);
+    free(w);
+}
+
+void wxo_run_rk3(const wxo_params *p, int n_steps, double *T, double *q,
+                 const double *U, const double *V) {
+    const size_t n = (size_t)p->nx * p->ny * p->nz;
+    double *Tn = (double *)malloc(sizeof(double) * n), *qn = (double *)malloc(sizeof(double) * n);
+    for (int s = 0; s < n_steps; ++s) {
+        wxo_step_rk3(p, T, q, U, V, Tn, qn);
+        memcpy(T, Tn, sizeof(double) * n);
+        memcpy(q, qn, sizeof(double) * n);
+    }
+    free(Tn);
+    free(qn);
 }
 
 void wxo_step_columns(const wxo_params *p, const double *T, const double *q,

@@ -106,6 +106,17 @@ double wxo_column_weighted_sum(const wxo_params *p, const double *phi);
 
 /* Threads the oracle's parallel loops use (1 when built without OpenMP). */
 
+/* The same step with the dynamics integrated by the three-stage
+ * Runge-Kutta scheme of Wicker and Skamarock (2002), the time integrator
+ * ASUCA uses (Sec. 2.1): with L the dynamics tendency (phi* = phi + dt L),
+ *   phi1 = phi^n + dt/3 L(phi^n),  phi2 = phi^n + dt/2 L(phi1),
+ *   phi3 = phi^n + dt L(phi2),
+ * then the column physics on (T3, q3) as in wxo_step; q^{n+1} = q3. */
+void wxo_step_rk3(const wxo_params *p, const double *T, const double *q,
+                  const double *U, const double *V, double *Tn, double *qn);
+void wxo_run_rk3(const wxo_params *p, int n_steps, double *T, double *q,
+                 const double *U, const double *V);
+
 /* ---------------------------------------------------------------------
  * The paper's reduced weather application, as its listings state it
  * (Sec. 3.1, Eq. 1; appendix: diffusion, physical processes, radiation,
