@@ -19,7 +19,7 @@ CUDA graph, the residual-checked MLP-surrogate step (network trained in this
 run by the library's kernels) against the plain step, and the paper's own
 reduced weather application on its three grids beside the paper's timings.
 
-  python bench.py --only f64|mixed|ensemble|surrogate|reduced_app|ablation [--nx --ny]   one variant
+  python bench.py --only f64|mixed|ensemble|surrogate|reduced_app|ablation|rk3 [--nx --ny]   one variant
 """
 from __future__ import annotations
 
@@ -445,6 +445,33 @@ def variant_ablation(steps=100):
     return out
 
 
+def variant_rk3(steps_f32=100, steps_f64=20, nx=1581, ny=1301, nz=58):
+    """WX_RK3 at the paper grid: three stage launches of the step kernel
+    (dynamics only), the stage-2 combine and the stage-3 combine fused with
+    the column physics.  HBM bytes per cell-step it moves by design:
+    3 x 16 (stages) + 32 (combine: read phi_n, E, phi_s, write) + 32 (fused
+    combine + physics: read phi_n, E, phi_s, write T, q) = 112 in FP32,
+    twice that in FP64."""
+    import torch
+    from paper_1802_05839_gb300 import wx
+    out = {}
+    for dtype, steps in (("f32", steps_f32), ("f64", steps_f64)):
+        case = make_case(dtype, nx, ny, nz)
+        ctx = wx.Context(nx, ny, nz, dtype)
+        ctx.set_params(case, flags=wx.WX_ADVECTION | wx.WX_PHYSICS | wx.WX_RK3)
+        ctx.load_fields(case.T, case.q, case.U, case.V)
+        st = torch.cuda.Stream()
+        ms = _time_steps(lambda: ctx.step(1, stream=st), steps, st)
+        ctx.sync()
+        launches = ctx.last_launches()
+        ctx.close()
+        b = 112 if dtype == "f32" else 224
+        out[dtype] = {"ms_per_step": ms, "value": case.cells / (ms * 1e-3), "unit": "cell-steps/s",
+                      "steps": steps, "gpu_launches_per_step": launches, "bytes_per_cell_step": b,
+                      "hbm_frac": case.cells * b / (ms * 1e-3) / 1e9 / peaks()[0]}
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -539,6 +566,7 @@ def run_ours(args):
             "surrogate": variant_surrogate(100, plain_ms=ms, train_epochs=args.epochs),
             "reduced_app": variant_reduced_app(100),
             "ablation": variant_ablation(100),
+            "rk3": variant_rk3(),
         }
     print(json.dumps(out))
 
@@ -557,7 +585,7 @@ def main():
     ap.add_argument("--nz", type=int, default=58, help="grid override (profiling captures only)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--epochs", type=int, default=32, help="surrogate training epochs")
-    ap.add_argument("--only", choices=["f64", "mixed", "ensemble", "surrogate", "reduced_app", "ablation"],
+    ap.add_argument("--only", choices=["f64", "mixed", "ensemble", "surrogate", "reduced_app", "ablation", "rk3"],
                     help="run one variant alone and print its record (profiling captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -575,6 +603,8 @@ def main():
             rec = variant_reduced_app(args.steps)
         elif args.only == "ablation":
             rec = variant_ablation(args.steps)
+        elif args.only == "rk3":
+            rec = variant_rk3(args.steps, max(3, args.steps // 5), args.nx, args.ny, args.nz)
         else:
             rec = variant_surrogate(args.steps, args.nx, args.ny, train_epochs=args.epochs)
         print(json.dumps({"variant": args.only, **rec}))

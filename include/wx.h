@@ -67,7 +67,13 @@ enum {
     WX_ADVECTION = 1u, /* include the upwind advection term                    */
     WX_PHYSICS = 2u,   /* run the column physics (Thomas solve + radiation)    */
     WX_SUMS = 4u,      /* record FP64 mass/energy sums after every step        */
-    WX_SURROGATE = 8u  /* column physics by the attached MLP, residual-checked */
+    WX_SURROGATE = 8u, /* column physics by the attached MLP, residual-checked */
+    WX_RK3 = 16u       /* dynamics by three-stage Runge-Kutta (Wicker-Skamarock,
+                          ASUCA's integrator, Sec. 2.1): phi1 = phi + dt/3 L(phi),
+                          phi2 = phi + dt/2 L(phi1), phi3 = phi + dt L(phi2),
+                          then the column physics on phi3; WX_F32 / WX_F64
+                          only, excludes WX_SUMS and WX_SURROGATE; one more
+                          field buffer on the device */
 };
 
 typedef struct {
@@ -83,7 +89,7 @@ typedef struct {
     const double *kappa_lev; /* [nz] vertical diffusivity profile (>= 0), host */
     const double *alpha;     /* [nz] absorber coefficient (>= 0), host         */
     const double *kappa_mult;/* [ny*nx] per-column multiplier (>= 0) or NULL   */
-    unsigned flags;          /* WX_ADVECTION | WX_PHYSICS | WX_SUMS | WX_SURROGATE */
+    unsigned flags;          /* WX_ADVECTION | WX_PHYSICS | WX_SUMS | WX_SURROGATE | WX_RK3 */
 } wx_params;
 
 /* Create a context for an nx x ny x nz grid (each >= 1; nz <= 256).

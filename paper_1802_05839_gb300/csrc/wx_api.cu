@@ -81,6 +81,7 @@ int apply_cfg(wx_ctx *c, const StepCfg &g) {
     ++c->generation;
     RC(encode_tmap(c, 0, g.ty, g.kb));
     RC(encode_tmap(c, 1, g.ty, g.kb));
+    if (c->fld[2]) RC(encode_tmap(c, 2, g.ty, g.kb));
     return WX_OK;
 }
 }  // namespace wx
@@ -163,7 +164,7 @@ extern "C" int wx_create(int nx, int ny, int nz, int dtype, wx_ctx **out) {
 extern "C" void wx_destroy(wx_ctx *c) {
     if (!c) return;
     free_surrogate(c);
-    void *ptrs[] = {c->fld[0], c->fld[1], c->U,        c->V,         c->kmult,     c->tab,
+    void *ptrs[] = {c->fld[0], c->fld[1], c->fld[2], c->tab_rk, c->U, c->V, c->kmult, c->tab,
                     c->d_lev,  c->staging, c->d_status, c->partials, c->sums_ring, c->flag_list,
                     c->flag_idx, c->flag_fac, c->flag_e, c->flag_side, c->flag_corr,
                     c->fin_park, c->fin_ticket, c->d_sums_count};
@@ -239,8 +240,10 @@ extern "C" int wx_set_params(wx_ctx *c, const wx_params *p) {
         return fail(c, WX_EINVAL, "wx_set_params: kappa_h and S0 must be finite and >= 0");
     if (!p->dz || !p->kappa_lev || !p->alpha)
         return fail(c, WX_EINVAL, "wx_set_params: dz, kappa_lev and alpha are required");
-    if (p->flags & ~(unsigned)(WX_ADVECTION | WX_PHYSICS | WX_SUMS | WX_SURROGATE))
+    if (p->flags & ~(unsigned)(WX_ADVECTION | WX_PHYSICS | WX_SUMS | WX_SURROGATE | WX_RK3))
         return fail(c, WX_EINVAL, "wx_set_params: unknown flag bits");
+    if ((p->flags & WX_RK3) && (c->dtype == WX_MIXED || (p->flags & (WX_SUMS | WX_SURROGATE))))
+        return fail(c, WX_EUNSUPPORTED, "wx_set_params: WX_RK3 needs WX_F32 or WX_F64 and excludes WX_SUMS, WX_SURROGATE");
     if ((p->flags & WX_SURROGATE) && (c->dtype != WX_F32 || c->nz != 58 || (p->flags & WX_SUMS)))
         return fail(c, WX_EUNSUPPORTED, "wx_set_params: WX_SURROGATE needs WX_F32, nz = 58 and no WX_SUMS");
     const int nz = c->nz;
@@ -292,6 +295,19 @@ extern "C" int wx_set_params(wx_ctx *c, const wx_params *p) {
             c->kmult = nullptr;
         }
         RC(setup_mixed(c, nullptr));
+    }
+    if (p->flags & WX_RK3) {
+        const size_t tbytes = (size_t)nz * kTabRec * 4 * c->t_bytes;
+        if (!c->fld[2]) {
+            const size_t fbytes = c->field_cells * c->cell_bytes;
+            CK(cudaMalloc(&c->fld[2], fbytes), "alloc RK3 stage buffer");
+            CK(cudaMemset(c->fld[2], 0, fbytes), "clear RK3 stage buffer");
+        }
+        if (!c->tab_rk) CK(cudaMalloc(&c->tab_rk, 3 * tbytes), "alloc RK3 tables");
+        for (int st = 0; st < 3; ++st)
+            RC(launch_tables_dt(c, st == 0 ? c->dt / 3.0 : (st == 1 ? c->dt / 2.0 : c->dt),
+                                (char *)c->tab_rk + st * tbytes, 0));
+        RC(encode_tmap(c, 2, c->cfg.ty, c->cfg.kb));
     }
     CK(cudaDeviceSynchronize(), "wx_set_params");
     // the kernel variant (and its shared-memory plan) depends on kappa_mult
@@ -428,6 +444,8 @@ extern "C" int wx_step(wx_ctx *c, int n_steps, void *stream) {
     if (c->flags & WX_SURROGATE) {
         if (!c->sur) return fail(c, WX_ESTATE, "wx_step: WX_SURROGATE without an attached network");
         for (int n = 0; n < n_steps; ++n) RC(launch_surrogate_step(c, s, &launches));
+    } else if (c->flags & WX_RK3) {
+        for (int n = 0; n < n_steps; ++n) RC(launch_rk3_step(c, s, &launches));
     } else {
         for (int n = 0; n < n_steps; ++n) RC(launch_step(c, s, &launches));
     }

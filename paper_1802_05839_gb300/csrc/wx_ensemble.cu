@@ -145,8 +145,8 @@ static int ens_ready(wx_ens *e) {
             return efail(e, WX_ESTATE, "member " + std::to_string(i) + ": set params and load fields first");
         if (c->flags != c0->flags || (c->kmult != nullptr) != (c0->kmult != nullptr))
             return efail(e, WX_EINVAL, "members must share the option flags and kappa_mult use");
-        if (c->flags & WX_SURROGATE)
-            return efail(e, WX_EUNSUPPORTED, "WX_SURROGATE members step with wx_step, not in a batch");
+        if (c->flags & (WX_SURROGATE | WX_RK3))
+            return efail(e, WX_EUNSUPPORTED, "WX_SURROGATE and WX_RK3 members step with wx_step, not in a batch");
         if (c->cfg.ty != e->cfg.ty || c->cfg.kb != e->cfg.kb) {
             const int rc = apply_cfg(c, e->cfg);
             if (rc != WX_OK) return efail(e, rc, c->err);

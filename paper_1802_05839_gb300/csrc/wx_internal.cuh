@@ -124,9 +124,16 @@ struct wx_ctx {
     int cell_bytes = 0, t_bytes = 0;
     int device = 0, num_sms = 0;
 
-    void *fld[2] = {nullptr, nullptr};
+    void *fld[3] = {nullptr, nullptr, nullptr};  // ping-pong + the RK3 stage buffer
     int cur = 0;
-    CUtensorMap tmap[2];
+    CUtensorMap tmap[3];
+    // WX_RK3: tables of the three stage steps dt/3, dt/2, dt; while a stage
+    // runs, the batch launcher reads buffer stage_in, writes stage_out with
+    // step stage_dt and table stage_tab, and leaves `cur` alone
+    void *tab_rk = nullptr;
+    int stage_in = -1, stage_out = -1;
+    double stage_dt = 0;
+    const void *stage_tab = nullptr;
 
     void *U = nullptr, *V = nullptr, *kmult = nullptr, *tab = nullptr;
     double *d_lev = nullptr;     // FP64 dz, kappa_lev, alpha [3][nz]
@@ -177,6 +184,8 @@ namespace wx {
 
 // launchers implemented in wx_step.cu
 int launch_tables(wx_ctx *c, cudaStream_t s);
+int launch_tables_dt(wx_ctx *c, double dt, void *dst, cudaStream_t s);
+int launch_rk3_step(wx_ctx *c, cudaStream_t s, long *launches);
 int launch_pack(wx_ctx *c, const double *T, const double *q, void *dst, cudaStream_t s);
 int launch_unpack(wx_ctx *c, const void *src, double *T, double *q, cudaStream_t s);
 int launch_convert(wx_ctx *c, const double *src, void *dst, size_t n, cudaStream_t s);

@@ -878,6 +878,16 @@ static int grid_for(size_t n) {
     return (int)(b > 65535 * 8 ? 65535 * 8 : (b == 0 ? 1 : b));
 }
 
+// Tables for another step length (the RK3 stages), written to dst.
+int launch_tables_dt(wx_ctx *c, double dt, void *dst, cudaStream_t s) {
+    if (c->t_bytes == 4)
+        tables_kernel<float><<<1, 32, 0, s>>>(c->d_lev, c->nz, dt, c->kappa_h, c->S0, c->q_ref, (Q4<float> *)dst);
+    else
+        tables_kernel<double><<<1, 32, 0, s>>>(c->d_lev, c->nz, dt, c->kappa_h, c->S0, c->q_ref, (Q4<double> *)dst);
+    WX_CK(cudaGetLastError(), "tables kernel");
+    return WX_OK;
+}
+
 int launch_tables(wx_ctx *c, cudaStream_t s) {
     if (c->t_bytes == 4)
         tables_kernel<float><<<1, 32, 0, s>>>(c->d_lev, c->nz, c->dt, c->kappa_h, c->S0, c->q_ref,
@@ -1000,14 +1010,16 @@ StepCfg default_cfg(const wx_ctx *c) {
 // A batch = the members one launch steps (one context, or an ensemble's
 // members), with the launch configuration of its owner.
 template <typename T> static void fill_member(const wx_ctx *c, Member<T> &M, long tile0, int ty) {
-    const int src = c->cur, dst = 1 - c->cur;
+    const bool stage = c->stage_in >= 0;  // one RK3 stage: its buffers, step and table
+    const int src = stage ? c->stage_in : c->cur, dst = stage ? c->stage_out : 1 - c->cur;
+    const double dt = stage ? c->stage_dt : c->dt;
     M.tin = c->tmap[src];
     StepArgs<T> &a = M.a;
     a.out = reinterpret_cast<T *>(c->fld[dst]);
     a.U = (const T *)c->U;
     a.V = (const T *)c->V;
     a.kmult = (const T *)c->kmult;
-    a.tab = (const Q4<T> *)c->tab;
+    a.tab = (const Q4<T> *)(stage ? c->stage_tab : c->tab);
     a.status = c->d_status;
     a.partials = c->partials;
     a.nx = c->nx;
@@ -1015,8 +1027,8 @@ template <typename T> static void fill_member(const wx_ctx *c, Member<T> &M, lon
     a.nz = c->nz;
     a.P = c->P;
     a.R = c->R;
-    a.dth = (T)(c->dt / c->h);
-    a.dh = (T)(c->dt * c->kappa_h / (c->h * c->h));
+    a.dth = (T)(dt / c->h);
+    a.dh = (T)(dt * c->kappa_h / (c->h * c->h));
     a.advection = (c->flags & WX_ADVECTION) ? 1 : 0;
     a.flag_idx = c->flag_idx;
     a.side = c->flag_side;
@@ -1118,7 +1130,7 @@ static int after_step(wx_ctx *c, int ty_used, cudaStream_t s, long *launches) {
         WX_CK(cudaGetLastError(), "sums kernel");
         ++*launches;
     }
-    c->cur = dst;
+    if (c->stage_in < 0) c->cur = dst;  // an RK3 stage leaves the buffer order to its driver
     return WX_OK;
 }
 
@@ -1146,6 +1158,171 @@ int launch_batch(wx_ctx *const *mem, int n, const StepCfg &cfg, unsigned *status
 int launch_step(wx_ctx *c, cudaStream_t s, long *launches) {
     wx_ctx *mem[1] = {c};
     return launch_batch(mem, 1, c->cfg, c->d_status, s, launches, c->err);
+}
+
+// ------------------------------------------------------------- WX_RK3
+// phi_out = phi_n + (E - phi_s) over whole state buffers (both fields,
+// ghost ring and padding included): E = phi_s + c dt L(phi_s) is what the
+// step kernel writes for one stage, so this is phi_n + c dt L(phi_s).
+template <typename T>
+__global__ void rk_combine_kernel(const T *__restrict__ base, const T *E, const T *S, T *out, size_t n) {
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        out[e] = base[e] + (E[e] - S[e]);
+}
+
+// The last RK3 stage's combine fused with the column physics, one thread
+// per column: phi3 = A + (E - S) for T and q (out holds E, the stage
+// kernel's output), q^{n+1} = q3, and T^{n+1} = the column physics of
+// (T3, q3), all written over `out` with the ghost copies.  Without a
+// per-column kappa_mult the elimination comes from the table, run from the
+// top with the heating folded into the back substitution as in the step
+// kernel (FMA-only recurrences; scratch F_k in shared memory); with one,
+// the forward sweep divides per level (scratch c'_k, d'_k).
+template <typename T, bool TABLE>
+__global__ void __launch_bounds__(64) rk_physics_kernel(T *__restrict__ out, const T *__restrict__ A,
+                                                        const T *__restrict__ S, int nx, int ny, int nz, int P,
+                                                        int R, const T *__restrict__ km,
+                                                        const Q4<T> *__restrict__ tab,
+                                                        unsigned *__restrict__ status) {
+    extern __shared__ __align__(16) unsigned char psm[];
+    T *scr = reinterpret_cast<T *>(psm);  // [level][thread], 1 or 2 arrays
+    const int t = threadIdx.x, nt = blockDim.x;
+    const long c = (long)blockIdx.x * nt + t;
+    if (c >= (long)nx * ny) return;
+    const int j = (int)(c / nx), i = (int)(c - (long)j * nx);
+    const size_t plane = (size_t)R * P, off = (size_t)(j + 1) * P + i + kGhostX;
+    auto at = [&](int k, int f) { return off + (size_t)(2 * k + f) * plane; };
+    auto phi3 = [&](int k, int f) { const size_t o = at(k, f); return A[o] + (out[o] - S[o]); };
+    auto put = [&](int k, int f, T v) {
+        T *row = out + at(k, f);
+        row[0] = v;
+        if (i == 0) row[nx] = v;                   // -> right ghost column
+        if (i == nx - 1) row[-nx] = v;             // -> left ghost column
+        if (j == 0) row[(size_t)ny * P] = v;       // -> top ghost row
+        if (j == ny - 1) row[-(long)ny * P] = v;   // -> bottom ghost row
+    };
+    const Q4<T> *tB = tab + REC_B * nz, *tC = tab + REC_C * nz, *tD = tab + REC_D * nz, *tE = tab + REC_E * nz;
+    bool ok = true;
+    if (TABLE) {
+        // pass 1, top down: q3 stored, optical depth, elimination, F_{k+1}
+        T tau = 0, Etop = 1, f_up = 0, h_up = 0;
+        for (int k = nz - 1; k >= 0; --k) {
+            const T q3 = phi3(k, 1), t3 = phi3(k, 0);
+            put(k, 1, q3);
+            ok = ok && isfinite((double)q3);
+            const T taub = tau + tB[k].z * q3;
+            const T Eb = exp2_neg(taub);
+            const T h = tC[k].x * (Etop - Eb);
+            const T f = (t3 + tC[k].z * f_up) * tD[k].x;
+            if (k < nz - 1) scr[(size_t)(k + 1) * nt + t] = f_up + h_up + tD[k + 1].z * h;
+            f_up = f;
+            h_up = h;
+            Etop = Eb;
+            tau = taub;
+        }
+        scr[t] = f_up + h_up;  // level 0: e_0 = 0
+        // pass 2, bottom up: T_k = F_k - e_k T_{k-1}
+        T prev = 0;
+        for (int k = 0; k < nz; ++k) {
+            const T v = scr[(size_t)k * nt + t] - tD[k].z * prev;
+            ok = ok && isfinite((double)v);
+            put(k, 0, v);
+            prev = v;
+        }
+    } else {
+        T *cp = scr, *dp = scr + (size_t)nz * nt;
+        const T s = km[c];
+        T cpp = 0, dpp = 0;
+        for (int k = 0; k < nz; ++k) {
+            const T ak = s * tE[k].x, ck = s * tE[k].y;
+            const T m = ((T(1) - ak) - ck) - ak * cpp;
+            const T inv = recip(m);
+            cpp = ck * inv;
+            dpp = (phi3(k, 0) - ak * dpp) * inv;
+            cp[(size_t)k * nt + t] = cpp;
+            dp[(size_t)k * nt + t] = dpp;
+        }
+        T x = 0, tau = 0, Etop = 1;
+        for (int k = nz - 1; k >= 0; --k) {
+            const T q3 = phi3(k, 1);
+            x = dp[(size_t)k * nt + t] - cp[(size_t)k * nt + t] * x;
+            const T taub = tau + tB[k].z * q3;
+            const T Eb = exp2_neg(taub);
+            const T v = x + tC[k].x * (Etop - Eb);
+            ok = ok && isfinite((double)v) && isfinite((double)q3);
+            put(k, 0, v);
+            put(k, 1, q3);
+            Etop = Eb;
+            tau = taub;
+        }
+    }
+    if (!ok) atomicOr(status, ST_NONFINITE);
+}
+
+// One RK3 step: with A = the current state, B = the other ping-pong buffer
+// and C = the stage buffer,
+//   stage 1: B <- step_{dt/3}(A)              (phi1 = A + dt/3 L(A))
+//   stage 2: C <- step_{dt/2}(B); C <- A + (C - B)
+//   stage 3: B <- step_{dt}(C);   then, fused with the column physics,
+//            phi3 = A + (B - C) and B <- physics(phi3)  (WX_PHYSICS), or
+//            B <- A + (B - C)
+//   B becomes current.  The step kernel runs without physics in every stage.
+template <typename T> static int rk_combine(wx_ctx *c, int base, int e, int st, int out, cudaStream_t s) {
+    const size_t n = 2 * c->field_cells;
+    rk_combine_kernel<T><<<grid_for(n), 256, 0, s>>>((const T *)c->fld[base], (const T *)c->fld[e],
+                                                     (const T *)c->fld[st], (T *)c->fld[out], n);
+    WX_CK(cudaGetLastError(), "RK3 combine kernel");
+    return WX_OK;
+}
+
+template <typename T> static int rk_physics(wx_ctx *c, int A, int B, int C, cudaStream_t s) {
+    constexpr int nt = 64;
+    const bool table = c->kmult == nullptr;
+    const size_t sm = (size_t)nt * c->nz * sizeof(T) * (table ? 1 : 2);
+    const unsigned g = (unsigned)(((long)c->nx * c->ny + nt - 1) / nt);
+    auto kern = table ? rk_physics_kernel<T, true> : rk_physics_kernel<T, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess) {
+        kern<<<g, nt, sm, s>>>((T *)c->fld[B], (const T *)c->fld[A], (const T *)c->fld[C], c->nx, c->ny, c->nz,
+                               c->P, c->R, (const T *)c->kmult, (const Q4<T> *)c->tab, c->d_status);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "RK3 physics kernel");
+    return WX_OK;
+}
+
+int launch_rk3_step(wx_ctx *c, cudaStream_t s, long *launches) {
+    const int A = c->cur, B = 1 - c->cur, C = 2;
+    const size_t tbytes = (size_t)c->nz * kTabRec * 4 * c->t_bytes;
+    const unsigned saved = c->flags;
+    const bool f32 = c->t_bytes == 4;
+    c->flags = saved & WX_ADVECTION;
+    int rc = WX_OK;
+    const int in[3] = {A, B, C}, out[3] = {B, C, B};
+    const double dts[3] = {c->dt / 3.0, c->dt / 2.0, c->dt};
+    for (int st = 0; st < 3 && rc == WX_OK; ++st) {
+        c->stage_in = in[st];
+        c->stage_out = out[st];
+        c->stage_dt = dts[st];
+        c->stage_tab = (const char *)c->tab_rk + st * tbytes;
+        rc = launch_step(c, s, launches);
+        if (rc == WX_OK && (st == 1 || (st == 2 && !(saved & WX_PHYSICS)))) {
+            rc = f32 ? rk_combine<float>(c, A, out[st], in[st], out[st], s)
+                     : rk_combine<double>(c, A, out[st], in[st], out[st], s);
+            ++*launches;
+        }
+    }
+    c->stage_in = c->stage_out = -1;
+    c->stage_tab = nullptr;
+    c->flags = saved;
+    if (rc != WX_OK) return rc;
+    if (saved & WX_PHYSICS) {
+        const int r2 = f32 ? rk_physics<float>(c, A, B, C, s) : rk_physics<double>(c, A, B, C, s);
+        if (r2 != WX_OK) return r2;
+        ++*launches;
+    }
+    c->cur = B;
+    return WX_OK;
 }
 
 // WX_MIXED set-up: flag the columns whose dominance ratio is below the

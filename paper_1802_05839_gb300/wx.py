@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libwx.so")
 
 WX_F32, WX_F64, WX_MIXED = 0, 1, 2
-WX_ADVECTION, WX_PHYSICS, WX_SUMS, WX_SURROGATE = 1, 2, 4, 8
+WX_ADVECTION, WX_PHYSICS, WX_SUMS, WX_SURROGATE, WX_RK3 = 1, 2, 4, 8, 16
 STATUS = {0: "WX_OK", -1: "WX_EINVAL", -2: "WX_ENOMEM", -3: "WX_ECUDA", -4: "WX_ECFL",
           -5: "WX_ENONFINITE", -6: "WX_ETIMEOUT", -7: "WX_ESTATE", -8: "WX_EUNSUPPORTED"}
 DTYPES = {"f32": WX_F32, "f64": WX_F64, "mixed": WX_MIXED}

@@ -1,0 +1,110 @@
+"""WX_RK3: the three-stage Runge-Kutta dynamics followed by the column
+physics, on the GPU (stage kernel runs, combine kernels, planar physics)
+against the FP64 oracle's wxo_step_rk3: FP64 <= 1e-12 and FP32 <= 1e-5 max
+relative error per step, FP32 <= 1e-4 relative L2 after 100 steps; a run
+restarted from its saved state equals the uninterrupted run bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1802_05839_gb300 import inputs, wx
+
+pytestmark = pytest.mark.gpu
+
+RK = wx.WX_ADVECTION | wx.WX_PHYSICS | wx.WX_RK3
+
+
+def relmax(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def ctx_for(case, dtype, flags=RK):
+    ctx = wx.Context(case.nx, case.ny, case.nz, dtype)
+    ctx.set_params(case, flags=flags)
+    ctx.load_fields(case.T, case.q, case.U, case.V)
+    return ctx
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 1e-5)])
+@pytest.mark.parametrize("shape,ns", [((37, 29, 8), False), ((33, 5, 3), False), ((1, 7, 5), False),
+                                      ((70, 50, 58), True)])
+def test_every_step_matches_oracle(dtype, tol, shape, ns):
+    nx, ny, nz = shape
+    case = inputs.paper_grid_case(nx, ny, nz, seed=4, near_singular=ns)
+    if dtype == "f32":
+        case = inputs.round_to_f32(case)
+    ctx = ctx_for(case, dtype)
+    T, q = case.T, case.q
+    for _ in range(4):
+        ctx.step(1)
+        ctx.sync()
+        Tg, qg = ctx.read_fields()
+        To, qo = oracle.step_rk3(case, T, q, case.U, case.V)
+        assert relmax(Tg, To) <= tol and relmax(qg, qo) <= tol
+        T, q = Tg, qg  # per-step error: the next oracle step starts from the GPU state
+    assert ctx.last_launches() == 5  # 3 stage kernels, 1 combine, combine + physics
+    ctx.close()
+
+
+def test_hundred_steps_fp32_relative_l2():
+    case = inputs.round_to_f32(inputs.small_case(64, 48, 16, seed=8))
+    ctx = ctx_for(case, "f32")
+    ctx.step(100)
+    ctx.sync()
+    Tg, qg = ctx.read_fields()
+    To, qo = oracle.run_rk3(case, 100, case.T, case.q, case.U, case.V)
+    assert np.linalg.norm(Tg - To) / np.linalg.norm(To) <= 1e-4
+    assert np.linalg.norm(qg - qo) / np.linalg.norm(qo) <= 1e-4
+    ctx.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_restart_is_bitwise(dtype):
+    case = inputs.paper_grid_case(45, 33, 12, seed=9)
+    if dtype == "f32":
+        case = inputs.round_to_f32(case)
+    a = ctx_for(case, dtype)
+    a.step(4)
+    a.sync()
+    b = ctx_for(case, dtype)
+    b.step(2)
+    b.sync()
+    T, q = b.read_fields()
+    b.load_fields(T, q, case.U, case.V)
+    b.step(2)
+    b.sync()
+    Ta, qa = a.read_fields()
+    Tb, qb = b.read_fields()
+    assert np.array_equal(Ta, Tb) and np.array_equal(qa, qb)
+    a.close()
+    b.close()
+
+
+def test_rk3_differs_from_euler_and_configuration_errors():
+    case = inputs.round_to_f32(inputs.small_case(40, 30, 8, seed=2))
+    e = ctx_for(case, "f64", flags=wx.WX_ADVECTION | wx.WX_PHYSICS)
+    r = ctx_for(case, "f64")
+    e.step(3)
+    r.step(3)
+    e.sync()
+    r.sync()
+    assert not np.array_equal(e.read_fields()[0], r.read_fields()[0])
+    e.close()
+    r.close()
+    m = wx.Context(40, 30, 8, "mixed")
+    with pytest.raises(wx.WxError) as ei:
+        m.set_params(case, flags=RK)
+    assert ei.value.code == -8
+    m.close()
+    f = wx.Context(40, 30, 8, "f32")
+    with pytest.raises(wx.WxError) as ei:
+        f.set_params(case, flags=RK | wx.WX_SUMS)
+    assert ei.value.code == -8
+    f.close()
+    ens = wx.Ensemble([(40, 30, 8)], "f32")
+    ens.members[0].set_params(case, flags=RK)
+    ens.members[0].load_fields(case.T, case.q, case.U, case.V)
+    with pytest.raises(wx.WxError) as ei:
+        ens.step(1)
+    assert ei.value.code == -8
+    ens.close()
