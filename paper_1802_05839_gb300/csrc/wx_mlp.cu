@@ -288,19 +288,25 @@ static bool encode_operand(CUtensorMap *m, const void *ptr, int rows, int K, int
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Descriptors are cached per (pointer, shape): the MLP reuses its buffers.
+// Descriptors are cached per (device, pointer, shape): the MLP reuses its
+// buffers.  The cache is cleared when it grows past kMapCacheMax entries
+// (callers that pass a fresh buffer every call, e.g. gathered minibatches).
+constexpr size_t kMapCacheMax = 4096;
 static std::mutex g_map_mu;
-static std::map<std::tuple<const void *, int, int, int>, CUtensorMap> g_maps;
+static std::map<std::tuple<int, const void *, int, int, int>, CUtensorMap> g_maps;
 
 static bool operand_map(CUtensorMap *m, const void *ptr, int rows, int K, int box_rows) {
+    int dev = 0;
+    cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(g_map_mu);
-    auto key = std::make_tuple(ptr, rows, K, box_rows);
+    auto key = std::make_tuple(dev, ptr, rows, K, box_rows);
     auto it = g_maps.find(key);
     if (it != g_maps.end()) {
         *m = it->second;
         return true;
     }
     if (!encode_operand(m, ptr, rows, K, box_rows)) return false;
+    if (g_maps.size() >= kMapCacheMax) g_maps.clear();
     g_maps[key] = *m;
     return true;
 }
@@ -311,12 +317,9 @@ template <int BN, int EPI> static cudaError_t gemm_launch(const CUtensorMap &a, 
     const int smem = gemm_smem(BN);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long tiles = (long)(g.M / 128) * (g.N / BN);
     k<<<(unsigned)std::min<long>(tiles, sms), kGemmThreads, smem, s>>>(a, b, g);
     return cudaGetLastError();
@@ -1263,10 +1266,12 @@ int launch_surrogate_step(wx_ctx *c, cudaStream_t s, long *launches) {
     }
     // 4. residual checks, fallback, T^{n+1}
     constexpr int apply_smem = kSB * (kTS + kYS) * (int)sizeof(float);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(sur_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, apply_smem);
-        attr = true;
+    {   // a per-device function attribute: set on every launch (cheap)
+        cudaError_t e = cudaFuncSetAttribute(sur_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, apply_smem);
+        if (e != cudaSuccess) {
+            c->err = std::string("surrogate apply attribute: ") + cudaGetErrorString(e);
+            return WX_ECUDA;
+        }
     }
     sur_apply_kernel<<<(unsigned)((ncol + kSB - 1) / kSB), kApplyThreads, apply_smem, s>>>(
         f, c->nx, c->ny, c->P, c->R, (const float *)c->kmult, (const Q4<float> *)c->tab, c->sur_Y, m->norm,
