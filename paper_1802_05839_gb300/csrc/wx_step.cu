@@ -958,10 +958,12 @@ int launch_columns(wx_ctx *c, const void *Ts, const void *qs, const void *km, vo
 }
 
 
-// WX_MIXED routes every column with kappa_mult != 1 through the side list,
-// so its step kernel keeps the kappa_mult = 1 table path (KMODE 2).
-static bool mixed(const wx_ctx *c) { return c->dtype == WX_MIXED && c->n_list > 0; }
-static bool per_col(const wx_ctx *c) { return c->kmult != nullptr && c->dtype != WX_MIXED; }
+// FP32 storage (WX_MIXED and WX_F32) with listed kappa_mult != 1 columns:
+// table path for every column, side solve for the listed ones (in FP64 for
+// the weakly dominant columns of WX_MIXED, in FP32 otherwise).  FP64
+// storage with kappa_mult eliminates per column on the fly.
+static bool mixed(const wx_ctx *c) { return (c->dtype == WX_MIXED || c->dtype == WX_F32) && c->n_list > 0; }
+static bool per_col(const wx_ctx *c) { return c->kmult != nullptr && c->dtype == WX_F64; }
 
 bool cfg_fits(const wx_ctx *c, const StepCfg &cfg, int *smem_bytes) {
     const SmemPlan p = plan_smem(c->nz, cfg.ty, cfg.stages, cfg.kb, c->t_bytes, per_col(c));
@@ -1336,14 +1338,15 @@ int setup_mixed(wx_ctx *c, const double *km64) {
             *p = nullptr;
         }
     c->n_flag = c->n_list = 0;
-    if (c->dtype != WX_MIXED || !km64) return WX_OK;
+    if ((c->dtype != WX_MIXED && c->dtype != WX_F32) || !km64) return WX_OK;
+    // WX_F32 lists the kappa_mult != 1 columns but solves none of them in FP64
+    const double thr = c->dtype == WX_MIXED ? c->dd_threshold : 0.0;
     const int ny = c->ny, nx = c->nx, nz = c->nz;
     const size_t ncol = (size_t)nx * ny;
     int *d_cnt = nullptr;  // [4][ny]: count64, count32, off64, off32; then the classes
     WX_CK(cudaMalloc(&d_cnt, 4 * (size_t)ny * sizeof(int) + ncol), "alloc flag counts");
     unsigned char *cls = reinterpret_cast<unsigned char *>(d_cnt + 4 * (size_t)ny);
-    flag_class_kernel<<<(unsigned)((ncol + 255) / 256), 256>>>(c->d_lev, km64, (long)ncol, nz, c->dt,
-                                                               c->dd_threshold, cls);
+    flag_class_kernel<<<(unsigned)((ncol + 255) / 256), 256>>>(c->d_lev, km64, (long)ncol, nz, c->dt, thr, cls);
     flag_count_kernel<<<(ny + 127) / 128, 128>>>(cls, nx, ny, d_cnt, d_cnt + ny);
     std::vector<int> cnt(2 * (size_t)ny), off(2 * (size_t)ny);
     cudaError_t e = cudaMemcpy(cnt.data(), d_cnt, 2 * ny * sizeof(int), cudaMemcpyDeviceToHost);
