@@ -207,6 +207,27 @@ def e2e_measure(case, dtype, iters=3):
             "path": "wx_load_fields(host) + wx_step(1) + wx_read_fields(host)"}
 
 
+# ---------------------------------------------------------------- replicas
+# With N GPUs the bench runs N independent replicas of the workload (the
+# step has no exchange between GPUs: one grid per GPU).  The job's time is
+# the slowest rank's; the job's throughput counts every rank's cells.
+def max_over_ranks(ms, device="cuda"):
+    """The largest of every rank's `ms` (all ranks receive it)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, cells_per_rank, ms_per_step):
+    """Whole-job cell-steps/s of `world` replicas, each stepping
+    `cells_per_rank` cells, timed by the slowest rank."""
+    return world * cells_per_rank / (ms_per_step * 1e-3)
+
+
 def _events(n):
     import torch
     return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
@@ -518,10 +539,8 @@ def run_ours(args):
     per = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
     if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = max_over_ranks(total_ms)
         dist.barrier()
-        total_ms = float(t.item())
     launches = ctx.last_launches() * args.steps  # one wx_step(1) per timed step
     step_cfg = ctx.step_config()
     ctx.close()
@@ -531,7 +550,7 @@ def run_ours(args):
         return
 
     ms = total_ms / args.steps
-    value = world * case.cells / (ms * 1e-3)
+    value = job_throughput(world, case.cells, ms)
     peak, peak_kind = peaks()
     alg_bytes = case.cells * CELL_BYTES[dtype] + case.nx * case.ny * COL_BYTES[dtype]
     kern_ms = statistics.mean(per)
