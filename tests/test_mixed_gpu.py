@@ -117,3 +117,25 @@ def test_error_against_the_oracle_at_steps_1_100_500():
             if dtype == "mixed":
                 bound = {1: 1e-5, 100: 1e-4, 500: 5e-4}[m]
                 assert eT <= bound and eq <= bound
+
+
+@pytest.mark.parametrize("shape", [(97, 61, 58), (70, 33, 17)])
+def test_fp32_with_kappa_mult_matches_oracle(shape):
+    """WX_F32 with a kappa_mult field: the table path plus the FP32 side
+    solve of the kappa_mult != 1 columns, within the FP32 step bound that the
+    weakly dominant columns allow (3e-5 per step, as for WX_MIXED)."""
+    nx, ny, nz = shape
+    case = inputs.round_to_f32(inputs.paper_grid_case(nx, ny, nz, seed=7, near_singular=True))
+    ctx = wx.Context(nx, ny, nz, "f32")
+    ctx.set_params(case)
+    ctx.load_fields(case.T, case.q, case.U, case.V)
+    assert ctx.flagged_columns() == 0      # none in FP64
+    T, q = case.T, case.q
+    for _ in range(3):
+        ctx.step(1)
+        ctx.sync()
+        Tg, qg = ctx.read_fields()
+        To, qo = oracle.step(case, T, q, case.U, case.V)
+        assert maxrel(Tg, To) <= 3e-5 and maxrel(qg, qo) <= 1e-5
+        T, q = Tg, qg
+    ctx.close()
