@@ -603,7 +603,7 @@ def main():
     ap.add_argument("--ny", type=int, default=1301, help="grid override (profiling captures only)")
     ap.add_argument("--nz", type=int, default=58, help="grid override (profiling captures only)")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--epochs", type=int, default=32, help="surrogate training epochs")
+    ap.add_argument("--epochs", type=int, default=64, help="surrogate training epochs")
     ap.add_argument("--only", choices=["f64", "mixed", "ensemble", "surrogate", "reduced_app", "ablation", "rk3"],
                     help="run one variant alone and print its record (profiling captures)")
     args = ap.parse_args()
