@@ -178,8 +178,10 @@ def run_reference(args):
     }))
 
 
-def e2e_measure(case, dtype, iters=3):
-    """Load (H2D from pinned host) + one step + read back (D2H) per step."""
+def e2e_measure(case, dtype, iters=5):
+    """Load (H2D from pinned host) + one step + read back (D2H) per step;
+    the median over `iters` steps (host-side copies on a shared host vary
+    from one iteration to the next), the mean beside it."""
     import torch
     from paper_1802_05839_gb300 import wx
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
@@ -192,19 +194,22 @@ def e2e_measure(case, dtype, iters=3):
     ctx.step(1)
     ctx.sync()
     ctx.read_fields()
-    t0 = time.perf_counter()
+    lib = wx.lib()
+    times = []
     for _ in range(iters):
+        t0 = time.perf_counter()
         ctx.load_fields(T, q, U, V)
         ctx.step(1)
         ctx.sync()
-        lib = wx.lib()
         wx._check(lib.wx_read_fields(ctx.ptr, wx._dptr(To), wx._dptr(qo)), ctx.ptr)
-    el = (time.perf_counter() - t0) / iters
+        times.append(time.perf_counter() - t0)
+    el = statistics.median(times)
     ctx.close()
     h2d = T.nbytes + q.nbytes + U.nbytes + V.nbytes
     return {"value": case.cells / el, "unit": "cell-steps/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(To.nbytes + qo.nbytes), "ms_per_step": el * 1e3,
-            "path": "wx_load_fields(host) + wx_step(1) + wx_read_fields(host)"}
+            "ms_per_step_mean": statistics.mean(times) * 1e3, "iterations": iters,
+            "path": "wx_load_fields(host) + wx_step(1) + wx_read_fields(host), median step"}
 
 
 # ---------------------------------------------------------------- replicas
