@@ -121,6 +121,15 @@ int wx_step(wx_ctx *c, int n_steps, void *cuda_stream);
  * a status (WX_ENONFINITE, WX_ETIMEOUT) or WX_OK.  Clears the word. */
 int wx_sync(wx_ctx *c);
 
+/* The state (T, q) alone in FP32 [nz][ny][nx], for WX_F32 / WX_MIXED
+ * contexts (WX_EUNSUPPORTED for WX_F64): the values the context stores, so
+ * half the bytes of wx_load_fields / wx_read_fields and no rounding.  The
+ * winds must have been loaded by wx_load_fields (WX_ESTATE otherwise); they
+ * are kept.  Loading resets the sums record like wx_load_fields.  Host
+ * (src_is_device = 0) or device input; host output; synchronous. */
+int wx_load_state_f32(wx_ctx *c, const float *T, const float *q, int src_is_device);
+int wx_read_state_f32(wx_ctx *c, float *T, float *q);
+
 /* Copy the current state to host FP64 arrays T, q [nz][ny][nx] (either may
  * be NULL).  Synchronous; a checkpoint that wx_load_fields restores. */
 int wx_read_fields(wx_ctx *c, double *T, double *q);

@@ -433,6 +433,47 @@ extern "C" int wx_read_fields(wx_ctx *c, double *T, double *q) {
     return WX_OK;
 }
 
+// FP32 state in and out (FP32-storage contexts): the step's inputs and
+// results in their storage precision, half the bytes of the FP64 calls.
+extern "C" int wx_load_state_f32(wx_ctx *c, const float *T, const float *q, int src_is_device) {
+    if (!c) return WX_EINVAL;
+    if (!T || !q) return fail(c, WX_EINVAL, "wx_load_state_f32: NULL array");
+    if (c->t_bytes != 4) return fail(c, WX_EUNSUPPORTED, "wx_load_state_f32: the context stores FP64");
+    if (!c->fields_loaded) return fail(c, WX_ESTATE, "wx_load_state_f32: load the winds with wx_load_fields first");
+    const size_t n = (size_t)c->nx * c->ny * c->nz;
+    const float *dT = T, *dq = q;
+    if (!src_is_device) {
+        RC(ensure_staging(c));  // 2n doubles: room for 2n floats
+        float *sT = reinterpret_cast<float *>(c->staging), *sq = sT + n;
+        CK(cudaMemcpy(sT, T, n * sizeof(float), cudaMemcpyHostToDevice), "upload T");
+        CK(cudaMemcpy(sq, q, n * sizeof(float), cudaMemcpyHostToDevice), "upload q");
+        dT = sT;
+        dq = sq;
+    }
+    CK(cudaDeviceSynchronize(), "wx_load_state_f32");
+    c->cur = 0;
+    RC(launch_pack_f32(c, dT, dq, c->fld[0], 0));
+    CK(cudaMemset(c->d_sums_count, 0, sizeof(long long)), "reset sums count");
+    CK(cudaDeviceSynchronize(), "wx_load_state_f32");
+    ++c->generation;
+    return WX_OK;
+}
+
+extern "C" int wx_read_state_f32(wx_ctx *c, float *T, float *q) {
+    if (!c) return WX_EINVAL;
+    if (c->t_bytes != 4) return fail(c, WX_EUNSUPPORTED, "wx_read_state_f32: the context stores FP64");
+    if (!c->fields_loaded) return fail(c, WX_ESTATE, "wx_read_state_f32: no fields loaded");
+    const size_t n = (size_t)c->nx * c->ny * c->nz;
+    RC(ensure_staging(c));
+    float *sT = reinterpret_cast<float *>(c->staging), *sq = sT + n;
+    CK(cudaDeviceSynchronize(), "wx_read_state_f32");
+    RC(launch_unpack_f32(c, c->fld[c->cur], T ? sT : nullptr, q ? sq : nullptr, 0));
+    CK(cudaDeviceSynchronize(), "unpack");
+    if (T) CK(cudaMemcpy(T, sT, n * sizeof(float), cudaMemcpyDeviceToHost), "download T");
+    if (q) CK(cudaMemcpy(q, sq, n * sizeof(float), cudaMemcpyDeviceToHost), "download q");
+    return WX_OK;
+}
+
 // ------------------------------------------------------------ stepping
 extern "C" int wx_step(wx_ctx *c, int n_steps, void *stream) {
     if (!c) return WX_EINVAL;

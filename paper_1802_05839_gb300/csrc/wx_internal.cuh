@@ -188,6 +188,8 @@ int launch_tables_dt(wx_ctx *c, double dt, void *dst, cudaStream_t s);
 int launch_rk3_step(wx_ctx *c, cudaStream_t s, long *launches);
 int launch_pack(wx_ctx *c, const double *T, const double *q, void *dst, cudaStream_t s);
 int launch_unpack(wx_ctx *c, const void *src, double *T, double *q, cudaStream_t s);
+int launch_pack_f32(wx_ctx *c, const float *T, const float *q, void *dst, cudaStream_t s);
+int launch_unpack_f32(wx_ctx *c, const void *src, float *T, float *q, cudaStream_t s);
 int launch_convert(wx_ctx *c, const double *src, void *dst, size_t n, cudaStream_t s);
 int launch_step(wx_ctx *c, cudaStream_t s, long *launches);
 int launch_batch(wx_ctx *const *members, int n, const StepCfg &cfg, unsigned *status, cudaStream_t s,

@@ -773,46 +773,6 @@ __global__ void tables_kernel(const double *lev, int nz, double dt, double kappa
     }
 }
 
-// FP64 [nz][ny][nx] (T, q) -> planar padded fields with the ghost ring.
-template <typename T>
-__global__ void pack_kernel(const double *__restrict__ Tsrc, const double *__restrict__ qsrc, T *__restrict__ dst,
-                            int nx, int ny, int nz, int P, int R) {
-    const size_t n = (size_t)P * R * 2 * nz;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        const int ip = (int)(e % P);
-        const int jp = (int)((e / P) % R);
-        const int f = (int)((e / ((size_t)P * R)) % 2);
-        const int k = (int)(e / ((size_t)P * R * 2));
-        T v = 0;
-        if (ip >= kGhostX - 1 && ip <= kGhostX + nx) {
-            const int i = (ip - kGhostX + nx) % nx;
-            const int j = (jp - 1 + ny) % ny;
-            const size_t s = ((size_t)k * ny + j) * nx + i;
-            v = (T)(f == 0 ? Tsrc[s] : qsrc[s]);
-        }
-        dst[e] = v;
-    }
-}
-
-template <typename T>
-__global__ void unpack_kernel(const T *__restrict__ src, double *__restrict__ Tdst, double *__restrict__ qdst,
-                              int nx, int ny, int nz, int P, int R) {
-    const size_t n = (size_t)nx * ny * nz;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e % nx);
-        const int j = (int)((e / nx) % ny);
-        const int k = (int)(e / ((size_t)nx * ny));
-        const size_t base = ((size_t)(2 * k) * R + j + 1) * P + i + kGhostX;
-        if (Tdst) Tdst[e] = (double)src[base];
-        if (qdst) qdst[e] = (double)src[base + (size_t)R * P];
-    }
-}
-
-template <typename T> __global__ void convert_kernel(const double *__restrict__ s, T *__restrict__ d, size_t n) {
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
-        d[e] = (T)s[e];
-}
-
 // Column physics only, one thread per column, columns [ncol][nz]: the
 // forward Thomas sweep of the implicit vertical diffusion and the
 // optical-depth scan from the top (same definitions as the step).
@@ -896,37 +856,6 @@ int launch_tables(wx_ctx *c, cudaStream_t s) {
         tables_kernel<double><<<1, 32, 0, s>>>(c->d_lev, c->nz, c->dt, c->kappa_h, c->S0, c->q_ref,
                                                (Q4<double> *)c->tab);
     WX_CK(cudaGetLastError(), "tables kernel");
-    return WX_OK;
-}
-
-int launch_pack(wx_ctx *c, const double *T, const double *q, void *dst, cudaStream_t s) {
-    const size_t n = 2 * c->field_cells;
-    if (c->t_bytes == 4)
-        pack_kernel<float><<<grid_for(n), 256, 0, s>>>(T, q, (float *)dst, c->nx, c->ny, c->nz, c->P, c->R);
-    else
-        pack_kernel<double><<<grid_for(n), 256, 0, s>>>(T, q, (double *)dst, c->nx, c->ny, c->nz, c->P, c->R);
-    WX_CK(cudaGetLastError(), "pack kernel");
-    return WX_OK;
-}
-
-int launch_unpack(wx_ctx *c, const void *src, double *T, double *q, cudaStream_t s) {
-    const size_t n = (size_t)c->nx * c->ny * c->nz;
-    if (c->t_bytes == 4)
-        unpack_kernel<float><<<grid_for(n), 256, 0, s>>>((const float *)src, T, q, c->nx, c->ny, c->nz, c->P,
-                                                         c->R);
-    else
-        unpack_kernel<double><<<grid_for(n), 256, 0, s>>>((const double *)src, T, q, c->nx, c->ny, c->nz, c->P,
-                                                          c->R);
-    WX_CK(cudaGetLastError(), "unpack kernel");
-    return WX_OK;
-}
-
-int launch_convert(wx_ctx *c, const double *src, void *dst, size_t n, cudaStream_t s) {
-    if (c->t_bytes == 4)
-        convert_kernel<float><<<grid_for(n), 256, 0, s>>>(src, (float *)dst, n);
-    else
-        convert_kernel<double><<<grid_for(n), 256, 0, s>>>(src, (double *)dst, n);
-    WX_CK(cudaGetLastError(), "convert kernel");
     return WX_OK;
 }
 

@@ -51,6 +51,8 @@ SIGNATURES = [
     ("wx_sync", ctypes.c_int, [_VP]),
     ("wx_read_fields", ctypes.c_int, [_VP, _VP, _VP]),
     ("wx_read_fields_device", ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    ("wx_load_state_f32", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int]),
+    ("wx_read_state_f32", ctypes.c_int, [_VP, _VP, _VP]),
     ("wx_get_sums", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("wx_physics_columns", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_long, _VP]),
     ("wx_info", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -196,10 +198,27 @@ class Context:
         _check(lib().wx_load_fields(self.ptr, _dptr(T), _dptr(q), _dptr(U), _dptr(V), int(dev)),
                self.ptr)
 
-    def read_fields(self):
+    def read_fields(self, T=None, q=None):
+        """FP64 host copies of T and q (into the given arrays, if any)."""
         n = (self.nz, self.ny, self.nx)
-        T, q = np.empty(n), np.empty(n)
+        T = np.empty(n) if T is None else T
+        q = np.empty(n) if q is None else q
         _check(lib().wx_read_fields(self.ptr, _dptr(T), _dptr(q)), self.ptr)
+        return T, q
+
+    def load_state_f32(self, T, q):
+        """T and q alone, FP32 (numpy host or torch CUDA); winds kept."""
+        dev = hasattr(T, "data_ptr")
+        if not dev:
+            T, q = (np.ascontiguousarray(a, np.float32) for a in (T, q))
+        _check(lib().wx_load_state_f32(self.ptr, _dptr(T), _dptr(q), int(dev)), self.ptr)
+
+    def read_state_f32(self, T=None, q=None):
+        """FP32 host copies of T and q (into the given arrays, if any)."""
+        n = (self.nz, self.ny, self.nx)
+        T = np.empty(n, np.float32) if T is None else T
+        q = np.empty(n, np.float32) if q is None else q
+        _check(lib().wx_read_state_f32(self.ptr, _dptr(T), _dptr(q)), self.ptr)
         return T, q
 
     def read_fields_into(self, T, q, stream=None):
