@@ -235,6 +235,26 @@ def test_radiation_beam_from_top():
     assert np.max(np.abs(H - expect)) < 1e-15
 
 
+def test_p8_scan_matches_brute_force_sums():
+    """Every level's optical depth from the top, summed afresh over the
+    levels above it (O(nz^2)), gives the oracle's heating profile."""
+    rng = np.random.default_rng(8)
+    for nz in (1, 2, 17, 58):
+        dz = 1.05 ** np.arange(nz)
+        alpha = 0.01 * np.exp(-np.arange(nz) / 8.0)
+        qs = rng.uniform(0.0, 0.02, nz)
+        S0, qref = 1.0, 0.01
+        dtau = [alpha[k] * dz[k] * qs[k] / qref for k in range(nz)]
+        H = np.empty(nz)
+        for k in range(nz):
+            top = 0.0
+            for kk in range(k + 1, nz):
+                top += dtau[kk]
+            H[k] = S0 * (math.exp(-top) - math.exp(-(top + dtau[k]))) / dz[k]
+        got = oracle.radiation(qs, alpha, dz, S0, qref)
+        assert np.max(np.abs(got - H)) <= 1e-15 * max(1.0, np.max(np.abs(H)))
+
+
 def test_p10_optically_thin_limit():
     """As q -> 0 the heating tends to S0 dtau_k/dz_k = S0 alpha_k q_k/q_ref."""
     nz = 20
