@@ -310,7 +310,8 @@ def variant_plain(dtype, steps, nx=1581, ny=1301, nz=58):
         out["flagged_fp64_columns"] = ctx.flagged_columns()
         out["sums_recorded"] = len(ctx.sums()[0])
     if dtype == "f64":
-        out["bound"] = "fp64 alu (one FP64 divide and exp2 per T cell; GB300 FP64 rate)"
+        out["bound"] = ("fp64 pipe (one exp2 and about 25 explicit FP64 operations per cell, "
+                        "reciprocals from the level tables; GB300 FP64 rate)")
     ctx.close()
     return out
 
