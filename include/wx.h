@@ -126,7 +126,8 @@ int wx_sync(wx_ctx *c);
  * half the bytes of wx_load_fields / wx_read_fields and no rounding.  The
  * winds must have been loaded by wx_load_fields (WX_ESTATE otherwise); they
  * are kept.  Loading resets the sums record like wx_load_fields.  Host
- * (src_is_device = 0) or device input; host output; synchronous. */
+ * (src_is_device = 0) or device input; host output (either of T, q may be
+ * NULL on read); synchronous. */
 int wx_load_state_f32(wx_ctx *c, const float *T, const float *q, int src_is_device);
 int wx_read_state_f32(wx_ctx *c, float *T, float *q);
 
