@@ -198,6 +198,9 @@ int launch_columns(wx_ctx *c, const void *Ts, const void *qs, const void *km, vo
                    long ncol, cudaStream_t s);
 StepCfg default_cfg(const wx_ctx *c);
 int setup_mixed(wx_ctx *c, const double *km64);
+// The side solve of the listed columns after a step into fld[dst] (WX_MIXED,
+// or WX_F32 with kappa_mult); with sums, their energy corrections.
+int launch_mixed_fixup(wx_ctx *c, int dst, bool sums, cudaStream_t s);
 bool cfg_fits(const wx_ctx *c, const StepCfg &cfg, int *smem_bytes);
 int encode_tmap(wx_ctx *c, int which, int ty, int kb);
 int apply_cfg(wx_ctx *c, const StepCfg &g);
