@@ -24,6 +24,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "wx_oracle.c")
 _LIB = os.path.join(_HERE, "libwxoracle.so")
+# A test may point the wrapper at another build of the oracle (a copy with a
+# planted mistake, to check that the pins catch it); it is loaded as is.
+_LIB_OVERRIDE = os.environ.get("WX_ORACLE_LIB")
 _lib = None
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -40,27 +43,30 @@ class _Params(ctypes.Structure):
     ]
 
 
-def build(openmp: bool = True) -> str:
-    """Compile the oracle into ``oracle/libwxoracle.so``."""
+def build(openmp: bool = True, src: str = _SRC, out: str = _LIB) -> str:
+    """Compile the oracle (``src``, default wx_oracle.c) into ``out``
+    (default ``oracle/libwxoracle.so``); returns the library's path."""
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared", _SRC, "-o", _LIB, "-lm"]
+           "-fPIC", "-shared", src, "-o", out, "-lm"]
     if openmp:
         cmd.insert(1, "-fopenmp")
     try:
         subprocess.run(cmd, check=True, capture_output=True, text=True)
     except subprocess.CalledProcessError as e:
         if openmp:  # toolchains without libgomp still get a serial oracle
-            return build(openmp=False)
+            return build(openmp=False, src=src, out=out)
         raise RuntimeError("oracle build failed:\n" + e.stderr) from e
-    return _LIB
+    return out
 
 
 def lib():
     global _lib
     if _lib is None:
-        if not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        path = _LIB_OVERRIDE or _LIB
+        if not _LIB_OVERRIDE and (not os.path.exists(_LIB) or
+                                  os.path.getmtime(_LIB) < os.path.getmtime(_SRC)):
             build()
-        L = ctypes.CDLL(_LIB)
+        L = ctypes.CDLL(path)
         P = ctypes.POINTER(_Params)
         L.wxo_dynamics.argtypes = [P, _D, _D, _D, _D, _D, _D]
         L.wxo_vdiff_coeffs.argtypes = [ctypes.c_int, ctypes.c_double, _D, _D,

@@ -89,6 +89,24 @@ def test_ghost_ring_is_state_with_its_own_rule():
     np.testing.assert_allclose(out, want, rtol=0, atol=1e-15)
 
 
+def test_ghost_row_rule():
+    """A unit value in the far ghost row j = ny+1 (i interior): it keeps
+    1 - 2d, the near ghost row j = 0 (which reads rows 1 and ny+1) and the
+    interior row j = ny (whose north neighbour it is) each read it with
+    weight d; nothing else sees it."""
+    d = 0.1
+    p = oracle.pf_params(NX, NY, NZ, d=d, radiation=0.0, transfer=0.0)
+    E = zeros()
+    k, i = 3, 4
+    E[k, NY + 1, i] = 1.0
+    out = oracle.pf_step(p, E)
+    want = zeros()
+    want[k, NY + 1, i] = 1 - 2 * d
+    want[k, 0, i] = d
+    want[k, NY, i] = d
+    np.testing.assert_allclose(out, want, rtol=0, atol=1e-15)
+
+
 def test_interior_edge_feeds_only_its_own_ghost_column():
     """A unit value at i = 1: the ghost column i = 0 reads it (d), the far
     ghost column i = nx+1 does not (it reads i = nx and i = 0)."""
