@@ -1,8 +1,9 @@
 """The pins catch plausible mistakes in the oracle.  Each case plants one
 mistake in a copy of the C oracle (a dropped term, a wrong sign, index,
-coefficient or time level), builds it beside the test, and runs the pin
-files against it in a child process: at least one pin must fail.  The
-unmodified source, built the same way, must pass them all."""
+coefficient or time level) or of the MLP oracle, builds or loads it beside
+the test, and runs the pin files against it in a child process: at least
+one pin must fail.  The unmodified sources, handled the same way, must pass
+them all."""
 import os
 import shutil
 import subprocess
@@ -83,3 +84,66 @@ def test_planted_mistake_fails_a_pin(name, tmp_path):
     assert source.count(good) == 1, "the planted text must name one place in the oracle"
     r = _run_pins(tmp_path, source.replace(good, bad))
     assert r.returncode == 1, f"no pin caught '{name}':\n" + r.stdout[-3000:]
+
+
+# --------------------------------------------------------------- MLP oracle
+MLP_MUTANTS = {
+    "bf16 rounds ties away from zero": ("r = ((u + 0x7FFF + lsb) & 0xFFFF0000)", "r = ((u + 0x8000) & 0xFFFF0000)"),
+    "input expansion without its low term": ("return hi, bf16(f - hi)", "return hi, 0.0 * hi"),
+    "GELU argument not scaled by 1/sqrt(2)": ("return 0.5 * z * (1.0 + erf(z * SQRT_HALF))",
+                                             "return 0.5 * z * (1.0 + erf(z))"),
+    "GELU derivative without z phi(z)": (
+        "return 0.5 * (1.0 + erf(z * SQRT_HALF)) + z * INV_SQRT_2PI * np.exp(-0.5 * z * z)",
+        "return 0.5 * (1.0 + erf(z * SQRT_HALF))"),
+    "forward without biases": ("z = h @ rnd(Ws[l]).T + np.asarray(bs[l], dtype=np.float64)",
+                               "z = h @ rnd(Ws[l]).T"),
+    "MSE gradient without its factor 2": ("return 2.0 * (Y - Yt) / Y.size", "return (Y - Yt) / Y.size"),
+    "bias gradient averaged over the batch": ("db[l] = g.sum(axis=0)", "db[l] = g.mean(axis=0)"),
+    "Adam without bias correction of m": ("mhat = m / (1.0 - b1 ** t)", "mhat = m"),
+    "cosine schedule without its offset": ("return 0.5 * lr0 * (1.0 + np.cos(np.pi * min(step, total) / total))",
+                                           "return lr0 * np.cos(np.pi * min(step, total) / total)"),
+    "features ignore kappa_mult": ("kv = km[:, None] * np.asarray(kappa_lev, dtype=np.float64)[None, :]",
+                                   "kv = np.ones_like(km)[:, None] * np.asarray(kappa_lev, dtype=np.float64)[None, :]"),
+    "normalisation std without the mean": ("sd = np.sqrt(np.maximum((F * F).mean(axis=0) - mean * mean, 0.0))",
+                                           "sd = np.sqrt(np.maximum((F * F).mean(axis=0), 0.0))"),
+    "rho_vd relative to |A T*| instead of |A T* - T*|": ("den = np.linalg.norm(AT - Ts[c])",
+                                                          "den = np.linalg.norm(AT)"),
+    "rho_H from the thickest layer's optical depth only": ("absorbed = S0 * (1.0 - np.exp(-tau.sum(axis=1)))",
+                                                           "absorbed = S0 * (1.0 - np.exp(-tau.max(axis=1)))"),
+}
+
+_MLP_RUNNER = """
+import importlib.util, sys
+import oracle, pytest
+spec = importlib.util.spec_from_file_location("oracle.mlp", sys.argv[1])
+mod = importlib.util.module_from_spec(spec)
+sys.modules["oracle.mlp"] = mod
+spec.loader.exec_module(mod)
+oracle.mlp = mod
+sys.exit(pytest.main(["-x", "-q", "-p", "no:cacheprovider", "tests/test_mlp_oracle_pins.py"]))
+"""
+
+
+def _run_mlp_pins(tmp_path, source):
+    path = tmp_path / "mlp.py"
+    path.write_text(source)
+    return subprocess.run([sys.executable, "-c", _MLP_RUNNER, str(path)], cwd=ROOT, capture_output=True,
+                          text=True, timeout=600)
+
+
+def _mlp_source():
+    return open(os.path.join(os.path.dirname(oracle._SRC), "mlp.py")).read()
+
+
+def test_unmodified_mlp_copy_passes_every_pin(tmp_path):
+    r = _run_mlp_pins(tmp_path, _mlp_source())
+    assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
+
+
+@pytest.mark.parametrize("name", sorted(MLP_MUTANTS))
+def test_planted_mlp_mistake_fails_a_pin(name, tmp_path):
+    good, bad = MLP_MUTANTS[name]
+    source = _mlp_source()
+    assert source.count(good) == 1, "the planted text must name one place in the oracle"
+    r = _run_mlp_pins(tmp_path, source.replace(good, bad))
+    assert r.returncode == 1, f"no pin caught '{name}':\n" + r.stdout[-3000:] + r.stderr[-2000:]
