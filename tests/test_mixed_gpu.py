@@ -139,3 +139,34 @@ def test_fp32_with_kappa_mult_matches_oracle(shape):
         assert maxrel(Tg, To) <= 3e-5 and maxrel(qg, qo) <= 1e-5
         T, q = Tg, qg
     ctx.close()
+
+
+def test_c3_full_size_sampled():
+    """The mixed-precision workload at its full size (1581x1301x58,
+    near-singular columns seeded, FP64 sums on), one step in the bench's
+    launch configuration: 3000 sampled columns plus 1000 flagged ones and
+    the corners against the oracle's per-column step (FP32 per-step bound),
+    and the recorded sums against the FP64 sums of the GPU state."""
+    case = inputs.round_to_f32(inputs.paper_grid_case(near_singular=True))
+    ctx = wx.Context(case.nx, case.ny, case.nz, "mixed")
+    ctx.set_params(case, flags=wx.WX_ADVECTION | wx.WX_PHYSICS | wx.WX_SUMS)
+    ctx.load_fields(case.T, case.q, case.U, case.V)
+    assert ctx.flagged_columns() > 0
+    ctx.step(1)
+    ctx.sync()
+    Tg, qg = ctx.read_fields()
+    m, e = ctx.sums()
+    ctx.close()
+    rng = np.random.default_rng(1)
+    flagged = np.flatnonzero(case.kappa_mult.reshape(-1) != 1.0)
+    pick = rng.choice(flagged, 1000, replace=False)
+    ci = np.concatenate([rng.integers(0, case.nx, 3000), pick % case.nx, [0, case.nx - 1, 0, case.nx - 1]])
+    cj = np.concatenate([rng.integers(0, case.ny, 3000), pick // case.nx, [0, 0, case.ny - 1, case.ny - 1]])
+    To, qo = oracle.step_columns(case, case.T, case.q, case.U, case.V, ci, cj)
+    Tgs, qgs = Tg[:, cj, ci].T, qg[:, cj, ci].T
+    assert np.max(np.abs(Tgs - To)) / np.max(np.abs(case.T)) <= 1e-5
+    assert np.max(np.abs(qgs - qo)) / np.max(np.abs(case.q)) <= 1e-5
+    w = case.h ** 2 * case.dz[:, None, None]
+    assert len(m) == 1
+    assert abs(e[-1] - np.sum(Tg * w)) / abs(e[-1]) < 1e-12
+    assert abs(m[-1] - np.sum(qg * w)) / abs(m[-1]) < 1e-12

@@ -108,3 +108,16 @@ def test_rk3_differs_from_euler_and_configuration_errors():
         ens.step(1)
     assert ei.value.code == -8
     ens.close()
+
+
+def test_paper_grid_full_size_fp32():
+    """1581x1301x58, FP32, one RK3 step in the bench's launch configuration
+    against the FP64 oracle's whole-grid RK3 step (FP32 per-step bound)."""
+    case = inputs.round_to_f32(inputs.paper_grid_case())
+    ctx = ctx_for(case, "f32")
+    ctx.step(1)
+    ctx.sync()
+    Tg, qg = ctx.read_fields()
+    ctx.close()
+    To, qo = oracle.step_rk3(case, case.T, case.q, case.U, case.V)
+    assert relmax(Tg, To) <= 1e-5 and relmax(qg, qo) <= 1e-5
