@@ -137,3 +137,28 @@ def test_autotuner_picks_a_config_restores_state_and_caches(tmp_path):
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
     ctx.close()
     ctx2.close()
+
+
+def test_c4_full_size_sampled():
+    """The 16-member ensemble at its full sizes (256x256x40 ... 1024x768x58),
+    autotuned and replayed from a graph as the bench runs it, one step:
+    every member at 400 sampled columns plus its corners against the
+    oracle's per-column step (FP32 per-step bound)."""
+    sizes = inputs.ensemble_sizes()
+    cases = [inputs.round_to_f32(inputs.ensemble_member(m, *s)) for m, s in enumerate(sizes)]
+    ens = wx.Ensemble(sizes, "f32")
+    for mem, c in zip(ens.members, cases):
+        mem.set_params(c)
+        mem.load_fields(c.T, c.q, c.U, c.V)
+    ens.tune()
+    ens.step(1, graph=True)
+    ens.sync()
+    rng = np.random.default_rng(2)
+    for mem, c in zip(ens.members, cases):
+        Tg, qg = mem.read_fields()
+        ci = np.concatenate([rng.integers(0, c.nx, 400), [0, c.nx - 1, 0, c.nx - 1]])
+        cj = np.concatenate([rng.integers(0, c.ny, 400), [0, 0, c.ny - 1, c.ny - 1]])
+        To, qo = oracle.step_columns(c, c.T, c.q, c.U, c.V, ci, cj)
+        assert np.max(np.abs(Tg[:, cj, ci].T - To)) / np.max(np.abs(c.T)) <= 1e-5
+        assert np.max(np.abs(qg[:, cj, ci].T - qo)) / np.max(np.abs(c.q)) <= 1e-5
+    ens.close()
