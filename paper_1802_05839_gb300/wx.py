@@ -145,6 +145,58 @@ def _dptr(a):
     return ctypes.c_void_p(a.ctypes.data)
 
 
+# Pointers cross the ABI without their sizes or types, so the binding checks
+# every array it passes: a wrong dtype or a short buffer would otherwise be
+# read or written out of bounds by the library.
+def _is_cuda(a):
+    return bool(getattr(a, "is_cuda", False))
+
+
+def _host(a, dtype, n, what):
+    """Host input: a C-contiguous numpy copy/view of `dtype` with n elements
+    (a CPU torch tensor is taken by value)."""
+    if _is_cuda(a):
+        raise TypeError(f"{what}: expected a host array, got a CUDA tensor")
+    if hasattr(a, "detach"):
+        a = a.detach().numpy()
+    a = np.ascontiguousarray(a, dtype)
+    if a.size != n:
+        raise ValueError(f"{what}: {a.size} elements, expected {n}")
+    return a
+
+
+def _out(a, dtype, n, what):
+    """Host output written in place: a writable C-contiguous numpy array of
+    `dtype` with n elements."""
+    if not (isinstance(a, np.ndarray) and a.dtype == np.dtype(dtype) and a.flags.c_contiguous
+            and a.flags.writeable):
+        raise TypeError(f"{what}: expected a writable C-contiguous numpy {np.dtype(dtype).name} array")
+    if a.size != n:
+        raise ValueError(f"{what}: {a.size} elements, expected {n}")
+    return a
+
+
+def _dev(t, dtype, min_numel, what, optional=False, exact=False):
+    """A CUDA tensor whose pointer crosses the ABI: dtype (a torch dtype name
+    such as "float32"), contiguity and at least (exact: exactly) min_numel
+    elements."""
+    if t is None:
+        if optional:
+            return None
+        raise TypeError(f"{what}: a CUDA tensor is required")
+    if not hasattr(t, "data_ptr"):
+        raise TypeError(f"{what}: expected a torch CUDA tensor, got {type(t).__name__}")
+    if str(t.dtype) != "torch." + dtype:
+        raise TypeError(f"{what}: dtype {t.dtype}, expected torch.{dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: not contiguous")
+    if t.numel() < min_numel or (exact and t.numel() != min_numel):
+        raise ValueError(f"{what}: {t.numel()} elements, need {'' if exact else 'at least '}{min_numel}")
+    if not _is_cuda(t):
+        raise TypeError(f"{what}: expected a CUDA tensor, got a {t.device} tensor")
+    return t
+
+
 def _stream_ptr(stream):
     if stream is None:
         return None
@@ -190,39 +242,54 @@ class Context:
         _check(lib().wx_set_params(self.ptr, ctypes.byref(p)), self.ptr)
 
     # -- state ---------------------------------------------------------
+    def _n3(self):
+        return self.nx * self.ny * self.nz
+
     def load_fields(self, T, q, U, V):
-        """numpy FP64 (host) or torch FP64 CUDA tensors (device)."""
-        dev = hasattr(T, "data_ptr")
-        if not dev:
-            T, q, U, V = (np.ascontiguousarray(a, np.float64) for a in (T, q, U, V))
+        """numpy FP64 (host) or torch FP64 CUDA tensors (device): T, q
+        [nz][ny][nx], U, V [ny][nx]."""
+        n3, n2 = self._n3(), self.nx * self.ny
+        dev = _is_cuda(T)
+        if dev:
+            T, q = _dev(T, "float64", n3, "T", exact=True), _dev(q, "float64", n3, "q", exact=True)
+            U, V = _dev(U, "float64", n2, "U", exact=True), _dev(V, "float64", n2, "V", exact=True)
+        else:
+            T, q = _host(T, np.float64, n3, "T"), _host(q, np.float64, n3, "q")
+            U, V = _host(U, np.float64, n2, "U"), _host(V, np.float64, n2, "V")
         _check(lib().wx_load_fields(self.ptr, _dptr(T), _dptr(q), _dptr(U), _dptr(V), int(dev)),
                self.ptr)
 
     def read_fields(self, T=None, q=None):
         """FP64 host copies of T and q (into the given arrays, if any)."""
         n = (self.nz, self.ny, self.nx)
-        T = np.empty(n) if T is None else T
-        q = np.empty(n) if q is None else q
+        T = np.empty(n) if T is None else _out(T, np.float64, self._n3(), "T")
+        q = np.empty(n) if q is None else _out(q, np.float64, self._n3(), "q")
         _check(lib().wx_read_fields(self.ptr, _dptr(T), _dptr(q)), self.ptr)
         return T, q
 
     def load_state_f32(self, T, q):
         """T and q alone, FP32 (numpy host or torch CUDA); winds kept."""
-        dev = hasattr(T, "data_ptr")
-        if not dev:
-            T, q = (np.ascontiguousarray(a, np.float32) for a in (T, q))
+        n3 = self._n3()
+        dev = _is_cuda(T)
+        if dev:
+            T, q = _dev(T, "float32", n3, "T", exact=True), _dev(q, "float32", n3, "q", exact=True)
+        else:
+            T, q = _host(T, np.float32, n3, "T"), _host(q, np.float32, n3, "q")
         _check(lib().wx_load_state_f32(self.ptr, _dptr(T), _dptr(q), int(dev)), self.ptr)
 
     def read_state_f32(self, T=None, q=None):
         """FP32 host copies of T and q (into the given arrays, if any)."""
         n = (self.nz, self.ny, self.nx)
-        T = np.empty(n, np.float32) if T is None else T
-        q = np.empty(n, np.float32) if q is None else q
+        T = np.empty(n, np.float32) if T is None else _out(T, np.float32, self._n3(), "T")
+        q = np.empty(n, np.float32) if q is None else _out(q, np.float32, self._n3(), "q")
         _check(lib().wx_read_state_f32(self.ptr, _dptr(T), _dptr(q)), self.ptr)
         return T, q
 
     def read_fields_into(self, T, q, stream=None):
-        """Device FP64 outputs (torch tensors), asynchronous on `stream`."""
+        """Device FP64 outputs (torch tensors, either may be None), asynchronous
+        on `stream`."""
+        T = _dev(T, "float64", self._n3(), "T", optional=True)
+        q = _dev(q, "float64", self._n3(), "q", optional=True)
         _check(lib().wx_read_fields_device(self.ptr, _dptr(T), _dptr(q), _stream_ptr(stream)),
                self.ptr)
 
@@ -239,8 +306,18 @@ class Context:
         return m[:n.value], e[:n.value]
 
     def physics_columns(self, Ts, qs, kappa_mult, Tout, tend=None, stream=None):
-        """Device arrays (torch tensors) of the context's storage type."""
-        ncol = Ts.shape[0]
+        """Device arrays (torch tensors) of the context's storage type: Ts, qs
+        [ncol][nz] in, kappa_mult [ncol] or None, Tout [ncol][nz] out, tend
+        [ncol][2][nz] out or None."""
+        st = "float64" if self.dtype == "f64" else "float32"
+        ncol = int(Ts.shape[0]) if hasattr(Ts, "shape") else 0
+        n = ncol * self.nz
+        Ts, qs = _dev(Ts, st, n, "Ts"), _dev(qs, st, n, "qs")
+        if Ts.numel() != n or qs.numel() != n:
+            raise ValueError(f"Ts, qs: expected [{ncol}][{self.nz}]")
+        kappa_mult = _dev(kappa_mult, st, ncol, "kappa_mult", optional=True, exact=True)
+        Tout = _dev(Tout, st, n, "Tout")
+        tend = _dev(tend, st, 2 * n, "tend", optional=True)
         _check(lib().wx_physics_columns(self.ptr, _dptr(Ts), _dptr(qs), _dptr(kappa_mult),
                                         _dptr(Tout), _dptr(tend), ncol, _stream_ptr(stream)),
                self.ptr)
@@ -359,6 +436,9 @@ def wx_sums_noalloc(T, q, dz, h, out, stream=None):
     import torch
     nz, ny, nx = T.shape
     dtype = WX_F32 if T.dtype == torch.float32 else WX_F64
+    name = "float32" if dtype == WX_F32 else "float64"
+    T, q = _dev(T, name, nx * ny * nz, "T", exact=True), _dev(q, name, nx * ny * nz, "q", exact=True)
+    dz, out = _dev(dz, "float64", nz, "dz", exact=True), _dev(out, "float64", 2, "out")
     code = lib().wx_sums_noalloc(_dptr(T), _dptr(q), dtype, nx, ny, nz, _dptr(dz), float(h),
                                  _dptr(out), _stream_ptr(stream))
     if code != 0:
@@ -374,11 +454,19 @@ def wx_gemm_bf16(A, B, epilogue=0, bias=None, aux=None, out=None, out2=None, sta
     """C = A . B^T (torch BF16 CUDA tensors A [M][K], B [N][K]) with an epilogue."""
     import torch
     M, K = A.shape
-    N = B.shape[0]
+    N, KB = B.shape
+    if KB != K:
+        raise ValueError(f"A is [{M}][{K}] but B is [{N}][{KB}]")
+    A, B = _dev(A, "bfloat16", M * K, "A", exact=True), _dev(B, "bfloat16", N * K, "B", exact=True)
     if out is None:
         out = torch.empty(M, N, device=A.device, dtype=torch.float32 if epilogue == 0 else torch.bfloat16)
     if status is None:
         status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    out = _dev(out, "float32" if epilogue == 0 else "bfloat16", M * N, "out")
+    out2 = _dev(out2, "bfloat16", M * N, "out2", optional=True)
+    bias = _dev(bias, "float32", N, "bias", optional=True)
+    aux = _dev(aux, "bfloat16", M * N, "aux", optional=epilogue != 2)
+    status = _dev(status, "int32", 1, "status")
     _mcheck(lib().wx_gemm_bf16(_dptr(A), _dptr(B), M, N, K, epilogue, _dptr(bias), _dptr(aux), _dptr(out),
                                _dptr(out2), _dptr(status), _stream_ptr(stream)))
     return out
@@ -389,6 +477,7 @@ def wx_gemm_bf16(A, B, epilogue=0, bias=None, aux=None, out=None, out2=None, sta
 MLP_SHAPES = [(512, 232), (512, 512), (512, 512), (116, 512)]  # (fan_out, fan_in)
 MLP_IN, MLP_IN_PAD, MLP_OUT, MLP_OUT_PAD = 232, 256, 116, 128
 MLP_X_WIDTH = 2 * MLP_IN_PAD  # [hi | lo] two-term BF16 input rows
+MLP_NZ = 58                    # levels of the columns the network serves
 
 
 def _f32arrays(arrs):
@@ -445,22 +534,53 @@ class MLP:
         a, _ = _f32arrays([kappa_lev, alpha_dz])
         _mcheck(lib().wx_mlp_set_levels(self.ptr, len(a[0]), _dptr(a[0]), _dptr(a[1])))
 
+    @staticmethod
+    def _columns(Ts, qs, kappa_mult, tend, tend_optional):
+        ncol = int(Ts.shape[0]) if hasattr(Ts, "shape") else 0
+        n = ncol * MLP_NZ
+        Ts, qs = _dev(Ts, "float32", n, "Ts"), _dev(qs, "float32", n, "qs")
+        if Ts.numel() != n or qs.numel() != n:
+            raise ValueError(f"Ts, qs: expected [{ncol}][{MLP_NZ}]")
+        kappa_mult = _dev(kappa_mult, "float32", ncol, "kappa_mult", optional=True, exact=True)
+        tend = _dev(tend, "float32", 2 * n, "tend", optional=tend_optional)
+        return ncol, Ts, qs, kappa_mult, tend
+
+    def _rows(self, X, what="X"):
+        M = int(X.shape[0]) if hasattr(X, "shape") else 0
+        X = _dev(X, "bfloat16", M * MLP_X_WIDTH, what)
+        if X.numel() != M * MLP_X_WIDTH:
+            raise ValueError(f"{what}: expected [M][{MLP_X_WIDTH}]")
+        return M, X
+
     def fit_norm(self, Ts, qs, kappa_mult, tend, stream=None):
+        _, Ts, qs, kappa_mult, tend = self._columns(Ts, qs, kappa_mult, tend, False)
         _mcheck(lib().wx_mlp_fit_norm(self.ptr, _dptr(Ts), _dptr(qs), _dptr(kappa_mult), _dptr(tend),
                                       Ts.shape[0], _stream_ptr(stream)))
 
     def prepare(self, Ts, qs, kappa_mult, tend, X, Yt=None, stream=None):
+        ncol, Ts, qs, kappa_mult, tend = self._columns(Ts, qs, kappa_mult, tend, Yt is None)
+        rows = (ncol + 127) // 128 * 128
+        X = _dev(X, "bfloat16", rows * MLP_X_WIDTH, "X")
+        Yt = _dev(Yt, "float32", rows * MLP_OUT_PAD, "Yt", optional=True)
         _mcheck(lib().wx_mlp_prepare(self.ptr, _dptr(Ts), _dptr(qs), _dptr(kappa_mult), _dptr(tend),
                                      Ts.shape[0], _dptr(X), _dptr(Yt), _stream_ptr(stream)))
 
     def forward(self, X, Y, stream=None):
+        M, X = self._rows(X)
+        Y = _dev(Y, "float32", M * MLP_OUT_PAD, "Y")
         _mcheck(lib().wx_mlp_forward(self.ptr, _dptr(X), X.shape[0], _dptr(Y), _stream_ptr(stream)))
 
     def gradients(self, X, Yt, loss=None, stream=None):
+        M, X = self._rows(X)
+        Yt = _dev(Yt, "float32", M * MLP_OUT_PAD, "Yt")
+        loss = _dev(loss, "float32", 1, "loss", optional=True)
         _mcheck(lib().wx_mlp_gradients(self.ptr, _dptr(X), _dptr(Yt), X.shape[0], _dptr(loss),
                                        _stream_ptr(stream)))
 
     def train_step(self, X, Yt, lr, loss=None, stream=None):
+        M, X = self._rows(X)
+        Yt = _dev(Yt, "float32", M * MLP_OUT_PAD, "Yt")
+        loss = _dev(loss, "float32", 1, "loss", optional=True)
         _mcheck(lib().wx_mlp_train_step(self.ptr, _dptr(X), _dptr(Yt), X.shape[0], float(lr),
                                         _dptr(loss), _stream_ptr(stream)))
 
@@ -498,9 +618,10 @@ class ReducedApp:
         self._check(lib().wx_pf_set_launch(self.ptr, {"ijk": 0, "kij": 1}[layout], int(block[0]), int(block[1])))
 
     def load(self, E):
-        dev = hasattr(E, "data_ptr")
-        if not dev:
-            E = np.ascontiguousarray(E, np.float64)
+        """The whole state [nz][ny+2][nx+2], FP64, host or CUDA tensor."""
+        n = self.nz * (self.ny + 2) * (self.nx + 2)
+        dev = _is_cuda(E)
+        E = _dev(E, "float64", n, "E", exact=True) if dev else _host(E, np.float64, n, "E")
         self._keep = E
         self._check(lib().wx_pf_load(self.ptr, _dptr(E), int(dev)))
 

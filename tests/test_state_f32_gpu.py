@@ -119,3 +119,35 @@ def test_pinned_host_arrays_give_the_same_state_as_pageable_ones(dtype):
         ctx.close()
     for x, y in zip(*res):
         assert np.array_equal(x, y)
+
+
+def test_binding_refuses_mistyped_or_short_arrays():
+    """Wrong dtypes, short buffers and host/device mixes are refused by the
+    binding before any pointer reaches the library; the context stays usable."""
+    case = inputs.small_case(nx=16, ny=8, nz=4, seed=3)
+    ctx = wx.Context(16, 8, 4, "f32")
+    ctx.set_params(case)
+    n = 16 * 8 * 4
+    d32 = torch.zeros(n, dtype=torch.float32, device="cuda")
+    d64 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    U = torch.from_numpy(np.ascontiguousarray(case.U)).cuda()
+    with pytest.raises(TypeError):
+        ctx.load_fields(d32, d32, U, U)                   # FP32 into the FP64 call
+    with pytest.raises(TypeError):
+        ctx.load_fields(d64, d64, case.U, case.V)         # device fields, host winds
+    with pytest.raises(ValueError):
+        ctx.load_fields(case.T[:, :, :-1], case.q, case.U, case.V)
+    ctx.load_fields(case.T, case.q, case.U, case.V)
+    with pytest.raises(ValueError):
+        ctx.load_state_f32(d32[:-1], d32[:-1])
+    with pytest.raises(TypeError):
+        ctx.read_state_f32(np.empty(n, np.float64), np.empty(n, np.float64))
+    with pytest.raises(ValueError):
+        ctx.read_fields_into(d64[:-1], d64)
+    T, q = ctx.read_state_f32()
+    assert np.array_equal(T, f32(case.T))
+    ctx.close()
+    app = wx.ReducedApp(8, 6, 4, "f64")
+    with pytest.raises(ValueError):
+        app.load(np.zeros((4, 6, 8)))                     # missing the ghost ring
+    app.close()
