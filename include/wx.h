@@ -100,7 +100,10 @@ int wx_create(int nx, int ny, int nz, int dtype, wx_ctx **out);
 /* Copy and validate parameters (positivity of dt, h, q_ref, dz; the
  * explicit update's coefficients must be non-negative, checked against the
  * winds at the next wx_step -> WX_ECFL).  Computes the per-level tables on
- * the device.  May be called again between steps. */
+ * the device.  May be called again between steps.  A WX_F64 context with a
+ * kappa_mult field eliminates per column on the fly and keeps two values
+ * per level of each column in shared memory: at most 174 levels
+ * (WX_EUNSUPPORTED beyond). */
 int wx_set_params(wx_ctx *c, const wx_params *p);
 
 /* Load the state: T, q [nz][ny][nx], face winds U, V [ny][nx] (U on the

@@ -247,6 +247,13 @@ extern "C" int wx_set_params(wx_ctx *c, const wx_params *p) {
     if ((p->flags & WX_SURROGATE) && (c->dtype != WX_F32 || c->nz != 58 || (p->flags & WX_SUMS)))
         return fail(c, WX_EUNSUPPORTED, "wx_set_params: WX_SURROGATE needs WX_F32, nz = 58 and no WX_SUMS");
     const int nz = c->nz;
+    if (p->kappa_mult && c->dtype == WX_F64 && plan_smem(nz, 1, 3, 2, 8, true).total > 227 * 1024) {
+        // per-column elimination keeps F_k and e_k of every column in shared memory
+        int nmax = 1;
+        while (plan_smem(nmax + 1, 1, 3, 2, 8, true).total <= 227 * 1024) ++nmax;
+        return fail(c, WX_EUNSUPPORTED, "wx_set_params: an FP64 context with kappa_mult takes at most " +
+                                            std::to_string(nmax) + " levels");
+    }
     for (int k = 0; k < nz; ++k) {
         if (!finite_pos(p->dz[k])) return fail(c, WX_EINVAL, "wx_set_params: dz must be finite and > 0");
         if (!finite_nonneg(p->kappa_lev[k]) || !finite_nonneg(p->alpha[k]))

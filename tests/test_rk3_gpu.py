@@ -27,7 +27,7 @@ def ctx_for(case, dtype, flags=RK):
 
 @pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 1e-5)])
 @pytest.mark.parametrize("shape,ns", [((37, 29, 8), False), ((33, 5, 3), False), ((1, 7, 5), False),
-                                      ((70, 50, 58), True)])
+                                      ((70, 50, 58), True), ((20, 7, 256), False), ((20, 7, 174), True)])
 def test_every_step_matches_oracle(dtype, tol, shape, ns):
     nx, ny, nz = shape
     case = inputs.paper_grid_case(nx, ny, nz, seed=4, near_singular=ns)

@@ -291,3 +291,33 @@ def test_bounded_wait_gives_up_and_context_survives():
     assert np.max(np.abs(T - To)) / np.max(np.abs(To)) <= 1e-5
     ctx.close()
     assert wx.wx_selftest_wait_timeout(0)[0] == -1
+
+
+@pytest.mark.parametrize("dtype,km", [("f64", False), ("f32", True), ("mixed", True)])
+def test_deepest_columns(dtype, km):
+    """nz = 256, the deepest column wx_create accepts (the launch
+    configuration falls back to short tiles to fit the per-column state),
+    with and without a per-column kappa_mult."""
+    case = inputs.paper_grid_case(40, 9, 256, seed=12, near_singular=km)
+    if dtype != "f64":
+        case = inputs.round_to_f32(case)
+    (Tg, qg), = gpu_run(case, dtype, 3)
+    To, qo = oracle.run(case, 3, case.T, case.q, case.U, case.V)
+    tol = 3 * TOL["f64" if dtype == "f64" else "f32"]
+    assert maxrel(Tg, To) <= tol and maxrel(qg, qo) <= tol
+
+
+def test_fp64_kappa_mult_depth_limit():
+    """FP64 with a per-column kappa_mult eliminates per column on the fly and
+    keeps two values per level of every column in shared memory: 174 levels
+    run (checked against the oracle), 175 are refused at wx_set_params."""
+    case = inputs.paper_grid_case(33, 6, 174, seed=13, near_singular=True)
+    (Tg, qg), = gpu_run(case, "f64", 2)
+    To, qo = oracle.run(case, 2, case.T, case.q, case.U, case.V)
+    assert maxrel(Tg, To) <= 3e-12 and maxrel(qg, qo) <= 3e-12
+    deep = inputs.paper_grid_case(8, 4, 175, seed=13, near_singular=True)
+    ctx = wx.Context(8, 4, 175, "f64")
+    with pytest.raises(wx.WxError) as e:
+        ctx.set_params(deep)
+    assert e.value.code == -8 and "174" in str(e.value)
+    ctx.close()
