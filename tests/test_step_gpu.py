@@ -321,3 +321,46 @@ def test_fp64_kappa_mult_depth_limit():
         ctx.set_params(deep)
     assert e.value.code == -8 and "174" in str(e.value)
     ctx.close()
+
+
+def test_zero_work_is_a_no_op():
+    """Empty requests: zero steps (single grid, ensemble with and without a
+    graph, reduced application) and zero columns leave every state bit for
+    bit and launch nothing; negative step counts are refused."""
+    import torch
+    case = inputs.round_to_f32(inputs.paper_grid_case(40, 24, 10, seed=14))
+    ctx = wx.Context(case.nx, case.ny, case.nz, "f32")
+    ctx.set_params(case)
+    ctx.load_fields(case.T, case.q, case.U, case.V)
+    before = ctx.read_fields()
+    ctx.step(0)
+    ctx.sync()
+    assert ctx.last_launches() == 0
+    after = ctx.read_fields()
+    assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+    e = torch.empty(0, dtype=torch.float32, device="cuda")
+    ctx.physics_columns(e, e, None, e, None)
+    ctx.sync()
+    with pytest.raises(wx.WxError) as err:
+        ctx.step(-1)
+    assert err.value.code == -1
+    ctx.close()
+    ens = wx.Ensemble([(case.nx, case.ny, case.nz)], "f32")
+    m = ens.members[0]
+    m.set_params(case)
+    m.load_fields(case.T, case.q, case.U, case.V)
+    for graph in (False, True):
+        ens.step(0, graph=graph)
+        ens.sync()
+        assert ens.last_launches() == 0
+    out = m.read_fields()
+    assert np.array_equal(out[0], before[0]) and np.array_equal(out[1], before[1])
+    ens.close()
+    app = wx.ReducedApp(9, 7, 4, "f64")
+    app.set_params()
+    E = np.arange(4 * 9 * 11, dtype=np.float64).reshape(4, 9, 11)
+    app.load(E)
+    app.step(0)
+    app.sync()
+    assert app.last_launches() == 0 and np.array_equal(app.read(), E)
+    app.close()
