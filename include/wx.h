@@ -134,6 +134,16 @@ int wx_sync(wx_ctx *c);
 int wx_load_state_f32(wx_ctx *c, const float *T, const float *q, int src_is_device);
 int wx_read_state_f32(wx_ctx *c, float *T, float *q);
 
+/* The same two transfers enqueued on the caller's stream without waiting:
+ * T and q must be pinned host memory (cudaHostAlloc or cudaHostRegister;
+ * WX_EINVAL otherwise) and stay untouched until the stream has passed the
+ * call; results are valid after the stream (or wx_sync) completes.  The
+ * copies go through the context's device staging buffer in stream order.
+ * Contexts on different streams overlap one's download with another's
+ * upload (the host link has a copy engine each way). */
+int wx_load_state_f32_async(wx_ctx *c, const float *T, const float *q, void *cuda_stream);
+int wx_read_state_f32_async(wx_ctx *c, float *T, float *q, void *cuda_stream);
+
 /* Copy the current state to host FP64 arrays T, q [nz][ny][nx] (either may
  * be NULL).  Synchronous; a checkpoint that wx_load_fields restores. */
 int wx_read_fields(wx_ctx *c, double *T, double *q);

@@ -481,6 +481,58 @@ extern "C" int wx_read_state_f32(wx_ctx *c, float *T, float *q) {
     return WX_OK;
 }
 
+// The same on the caller's stream, without waiting: host arrays must be
+// pinned (the copy engines read and write them while the host goes on), and
+// stay untouched until the stream has passed the call.  Two contexts on two
+// streams then overlap one's download with the other's upload.
+static bool pinned_host(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+extern "C" int wx_load_state_f32_async(wx_ctx *c, const float *T, const float *q, void *stream) {
+    if (!c) return WX_EINVAL;
+    if (!T || !q) return fail(c, WX_EINVAL, "wx_load_state_f32_async: NULL array");
+    if (c->t_bytes != 4) return fail(c, WX_EUNSUPPORTED, "wx_load_state_f32_async: the context stores FP64");
+    if (!c->fields_loaded)
+        return fail(c, WX_ESTATE, "wx_load_state_f32_async: load the winds with wx_load_fields first");
+    if (!pinned_host(T) || !pinned_host(q))
+        return fail(c, WX_EINVAL, "wx_load_state_f32_async: T and q must be pinned host memory");
+    const size_t n = (size_t)c->nx * c->ny * c->nz;
+    cudaStream_t s = (cudaStream_t)stream;
+    RC(ensure_staging(c));  // 2n doubles: room for 2n floats
+    float *sT = reinterpret_cast<float *>(c->staging), *sq = sT + n;
+    CK(cudaMemcpyAsync(sT, T, n * sizeof(float), cudaMemcpyHostToDevice, s), "upload T");
+    CK(cudaMemcpyAsync(sq, q, n * sizeof(float), cudaMemcpyHostToDevice, s), "upload q");
+    c->cur = 0;
+    RC(launch_pack_f32(c, sT, sq, c->fld[0], s));
+    CK(cudaMemsetAsync(c->d_sums_count, 0, sizeof(long long), s), "reset sums count");
+    ++c->generation;
+    c->last_stream = s;
+    return WX_OK;
+}
+
+extern "C" int wx_read_state_f32_async(wx_ctx *c, float *T, float *q, void *stream) {
+    if (!c) return WX_EINVAL;
+    if (c->t_bytes != 4) return fail(c, WX_EUNSUPPORTED, "wx_read_state_f32_async: the context stores FP64");
+    if (!c->fields_loaded) return fail(c, WX_ESTATE, "wx_read_state_f32_async: no fields loaded");
+    if ((T && !pinned_host(T)) || (q && !pinned_host(q)))
+        return fail(c, WX_EINVAL, "wx_read_state_f32_async: T and q must be pinned host memory");
+    const size_t n = (size_t)c->nx * c->ny * c->nz;
+    cudaStream_t s = (cudaStream_t)stream;
+    RC(ensure_staging(c));
+    float *sT = reinterpret_cast<float *>(c->staging), *sq = sT + n;
+    RC(launch_unpack_f32(c, c->fld[c->cur], T ? sT : nullptr, q ? sq : nullptr, s));
+    if (T) CK(cudaMemcpyAsync(T, sT, n * sizeof(float), cudaMemcpyDeviceToHost, s), "download T");
+    if (q) CK(cudaMemcpyAsync(q, sq, n * sizeof(float), cudaMemcpyDeviceToHost, s), "download q");
+    c->last_stream = s;
+    return WX_OK;
+}
+
 // ------------------------------------------------------------ stepping
 extern "C" int wx_step(wx_ctx *c, int n_steps, void *stream) {
     if (!c) return WX_EINVAL;

@@ -53,6 +53,8 @@ SIGNATURES = [
     ("wx_read_fields_device", ctypes.c_int, [_VP, _VP, _VP, _VP]),
     ("wx_load_state_f32", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int]),
     ("wx_read_state_f32", ctypes.c_int, [_VP, _VP, _VP]),
+    ("wx_load_state_f32_async", ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    ("wx_read_state_f32_async", ctypes.c_int, [_VP, _VP, _VP, _VP]),
     ("wx_get_sums", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("wx_physics_columns", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_long, _VP]),
     ("wx_info", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -284,6 +286,17 @@ class Context:
         q = np.empty(n, np.float32) if q is None else _out(q, np.float32, self._n3(), "q")
         _check(lib().wx_read_state_f32(self.ptr, _dptr(T), _dptr(q)), self.ptr)
         return T, q
+
+    def load_state_f32_async(self, T, q, stream=None):
+        """Enqueue the upload of pinned host FP32 T, q on `stream`."""
+        n3 = self._n3()
+        T, q = _host(T, np.float32, n3, "T"), _host(q, np.float32, n3, "q")
+        _check(lib().wx_load_state_f32_async(self.ptr, _dptr(T), _dptr(q), _stream_ptr(stream)), self.ptr)
+
+    def read_state_f32_async(self, T, q, stream=None):
+        """Enqueue the download into pinned host FP32 arrays T, q on `stream`."""
+        T, q = _out(T, np.float32, self._n3(), "T"), _out(q, np.float32, self._n3(), "q")
+        _check(lib().wx_read_state_f32_async(self.ptr, _dptr(T), _dptr(q), _stream_ptr(stream)), self.ptr)
 
     def read_fields_into(self, T, q, stream=None):
         """Device FP64 outputs (torch tensors, either may be None), asynchronous

@@ -151,3 +151,68 @@ def test_binding_refuses_mistyped_or_short_arrays():
     with pytest.raises(ValueError):
         app.load(np.zeros((4, 6, 8)))                     # missing the ghost ring
     app.close()
+
+
+def test_async_transfers_match_the_synchronous_ones():
+    """Enqueued upload, step and download on a stream give the bits of the
+    synchronous calls; pageable host arrays are refused."""
+    case = inputs.round_to_f32(inputs.small_case(nx=70, ny=33, nz=9, seed=15))
+    T32, q32 = _pinned(f32(case.T) * np.float32(1.01)), _pinned(f32(case.q))
+    shape = (case.nz, case.ny, case.nx)
+    a = wx.Context(case.nx, case.ny, case.nz, "f32")
+    a.set_params(case)
+    a.load_fields(case.T, case.q, case.U, case.V)
+    a.load_state_f32(T32, q32)
+    a.step(2)
+    a.sync()
+    want = a.read_state_f32()
+    a.close()
+    b = wx.Context(case.nx, case.ny, case.nz, "f32")
+    b.set_params(case)
+    b.load_fields(case.T, case.q, case.U, case.V)
+    s = torch.cuda.Stream()
+    oT, oq = _pinned(np.zeros(shape, np.float32)), _pinned(np.zeros(shape, np.float32))
+    b.load_state_f32_async(T32, q32, stream=s)
+    b.step(2, stream=s)
+    b.read_state_f32_async(oT, oq, stream=s)
+    s.synchronize()
+    assert np.array_equal(oT, want[0]) and np.array_equal(oq, want[1])
+    with pytest.raises(wx.WxError) as e:
+        b.load_state_f32_async(np.ascontiguousarray(T32.copy()), q32, stream=s)
+    assert e.value.code == -1
+    with pytest.raises(wx.WxError) as e:
+        b.read_state_f32_async(np.zeros(shape, np.float32), oq, stream=s)
+    assert e.value.code == -1
+    b.close()
+
+
+def test_two_contexts_pipelined_on_two_streams():
+    """Independent states pushed through two contexts on two streams,
+    alternating, all enqueued before one synchronize: every result equals
+    the synchronous single-context step of its own input."""
+    case = inputs.round_to_f32(inputs.small_case(nx=64, ny=40, nz=12, seed=16))
+    shape = (case.nz, case.ny, case.nx)
+    ins = [(_pinned(f32(case.T) + np.float32(i)), _pinned(f32(case.q) * np.float32(1 + 0.1 * i))) for i in range(6)]
+    outs = [(_pinned(np.zeros(shape, np.float32)), _pinned(np.zeros(shape, np.float32))) for _ in range(6)]
+    ctxs, streams = [], [torch.cuda.Stream(), torch.cuda.Stream()]
+    for _ in range(2):
+        c = wx.Context(case.nx, case.ny, case.nz, "f32")
+        c.set_params(case)
+        c.load_fields(case.T, case.q, case.U, case.V)
+        ctxs.append(c)
+    for it in range(6):
+        c, s = ctxs[it % 2], streams[it % 2]
+        c.load_state_f32_async(*ins[it], stream=s)
+        c.step(1, stream=s)
+        c.read_state_f32_async(*outs[it], stream=s)
+    for s in streams:
+        s.synchronize()
+    ref = ctxs[0]
+    for it in range(6):
+        ref.load_state_f32(*ins[it])
+        ref.step(1)
+        ref.sync()
+        T, q = ref.read_state_f32()
+        assert np.array_equal(outs[it][0], T) and np.array_equal(outs[it][1], q)
+    for c in ctxs:
+        c.close()
