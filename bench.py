@@ -265,19 +265,22 @@ def e2e_measure(case, dtype, iters=5):
             st.synchronize()
 
     pipelined(4)
-    n_pipe = 4 * iters
-    t0 = time.perf_counter()
-    pipelined(n_pipe)
-    el_p = (time.perf_counter() - t0) / n_pipe
+    n_pipe, rounds = 4 * iters, []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        pipelined(n_pipe)
+        rounds.append((time.perf_counter() - t0) / n_pipe)
+    el_p = statistics.median(rounds)
     for c in ctxs:
         c.close()
     return {"value": case.cells / el_p, "unit": "cell-steps/s",
             "h2d_bytes_per_step": int(T32.nbytes + q32.nbytes),
             "d2h_bytes_per_step": int(To32.nbytes + qo32.nbytes), "ms_per_step": el_p * 1e3,
-            "iterations": n_pipe,
+            "iterations": n_pipe, "ms_per_step_rounds": [r * 1e3 for r in rounds],
             "path": f"two contexts on two streams take alternate steps: wx_load_state_f32_async(pinned "
                     f"host T, q) + wx_step(1) + wx_read_state_f32_async(pinned host) each step, all "
-                    f"enqueued; {n_pipe} steps timed from the first call to the last stream synchronize; "
+                    f"enqueued; median of 3 rounds of {n_pipe} steps, each timed from the first call to "
+                    f"the last stream synchronize; "
                     f"winds (constant in time) loaded once per context by wx_load_fields before timing",
             "sync_single_context": rec_sync, "fp64_api": rec64}
 
