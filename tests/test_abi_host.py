@@ -59,3 +59,35 @@ def test_create_fails_cleanly_without_gpu_or_with_bad_args(lib):
     lib.wx_destroy(None)  # NULL-safe
     assert lib.wx_step(None, 1, None) == -1
     assert lib.wx_sync(None) == -1
+
+
+def _build_c_example(tmp_path):
+    """Compile and link the plain-C example against include/wx.h and
+    libwx.so (C99, warnings as errors)."""
+    import subprocess
+    if not os.path.exists(wx.LIB_PATH):
+        from paper_1802_05839_gb300 import build
+        build.build()
+    exe = str(tmp_path / "c_abi_example")
+    libdir = os.path.dirname(wx.LIB_PATH)
+    cmd = ["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-O1",
+           os.path.join(ROOT, "tests", "c_abi_example.c"), "-I", os.path.join(ROOT, "include"),
+           "-L", libdir, "-lwx", "-Wl,-rpath," + libdir, "-lm", "-o", exe]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    return exe
+
+
+def test_header_is_plain_c_and_links(tmp_path):
+    """include/wx.h compiles as strict C99 and every call the example makes
+    resolves against the library (no C++ or CUDA types leak through)."""
+    assert os.path.exists(_build_c_example(tmp_path))
+
+
+@pytest.mark.gpu
+def test_c_example_runs(tmp_path):
+    import subprocess
+    exe = _build_c_example(tmp_path)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "all checks passed" in r.stdout
