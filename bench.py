@@ -178,14 +178,14 @@ def run_reference(args):
     }))
 
 
-def e2e_measure(case, dtype, iters=5):
+def e2e_measure(case, dtype, iters=5, n_ctx=3):
     """Load (H2D from pinned host) + one step + read back (D2H) per step;
     the median over `iters` steps (host-side copies on a shared host vary
     from one iteration to the next), the mean beside it.
 
     FP32-storage contexts move the state (T, q) in FP32, the prescribed
     winds (constant in time) loaded once beforehand.  The reported figure is
-    pipelined: two contexts on two streams take alternate steps through the
+    pipelined: n_ctx contexts on n_ctx streams take steps in turn through the
     enqueued calls (wx_load_state_f32_async / wx_read_state_f32_async), so
     downloads overlap uploads; the synchronous one-context figure is kept
     under `sync_single_context`, and the FP64 calls (wx_load_fields with the
@@ -245,22 +245,25 @@ def e2e_measure(case, dtype, iters=5):
                 "path": "one context, synchronous: wx_load_state_f32(host T, q) + wx_step(1) + "
                         "wx_read_state_f32(host), median step"}
 
-    # Pipelined: two contexts on two streams take alternate steps, every
+    # Pipelined: n_ctx contexts on n_ctx streams take steps in turn, every
     # transfer enqueued (pinned host arrays), so one context's download
-    # overlaps the other's upload on the link's two copy engines.
-    ctx2 = wx.Context(case.nx, case.ny, case.nz, dtype)
-    ctx2.set_params(case)
-    ctx2.load_fields(T, q, U, V)
-    ctxs, streams = [ctx, ctx2], [torch.cuda.Stream(), torch.cuda.Stream()]
-    outs = [(To32, qo32), (torch.empty(T.shape, dtype=torch.float32).pin_memory().numpy(),
-                           torch.empty(T.shape, dtype=torch.float32).pin_memory().numpy())]
+    # overlaps another's upload on the link's two copy engines.
+    ctxs, streams, outs = [ctx], [torch.cuda.Stream()], [(To32, qo32)]
+    for _ in range(n_ctx - 1):
+        cx = wx.Context(case.nx, case.ny, case.nz, dtype)
+        cx.set_params(case)
+        cx.load_fields(T, q, U, V)
+        ctxs.append(cx)
+        streams.append(torch.cuda.Stream())
+        outs.append((torch.empty(T.shape, dtype=torch.float32).pin_memory().numpy(),
+                     torch.empty(T.shape, dtype=torch.float32).pin_memory().numpy()))
 
     def pipelined(n):
         for it in range(n):
-            c, st = ctxs[it % 2], streams[it % 2]
+            c, st = ctxs[it % n_ctx], streams[it % n_ctx]
             c.load_state_f32_async(T32, q32, stream=st)
             c.step(1, stream=st)
-            c.read_state_f32_async(*outs[it % 2], stream=st)
+            c.read_state_f32_async(*outs[it % n_ctx], stream=st)
         for st in streams:
             st.synchronize()
 
@@ -277,7 +280,7 @@ def e2e_measure(case, dtype, iters=5):
             "h2d_bytes_per_step": int(T32.nbytes + q32.nbytes),
             "d2h_bytes_per_step": int(To32.nbytes + qo32.nbytes), "ms_per_step": el_p * 1e3,
             "iterations": n_pipe, "ms_per_step_rounds": [r * 1e3 for r in rounds],
-            "path": f"two contexts on two streams take alternate steps: wx_load_state_f32_async(pinned "
+            "path": f"{n_ctx} contexts on {n_ctx} streams take steps in turn: wx_load_state_f32_async(pinned "
                     f"host T, q) + wx_step(1) + wx_read_state_f32_async(pinned host) each step, all "
                     f"enqueued; median of 3 rounds of {n_pipe} steps, each timed from the first call to "
                     f"the last stream synchronize; "
@@ -653,7 +656,7 @@ def run_ours(args):
         "clocks": clk,
     }
     if not args.skip_e2e:
-        out["e2e"] = e2e_measure(case, dtype)
+        out["e2e"] = e2e_measure(case, dtype, n_ctx=args.e2e_contexts)
     if not args.skip_cpu:
         out["cpu_baseline"] = cpu_baseline(case if dtype == "f64" else make_case("f64"))
     if not args.no_variants and dtype == "f32" and (case.nx, case.ny, case.nz) == (1581, 1301, 58):
@@ -677,6 +680,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64", "mixed"])
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--e2e-contexts", type=int, default=3,
+                    help="contexts (and streams) the pipelined end-to-end measurement rotates through")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--nx", type=int, default=1581, help="grid override (profiling captures only)")
     ap.add_argument("--ny", type=int, default=1301, help="grid override (profiling captures only)")
