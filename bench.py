@@ -359,6 +359,34 @@ def variant_plain(dtype, steps, nx=1581, ny=1301, nz=58):
     return out
 
 
+def variant_decomposed(steps, nx=1581, ny=1301, nz=58, layouts=((2, 2), (4, 4)), plain_ms=None):
+    """The paper grid split into px x py blocks (simulated ranks on one GPU):
+    per step one step-kernel launch over all blocks and one halo-exchange
+    launch; the exchange's algorithmic bytes are its strips read + written."""
+    import torch
+    from paper_1802_05839_gb300 import wx
+    case = make_case("f32", nx, ny, nz)
+    peak, _ = peaks()
+    out = {"workload": f"paper grid {nx}x{ny}x{nz} (f32) in px x py blocks, depth-1 halo exchange"}
+    for px, py in layouts:
+        d = wx.Decomposition(nx, ny, nz, "f32", px, py)
+        d.set_params(case)
+        d.load_fields(case.T, case.q, case.U, case.V)
+        st = torch.cuda.Stream()
+        ms = _time_steps(lambda: d.step(1, stream=st), steps, st)
+        d.sync()
+        halo_cells = 2 * nz * 2 * (ny * px + nx * py)   # both fields, 4 strips per block
+        alg = case.cells * CELL_BYTES["f32"] + nx * ny * COL_BYTES["f32"] + halo_cells * 2 * 4
+        rec = {"ms_per_step": ms, "value": case.cells / (ms * 1e-3), "unit": "cell-steps/s",
+               "steps": steps, "blocks": px * py, "gpu_launches_per_step": d.last_launches(),
+               "halo_bytes_per_step": halo_cells * 2 * 4, "hbm_frac": alg / (ms * 1e-3) / 1e9 / peak}
+        if plain_ms:
+            rec["vs_plain_step"] = ms / plain_ms
+        out[f"{px}x{py}"] = rec
+        d.close()
+    return out
+
+
 def variant_ensemble(steps):
     """16 uneven members (C4), one persistent launch per step, graph-replayed."""
     import torch
@@ -575,6 +603,30 @@ def variant_rk3(steps_f32=100, steps_f64=20, nx=1581, ny=1301, nz=58):
     return out
 
 
+def variants_summary(v):
+    """The variants' headline figures in a few hundred bytes; written as the
+    line's last key, so that a reader keeping only the line's tail still
+    sees them."""
+    r = lambda x, n=4: None if x is None else float(f"{x:.{n}g}")
+    s = {}
+    for k in ("f64", "mixed", "ensemble", "rk3_f32", "decomposed_2x2", "decomposed_4x4"):
+        if k.startswith("decomposed"):
+            rec = (v.get("decomposed") or {}).get(k.split("_")[1])
+        else:
+            rec = v.get(k) if k != "rk3_f32" else (v.get("rk3") or {}).get("f32")
+        if rec:
+            s[k] = {"ms": r(rec.get("ms_per_step")), "hbm_frac": r(rec.get("hbm_frac"), 3)}
+    sur = v.get("surrogate")
+    if sur:
+        s["surrogate"] = {"ms": r(sur.get("ms_per_step")), "vs_plain": r(sur.get("vs_plain_step"), 3),
+                          "fallback_frac": r(sur.get("fallback_frac"), 3),
+                          "tendency_rel_l2": r(sur.get("val_tendency_rel_l2", {}).get("all"), 3),
+                          "gemm_bf16_frac": r(sur.get("network_forward", {}).get("frac"), 3)}
+        if "fallback_frac_at" in sur:
+            s["surrogate"]["fallback_frac_at"] = {k: r(x, 3) for k, x in sur["fallback_frac_at"].items()}
+    return s
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -668,7 +720,9 @@ def run_ours(args):
             "reduced_app": variant_reduced_app(100),
             "ablation": variant_ablation(100),
             "rk3": variant_rk3(),
+            "decomposed": variant_decomposed(100, plain_ms=ms),
         }
+        out["variants_summary"] = variants_summary(out["variants"])
     print(json.dumps(out))
 
 
@@ -688,7 +742,8 @@ def main():
     ap.add_argument("--nz", type=int, default=58, help="grid override (profiling captures only)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--epochs", type=int, default=64, help="surrogate training epochs")
-    ap.add_argument("--only", choices=["f64", "mixed", "ensemble", "surrogate", "reduced_app", "ablation", "rk3"],
+    ap.add_argument("--only", choices=["f64", "mixed", "ensemble", "surrogate", "reduced_app", "ablation", "rk3",
+                                       "decomposed"],
                     help="run one variant alone and print its record (profiling captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -706,6 +761,8 @@ def main():
             rec = variant_reduced_app(args.steps)
         elif args.only == "ablation":
             rec = variant_ablation(args.steps)
+        elif args.only == "decomposed":
+            rec = variant_decomposed(args.steps, args.nx, args.ny, args.nz)
         elif args.only == "rk3":
             rec = variant_rk3(args.steps, max(3, args.steps // 5), args.nx, args.ny, args.nz)
         else:

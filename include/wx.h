@@ -194,22 +194,26 @@ long wx_last_launches(const wx_ctx *c);
 
 /* FP64 sums of caller-owned fields without any device allocation.  The
  * paper has no counterpart: this exists for callers that cannot allocate
- * device memory (inside a CUDA-graph capture, under an allocator that owns
- * every device byte, or in a latency-bound loop).
+ * device memory, such as plug-ins whose host application owns every device
+ * byte through its own pool, or real-time loops that cannot accept the
+ * implicit synchronisation, latency or possible failure of cudaMalloc.
  *   T, q     device arrays [nz][ny][nx], float (dtype WX_F32) or double
  *            (WX_F64);
- *   dz       device array [nz] of double;
+ *   dz       device array [nz] of double (used at full FP64 precision for
+ *            either dtype: FP32 fields are weighted by dz split into two
+ *            floats with compensated products and sums);
  *   out      device array of 2 doubles: out[0] = h^2 sum q dz_k,
  *            out[1] = h^2 sum T dz_k (deterministic order).
  * Per-tile partial sums go to one fixed __device__ array inside the library
- * (1 MiB, held by each GPU that loads it until the process exits), so grids
- * needing more than 65536 tiles of 32x4 columns are rejected with
- * WX_EUNSUPPORTED.  Nothing has to be cleared between calls, but calls
- * sharing that array must not overlap on the GPU (they would race).  The
- * first call on a device looks up the array's address with that device
- * current; make it before any stream capture.  Asynchronous on the stream.
- * Errors: WX_EINVAL, WX_EUNSUPPORTED, WX_ECUDA; message in
- * wx_sums_noalloc_error(). */
+ * (1 MiB, held by each GPU that loads it until the process exits).  Limits:
+ * at most 65536 tiles of 32x4 columns, and ny <= 4*65535 = 262140 (the tile
+ * grid's row limit); larger grids are rejected with WX_EUNSUPPORTED.
+ * Nothing has to be cleared between calls, but calls sharing that array
+ * must not overlap on the GPU (they would race).  The first successful call
+ * on a device looks up the array's address with that device current; make
+ * it before any stream capture (a failed lookup is retried on the next
+ * call).  Asynchronous on the stream.  Errors: WX_EINVAL, WX_EUNSUPPORTED,
+ * WX_ECUDA; message in wx_sums_noalloc_error(). */
 int wx_sums_noalloc(const void *T, const void *q, int dtype, int nx, int ny,
                     int nz, const double *dz, double h, double *out,
                     void *cuda_stream);
@@ -317,6 +321,77 @@ int wx_ens_tune(wx_ens *e, const char *cache_path, int force,
 long wx_ens_last_launches(const wx_ens *e);
 void wx_ens_destroy(wx_ens *e);          /* NULL-safe; frees the members */
 const char *wx_ens_last_error(const wx_ens *e);
+
+/* ------------------------------------------ horizontal decomposition
+ * The paper's multi-GPU layout of ASUCA (App. F decomposition table;
+ * Sec. 5.4, the halo exchange's share of the strong-scaling runs): one
+ * periodic nx x ny x nz grid split into px x py horizontal blocks (ASUCA
+ * decomposes only in i and j, never in k).  Each block is a sub-domain
+ * context with its own resident fields and ghost ring; a step is the step
+ * kernel over every block (one launch over all blocks' tiles, like an
+ * ensemble) that writes no periodic ghost copies, then ONE halo-exchange
+ * launch that fills every block's four depth-1 ghost strips (west and east
+ * columns, south and north rows, for T and q at every level) from its
+ * neighbours' edge lines.  Corners are not exchanged: the 7-point stencil
+ * and the upwind fluxes never read them.  The blocks run as simulated
+ * ranks on one GPU; the interior of every block is bit-for-bit the
+ * undecomposed step's.  Sub-domain r = iy*px + ix covers columns
+ * [xsplit[ix], xsplit[ix+1]) x [ysplit[iy], ysplit[iy+1]). */
+typedef struct wx_dom wx_dom;
+
+enum { WX_HALO_WEST = 0, WX_HALO_EAST = 1, WX_HALO_SOUTH = 2, WX_HALO_NORTH = 3 };
+
+/* One ghost strip of a sub-domain: for every level and field, the ghost
+ * line dst_line of sub-domain r (a column index -1 or nx_r for WEST/EAST, a
+ * row index -1 or ny_r for SOUTH/NORTH, in r's local coordinates) receives
+ * line src_line of sub-domain src (its last or first interior column or
+ * row, in src's local coordinates); len cells (ny_r for columns, nx_r for
+ * rows).  src == r where a block is its own periodic neighbour. */
+typedef struct {
+    int dir, src, src_line, dst_line, len;
+} wx_halo_strip;
+
+/* The four strips of sub-domain r (WEST, EAST, SOUTH, NORTH order) of a
+ * px x py decomposition of an nx x ny grid.  xsplit[px+1] / ysplit[py+1]:
+ * block boundaries, 0 = x_0 < x_1 < ... < x_px = nx (strictly increasing,
+ * so blocks are >= 1 column wide), or NULL for the even split x_i =
+ * floor(i nx / px).  Host-only bookkeeping (no CUDA call); the device
+ * exchange is built from it.  WX_EINVAL for bad sizes or splits. */
+int wx_dom_halo_plan(int nx, int ny, int px, int py, const int *xsplit,
+                     const int *ysplit, int r, wx_halo_strip out[4]);
+
+/* px * py in 1..16 blocks; dtype WX_F32, WX_F64 or WX_MIXED.  WX_EINVAL,
+ * WX_EUNSUPPORTED, WX_ENOMEM, WX_ECUDA; message in wx_dom_last_error(NULL). */
+int wx_dom_create(int nx, int ny, int nz, int dtype, int px, int py,
+                  const int *xsplit, const int *ysplit, wx_dom **out);
+/* Parameters of the whole grid (kappa_mult [ny*nx] is split per block).
+ * WX_RK3 and WX_SURROGATE are refused (WX_EUNSUPPORTED). */
+int wx_dom_set_params(wx_dom *d, const wx_params *p);
+/* Host FP64 arrays of the whole grid: T, q [nz][ny][nx]; U, V [ny][nx].
+ * Scatters them to the blocks (with each block's west/south face winds
+ * from its neighbours) and runs the exchange once.  Synchronous. */
+int wx_dom_load_fields(wx_dom *d, const double *T, const double *q,
+                       const double *U, const double *V);
+/* n_steps >= 0 steps on the caller's stream, 2 launches per step (plus the
+ * blocks' side solves and sums kernels where enabled); asynchronous. */
+int wx_dom_step(wx_dom *d, int n_steps, void *cuda_stream);
+/* Wait for the last stream; WX_ETIMEOUT / WX_ENONFINITE as wx_sync. */
+int wx_dom_sync(wx_dom *d);
+/* Gathers the blocks' states into host FP64 arrays of the whole grid
+ * (either may be NULL).  Synchronous. */
+int wx_dom_read_fields(wx_dom *d, double *T, double *q);
+/* The whole grid's FP64 sums per recorded step (WX_SUMS): each block's
+ * recorded sums, added in block order r = 0, 1, ... (the 2-double
+ * reduction a multi-GPU run would do across ranks).  As wx_get_sums. */
+int wx_dom_get_sums(wx_dom *d, double *mass_q, double *energy_T,
+                    int max_steps, int *n_out);
+int wx_dom_size(const wx_dom *d);          /* px * py, 0 for NULL */
+/* Block r (owned by the decomposition; read-only use: stepping it alone
+ * would leave its ghost ring stale), NULL if out of range. */
+wx_ctx *wx_dom_block(wx_dom *d, int r);
+long wx_dom_last_launches(const wx_dom *d);
+void wx_dom_destroy(wx_dom *d);            /* NULL-safe; frees the blocks */
+const char *wx_dom_last_error(const wx_dom *d);
 
 /* ----------------------------------------------- learned column physics
  * A small MLP surrogate of the column physics (232 -> 512 -> 512 -> 512 ->

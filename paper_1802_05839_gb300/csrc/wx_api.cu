@@ -167,7 +167,7 @@ extern "C" void wx_destroy(wx_ctx *c) {
     void *ptrs[] = {c->fld[0], c->fld[1], c->fld[2], c->tab_rk, c->U, c->V, c->kmult, c->tab,
                     c->d_lev,  c->staging, c->d_status, c->partials, c->sums_ring, c->flag_list,
                     c->flag_idx, c->flag_fac, c->flag_e, c->flag_side, c->flag_corr,
-                    c->fin_park, c->fin_ticket, c->d_sums_count};
+                    c->fin_park, c->fin_ticket, c->d_sums_count, c->Uw0, c->Vs0};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete c;
@@ -345,9 +345,10 @@ int wx::check_cfl(wx_ctx *c) {
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
                 const double ue = c->U_h[(size_t)j * nx + i];
-                const double uw = c->U_h[(size_t)j * nx + (i == 0 ? nx - 1 : i - 1)];
+                const bool hw = i == 0 && !c->Uw0_h.empty(), hs = j == 0 && !c->Vs0_h.empty();
+                const double uw = hw ? c->Uw0_h[j] : c->U_h[(size_t)j * nx + (i == 0 ? nx - 1 : i - 1)];
                 const double vn = c->V_h[(size_t)j * nx + i];
-                const double vs = c->V_h[(size_t)(j == 0 ? ny - 1 : j - 1) * nx + i];
+                const double vs = hs ? c->Vs0_h[i] : c->V_h[(size_t)(j == 0 ? ny - 1 : j - 1) * nx + i];
                 if (!std::isfinite(ue) || !std::isfinite(vn))
                     return fail(c, WX_EINVAL, "winds must be finite");
                 const double o = std::max(ue, 0.0) - std::min(uw, 0.0) + std::max(vn, 0.0) - std::min(vs, 0.0);

@@ -45,6 +45,26 @@ template <typename T> struct alignas(4 * sizeof(T)) Q4 { T x, y, z, w; };
 // device status word bits
 enum : unsigned { ST_NONFINITE = 1u, ST_TIMEOUT = 2u, ST_BADARG = 4u };
 
+// One level of the Thomas forward sweep of a column's implicit vertical
+// diffusion, (I - dt L_v) x = r with zero-flux ends, in a form in which
+// nothing cancels.  The sub- and super-diagonals are a_k = -na_k <= 0 and
+// c_k = -nc_k <= 0 and the diagonal b_k = 1 + na_k + nc_k, so the textbook
+// pivot m_k = b_k - a_k c'_{k-1} equals 1 + nc_k + na_k g_{k-1} with
+// g_k = 1 + c'_k = (1 + na_k g_{k-1}) / m_k: sums of nonnegative terms only.
+// The textbook form subtracts two numbers of size ~na_k when the column is
+// near-singular (na, nc >> 1) and loses that many digits in FP32.
+template <typename T> struct ThomasSweep {
+    T g = T(0), d = T(0);  // g_{k-1} and d'_{k-1}
+    // advances to level k (na_0 = 0 at the bottom); returns c'_k, d holds d'_k
+    __device__ __forceinline__ T level(T na, T nc, T r) {
+        const T m = fma(na, g, T(1) + nc);
+        const T inv = T(1) / m;
+        g = fma(na, g, T(1)) * inv;
+        d = fma(na, d, r) * inv;
+        return -nc * inv;
+    }
+};
+
 template <typename T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };
@@ -63,6 +83,12 @@ template <typename T> struct StepArgs {
     const int *flag_idx;          // [ny][nx]: index f of a listed column, else -1
     float *side;                  // [nz][2][n_list]
     long n_list;
+    // sub-domain of a decomposed grid: the west-face winds of column 0
+    // ([ny]) and the south-face winds of row 0 ([nx]) come from the
+    // neighbours (nullptr: periodic within this grid), and the ghost ring is
+    // filled by the halo exchange, so the step writes no ghost copies
+    const T *Uw0, *Vs0;
+    int halo;
 };
 
 // One member of a (possibly single-member) batch stepped by one launch:
@@ -171,6 +197,13 @@ struct wx_ctx {
     float *sur_Y = nullptr, *sur_lev = nullptr;  // [rows][128]; [2][nz] kappa_lev, alpha dz
     unsigned long long *sur_nfb = nullptr;       // fallback columns of the last step
     unsigned sur_gen = ~0u;       // generation sur_lev was built for
+
+    // sub-domain of a wx_dom: neighbours' face winds at the west column and
+    // the south row (device, storage type; host FP64 copies for the CFL
+    // check), and no periodic ghost copies in the step
+    bool halo = false;
+    void *Uw0 = nullptr, *Vs0 = nullptr;
+    std::vector<double> Uw0_h, Vs0_h;
 
     wx::StepCfg cfg;
     bool cfg_forced = false;

@@ -1159,15 +1159,10 @@ __global__ void __launch_bounds__(kApplyThreads) sur_apply_kernel(float *__restr
             // scratch), back substitution with the heating of the
             // optical-depth scan from the top
             float *cp = yr, *dp = yr + kNZ;
-            float cpp = 0.f, dpp = 0.f;
+            ThomasSweep<float> fw;
             for (int k = 0; k < kNZ; ++k) {
-                const float ak = s * sE[k].x, ck = s * sE[k].y;
-                const float m = ((1.f - ak) - ck) - ak * cpp;
-                const float inv = 1.f / m;
-                cpp = ck * inv;
-                dpp = (ts[k] - ak * dpp) * inv;
-                cp[k] = cpp;
-                dp[k] = dpp;
+                cp[k] = fw.level(-s * sE[k].x, -s * sE[k].y, ts[k]);
+                dp[k] = fw.d;
             }
             float x = 0.f, tau = 0.f, Etop = 1.f;
             for (int k = kNZ - 1; k >= 0; --k) {

@@ -247,9 +247,11 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
             const bool v = (i0 + c < nx) && (j < ny) && M.a.advection;
             const int ic = v ? i0 + c : 0, jc = v ? j : 0;
             wd.v[4 * c + 0] = v ? M.a.U[(size_t)jc * nx + ic] : T(0);
-            wd.v[4 * c + 1] = v ? M.a.U[(size_t)jc * nx + (ic == 0 ? nx - 1 : ic - 1)] : T(0);
+            const T *uw = (ic == 0 && M.a.Uw0) ? M.a.Uw0 + jc : M.a.U + (size_t)jc * nx + (ic == 0 ? nx - 1 : ic - 1);
+            const T *vs = (jc == 0 && M.a.Vs0) ? M.a.Vs0 + ic : M.a.V + (size_t)(jc == 0 ? ny - 1 : jc - 1) * nx + ic;
+            wd.v[4 * c + 1] = v ? *uw : T(0);
             wd.v[4 * c + 2] = v ? M.a.V[(size_t)jc * nx + ic] : T(0);
-            wd.v[4 * c + 3] = v ? M.a.V[(size_t)(jc == 0 ? ny - 1 : jc - 1) * nx + ic] : T(0);
+            wd.v[4 * c + 3] = v ? *vs : T(0);
         }
         return wd;
     };
@@ -275,7 +277,10 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
         const int bx = t % gx, by = t / gx;
         const int i0 = bx * kTileX + 2 * tx, j = by * TY + wy;
         const bool va = (i0 < nx) && (j < ny), vb = (i0 + 1 < nx) && (j < ny);
-        const bool edge = bx == 0 || bx == gx - 1 || by == 0 || by == gy - 1;
+        // masked stores for ragged tiles, plus the periodic ghost copies of
+        // border tiles (a decomposed block's ghosts come from the exchange)
+        const bool edge = a.halo ? ((bx == gx - 1 && nx % kTileX) || (by == gy - 1 && ny % TY))
+                                 : (bx == 0 || bx == gx - 1 || by == 0 || by == gy - 1);
 
         // per-column coefficients of the horizontal operator, paired (a, b)
         const Winds wc = wnext;
@@ -295,7 +300,7 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
                            a.dth * (fmax(ue, zero) - fmin(uw, zero) + fmax(vn, zero) - fmin(vs, zero));
                 const bool v = c ? vb : va;
                 k1[c] = (KMODE == 1 && a.kmult && v) ? a.kmult[(size_t)j * nx + i0 + c] : T(1);
-                fl[c] = (KMODE == 2 && v) ? a.flag_idx[(size_t)j * nx + i0 + c] : -1;
+                fl[c] = (KMODE == 2 && v && a.flag_idx) ? a.flag_idx[(size_t)j * nx + i0 + c] : -1;
             }
             cC = V{c5[0][0], c5[1][0]};
             cE = V{c5[0][1], c5[1][1]};
@@ -353,6 +358,7 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
                 T *row = a.out + k * lev + fld + (size_t)(j + 1) * a.P;
                 if (va) row[i0 + kGhostX] = Qs.x;
                 if (vb) row[i0 + 1 + kGhostX] = Qs.y;
+                if (!a.halo) {  // periodic ghost copies (a sub-domain's come from the exchange)
                 if (va && i0 == 0) row[kGhostX + nx] = Qs.x;
                 if (vb && i0 + 1 == nx - 1) row[kGhostX - 1] = Qs.y;
                 if (va && i0 == nx - 1) row[kGhostX - 1] = Qs.x;
@@ -365,6 +371,7 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
                     T *g = a.out + k * lev + fld;
                     if (va) g[i0 + kGhostX] = Qs.x;
                     if (vb) g[i0 + 1 + kGhostX] = Qs.y;
+                }
                 }
             }
             qp -= lev;
@@ -491,6 +498,7 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
                 T *row = a.out + k * lev + (size_t)(j + 1) * a.P;
                 if (va) row[i0 + kGhostX] = tn.x;
                 if (vb) row[i0 + 1 + kGhostX] = tn.y;
+                if (!a.halo) {
                 if (va && i0 == 0) row[kGhostX + nx] = tn.x;
                 if (vb && i0 + 1 == nx - 1) row[kGhostX - 1] = tn.y;
                 if (va && i0 == nx - 1) row[kGhostX - 1] = tn.x;
@@ -503,6 +511,7 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
                     T *g = a.out + k * lev;
                     if (va) g[i0 + kGhostX] = tn.x;
                     if (vb) g[i0 + 1 + kGhostX] = tn.y;
+                }
                 }
                 const V tm = V{va ? tn.x : T(0), vb ? tn.y : T(0)};
                 if (SUMS)
@@ -655,15 +664,10 @@ __global__ void __launch_bounds__(128) columns_kernel(const T *__restrict__ Ts, 
     const T *qc = qs + col * nz;
     const T s = km ? km[col] : T(1);
     const Q4<T> *tB = tab + REC_B * nz, *tC = tab + REC_C * nz, *tE = tab + REC_E * nz;
-    T cpp = 0, dpp = 0;
+    ThomasSweep<T> fw;
     for (int k = 0; k < nz; ++k) {
-        const T ak = s * tE[k].x, ck = s * tE[k].y;
-        const T m = ((T(1) - ak) - ck) - ak * cpp;
-        const T inv = recip(m);
-        cpp = ck * inv;
-        dpp = (tc[k] - ak * dpp) * inv;
-        cpa[k * nt + t] = cpp;
-        dpa[k * nt + t] = dpp;
+        cpa[k * nt + t] = fw.level(-s * tE[k].x, -s * tE[k].y, tc[k]);
+        dpa[k * nt + t] = fw.d;
     }
     T x = 0, tau = 0, Etop = 1;
     for (int k = nz - 1; k >= 0; --k) {
@@ -825,6 +829,9 @@ template <typename T> static void fill_member(const wx_ctx *c, Member<T> &M, lon
     a.flag_idx = c->flag_idx;
     a.side = c->flag_side;
     a.n_list = c->n_list;
+    a.Uw0 = (const T *)c->Uw0;
+    a.Vs0 = (const T *)c->Vs0;
+    a.halo = c->halo ? 1 : 0;
     M.tile0 = tile0;
     M.gx = (c->nx + kTileX - 1) / kTileX;
     M.gy = (c->ny + ty - 1) / ty;
@@ -893,8 +900,13 @@ static int dispatch_flags(wx_ctx *const *mem, int n, const StepCfg &cfg, int sms
 template <typename T>
 static int dispatch_kmode(wx_ctx *const *mem, int n, const StepCfg &cfg, int sms, unsigned *st, cudaStream_t s,
                           std::string &err) {
-    if constexpr (std::is_same<T, float>::value)
-        if (mixed(mem[0])) return dispatch_flags<T, 2>(mem, n, cfg, sms, st, s, err);
+    // members share kappa_mult use; one with listed columns takes the whole
+    // batch through the listing variant (members without any list none)
+    if constexpr (std::is_same<T, float>::value) {
+        bool any = false;
+        for (int i = 0; i < n; ++i) any = any || mixed(mem[i]);
+        if (any) return dispatch_flags<T, 2>(mem, n, cfg, sms, st, s, err);
+    }
     if (!per_col(mem[0])) return dispatch_flags<T, 0>(mem, n, cfg, sms, st, s, err);
     return dispatch_flags<T, 1>(mem, n, cfg, sms, st, s, err);
 }
@@ -1020,15 +1032,10 @@ __global__ void __launch_bounds__(64) rk_physics_kernel(T *__restrict__ out, con
     } else {
         T *cp = scr, *dp = scr + (size_t)nz * nt;
         const T s = km[c];
-        T cpp = 0, dpp = 0;
+        ThomasSweep<T> fw;
         for (int k = 0; k < nz; ++k) {
-            const T ak = s * tE[k].x, ck = s * tE[k].y;
-            const T m = ((T(1) - ak) - ck) - ak * cpp;
-            const T inv = recip(m);
-            cpp = ck * inv;
-            dpp = (phi3(k, 0) - ak * dpp) * inv;
-            cp[(size_t)k * nt + t] = cpp;
-            dp[(size_t)k * nt + t] = dpp;
+            cp[(size_t)k * nt + t] = fw.level(-s * tE[k].x, -s * tE[k].y, phi3(k, 0));
+            dp[(size_t)k * nt + t] = fw.d;
         }
         T x = 0, tau = 0, Etop = 1;
         for (int k = nz - 1; k >= 0; --k) {

@@ -80,6 +80,21 @@ SIGNATURES = [
     ("wx_ens_last_launches", ctypes.c_long, [_VP]),
     ("wx_ens_destroy", None, [_VP]),
     ("wx_ens_last_error", ctypes.c_char_p, [_VP]),
+    ("wx_dom_halo_plan", ctypes.c_int, [ctypes.c_int] * 4 + [ctypes.POINTER(ctypes.c_int)] * 2 +
+     [ctypes.c_int, _VP]),
+    ("wx_dom_create", ctypes.c_int, [ctypes.c_int] * 6 + [ctypes.POINTER(ctypes.c_int)] * 2 +
+     [ctypes.POINTER(_VP)]),
+    ("wx_dom_set_params", ctypes.c_int, [_VP, ctypes.POINTER(wx_params)]),
+    ("wx_dom_load_fields", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    ("wx_dom_step", ctypes.c_int, [_VP, ctypes.c_int, _VP]),
+    ("wx_dom_sync", ctypes.c_int, [_VP]),
+    ("wx_dom_read_fields", ctypes.c_int, [_VP, _VP, _VP]),
+    ("wx_dom_get_sums", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    ("wx_dom_size", ctypes.c_int, [_VP]),
+    ("wx_dom_block", _VP, [_VP, ctypes.c_int]),
+    ("wx_dom_last_launches", ctypes.c_long, [_VP]),
+    ("wx_dom_destroy", None, [_VP]),
+    ("wx_dom_last_error", ctypes.c_char_p, [_VP]),
     ("wx_gemm_bf16", ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP,
                                     _VP, _VP, _VP, _VP, _VP]),
     ("wx_mlp_last_error", ctypes.c_char_p, []),
@@ -658,3 +673,108 @@ def wx_selftest_wait_timeout(limit_ns):
     w = ctypes.c_ulonglong()
     code = lib().wx_selftest_wait_timeout(int(limit_ns), ctypes.byref(w))
     return code, w.value
+
+
+# ---------------------------------------------------------------- decomposition
+WX_HALO_WEST, WX_HALO_EAST, WX_HALO_SOUTH, WX_HALO_NORTH = 0, 1, 2, 3
+
+
+class wx_halo_strip(ctypes.Structure):
+    _fields_ = [("dir", ctypes.c_int), ("src", ctypes.c_int), ("src_line", ctypes.c_int),
+                ("dst_line", ctypes.c_int), ("len", ctypes.c_int)]
+
+
+def _splits(parts, given):
+    if given is None:
+        return None
+    given = [int(x) for x in given]
+    if len(given) != parts + 1:
+        raise ValueError(f"split: {len(given)} boundaries, expected {parts + 1}")
+    return (ctypes.c_int * (parts + 1))(*given)
+
+
+def halo_plan(nx, ny, px, py, r, xsplit=None, ysplit=None):
+    """The four ghost strips of block r (wx_dom_halo_plan) as dicts with the
+    keys dir, src, src_line, dst_line, len.  Host-only: no GPU needed."""
+    out = (wx_halo_strip * 4)()
+    code = lib().wx_dom_halo_plan(int(nx), int(ny), int(px), int(py), _splits(px, xsplit),
+                                  _splits(py, ysplit), int(r), ctypes.cast(out, _VP))
+    if code != 0:
+        raise WxError(code, "wx_dom_halo_plan: bad sizes or splits")
+    return [{k: getattr(s, k) for k, _ in wx_halo_strip._fields_} for s in out]
+
+
+def _dcheck(code, d):
+    if code != 0:
+        msg = lib().wx_dom_last_error(d)
+        raise WxError(code, msg.decode() if msg else "")
+
+
+class Decomposition:
+    """One periodic nx x ny x nz grid split into px x py blocks stepped with
+    a depth-1 halo exchange (wx_dom_*): host FP64 arrays of the whole grid
+    in and out."""
+
+    def __init__(self, nx, ny, nz, dtype="f32", px=2, py=1, xsplit=None, ysplit=None):
+        self.nx, self.ny, self.nz, self.dtype, self.px, self.py = int(nx), int(ny), int(nz), dtype, px, py
+        p = _VP()
+        _dcheck(lib().wx_dom_create(self.nx, self.ny, self.nz, DTYPES[dtype], int(px), int(py),
+                                    _splits(px, xsplit), _splits(py, ysplit), ctypes.byref(p)), None)
+        self.ptr = p
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            lib().wx_dom_destroy(self.ptr)
+            self.ptr = None
+
+    __del__ = close
+
+    def set_params(self, case, flags=None, dd_threshold=0.0):
+        if flags is None:
+            flags = (WX_ADVECTION if case.advection else 0) | (WX_PHYSICS if case.physics else 0)
+        n2 = self.nx * self.ny
+        arr = lambda a: None if a is None else np.ascontiguousarray(a, np.float64).reshape(-1)
+        keep = [arr(case.dz), arr(case.kappa_lev), arr(case.alpha), arr(case.kappa_mult)]
+        for a, n, what in zip(keep, (self.nz, self.nz, self.nz, n2), ("dz", "kappa_lev", "alpha", "kappa_mult")):
+            if a is not None and a.size != n:
+                raise ValueError(f"{what}: {a.size} elements, expected {n}")
+        ptr = lambda a: None if a is None else a.ctypes.data_as(_D)
+        p = wx_params(case.dt, case.h, case.kappa_h, case.S0, case.q_ref, dd_threshold,
+                      ptr(keep[0]), ptr(keep[1]), ptr(keep[2]), ptr(keep[3]), flags)
+        self._keep = keep
+        _dcheck(lib().wx_dom_set_params(self.ptr, ctypes.byref(p)), self.ptr)
+
+    def load_fields(self, T, q, U, V):
+        n3, n2 = self.nx * self.ny * self.nz, self.nx * self.ny
+        T, q = _host(T, np.float64, n3, "T"), _host(q, np.float64, n3, "q")
+        U, V = _host(U, np.float64, n2, "U"), _host(V, np.float64, n2, "V")
+        _dcheck(lib().wx_dom_load_fields(self.ptr, _dptr(T), _dptr(q), _dptr(U), _dptr(V)), self.ptr)
+
+    def step(self, n_steps=1, stream=None):
+        _dcheck(lib().wx_dom_step(self.ptr, int(n_steps), _stream_ptr(stream)), self.ptr)
+
+    def sync(self):
+        _dcheck(lib().wx_dom_sync(self.ptr), self.ptr)
+
+    def read_fields(self):
+        T, q = np.empty((self.nz, self.ny, self.nx)), np.empty((self.nz, self.ny, self.nx))
+        _dcheck(lib().wx_dom_read_fields(self.ptr, _dptr(T), _dptr(q)), self.ptr)
+        return T, q
+
+    def sums(self, max_steps=4096):
+        m, e = np.empty(max_steps), np.empty(max_steps)
+        n = ctypes.c_int(0)
+        _dcheck(lib().wx_dom_get_sums(self.ptr, _dptr(m), _dptr(e), max_steps, ctypes.byref(n)), self.ptr)
+        return m[:n.value], e[:n.value]
+
+    def size(self):
+        return int(lib().wx_dom_size(self.ptr))
+
+    def last_launches(self):
+        return int(lib().wx_dom_last_launches(self.ptr))
+
+    def block_step_config(self, r=0):
+        """Launch configuration of block r (all blocks share it)."""
+        b = _Member(_VP(lib().wx_dom_block(self.ptr, int(r))), 0, 0, 0, self.dtype)
+        return b.step_config()

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
+from increments import assert_increments
 from paper_1802_05839_gb300 import inputs, wx
 
 pytestmark = pytest.mark.gpu
@@ -161,4 +162,8 @@ def test_c4_full_size_sampled():
         To, qo = oracle.step_columns(c, c.T, c.q, c.U, c.V, ci, cj)
         assert np.max(np.abs(Tg[:, cj, ci].T - To)) / np.max(np.abs(c.T)) <= 1e-5
         assert np.max(np.abs(qg[:, cj, ci].T - qo)) / np.max(np.abs(c.q)) <= 1e-5
+        dyn = c.copy()
+        dyn.physics = False
+        Ts, _ = oracle.step_columns(dyn, c.T, c.q, c.U, c.V, ci, cj)
+        assert_increments(c.T[:, cj, ci].T, Ts, Tg[:, cj, ci].T, To, what=f"member {c.nx}x{c.ny}x{c.nz}")
     ens.close()

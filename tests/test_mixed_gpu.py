@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
+from increments import assert_increments, strong_physics
 from paper_1802_05839_gb300 import inputs, wx
 
 pytestmark = pytest.mark.gpu
@@ -47,13 +48,48 @@ def test_flagged_columns_are_the_weakly_dominant_ones():
     ctx.close()
 
 
+def per_step(case, dtype, n, flags=None):
+    """n steps one at a time; each checked against the oracle step from the
+    GPU's own previous state: field error <= 1e-5, and the increments (all
+    columns, then the listed kappa_mult != 1 ones alone) within 8 ulp."""
+    ctx = wx.Context(case.nx, case.ny, case.nz, dtype)
+    ctx.set_params(case, flags=flags)
+    ctx.load_fields(case.T, case.q, case.U, case.V)
+    listed = np.broadcast_to((case.kappa_mult != 1.0)[None], (case.nz, case.ny, case.nx))
+    T, q = case.T, case.q
+    for s in range(n):
+        ctx.step(1)
+        ctx.sync()
+        Tg, qg = ctx.read_fields()
+        To, qo = oracle.step(case, T, q, case.U, case.V)
+        assert maxrel(Tg, To) <= 1e-5 and maxrel(qg, qo) <= 1e-5, (s, maxrel(Tg, To), maxrel(qg, qo))
+        Ts, _ = oracle.dynamics(case, T, q, case.U, case.V)
+        assert_increments(T, Ts, Tg, To, what=f"{dtype} step {s}")
+        if listed.any():
+            assert_increments(T, Ts, Tg, To, mask=listed, what=f"{dtype} step {s}, listed columns")
+        T, q = Tg, qg
+    ctx.close()
+
+
 @pytest.mark.parametrize("shape", [(97, 61, 58), (70, 33, 17), (1, 5, 9)])
 def test_mixed_matches_oracle(shape):
     nx, ny, nz = shape
     case = inputs.round_to_f32(inputs.paper_grid_case(nx, ny, nz, seed=5, near_singular=True))
     Tg, qg, nflag, _, _ = run(case, "mixed", 5)
     To, qo = oracle.run(case, 5, case.T, case.q, case.U, case.V)
-    assert maxrel(Tg, To) <= 3e-5 and maxrel(qg, qo) <= 3e-5
+    # five steps accumulated: five times the per-step bound
+    assert maxrel(Tg, To) <= 5e-5 and maxrel(qg, qo) <= 5e-5
+    per_step(case, "mixed", 3)
+
+
+@pytest.mark.parametrize("dtype", ["mixed", "f32"])
+def test_strong_physics_increments_with_kappa_mult(dtype):
+    """Physics increments ~1 K on well-conditioned columns and several K on
+    the near-singular ones (FP64 elimination under WX_MIXED, the FP32 side
+    solve under WX_F32): both within 8 ulp of the oracle's."""
+    case = inputs.round_to_f32(strong_physics(
+        inputs.paper_grid_case(97, 61, 58, seed=3, near_singular=True)))
+    per_step(case, dtype, 3)
 
 
 def test_mixed_improves_flagged_columns_over_fp32():
@@ -122,23 +158,15 @@ def test_error_against_the_oracle_at_steps_1_100_500():
 @pytest.mark.parametrize("shape", [(97, 61, 58), (70, 33, 17)])
 def test_fp32_with_kappa_mult_matches_oracle(shape):
     """WX_F32 with a kappa_mult field: the table path plus the FP32 side
-    solve of the kappa_mult != 1 columns, within the FP32 step bound that the
-    weakly dominant columns allow (3e-5 per step, as for WX_MIXED)."""
+    solve of the kappa_mult != 1 columns, within the FP32 per-step bound
+    (1e-5) and the increment bar, on all columns and the listed ones."""
     nx, ny, nz = shape
     case = inputs.round_to_f32(inputs.paper_grid_case(nx, ny, nz, seed=7, near_singular=True))
     ctx = wx.Context(nx, ny, nz, "f32")
     ctx.set_params(case)
-    ctx.load_fields(case.T, case.q, case.U, case.V)
     assert ctx.flagged_columns() == 0      # none in FP64
-    T, q = case.T, case.q
-    for _ in range(3):
-        ctx.step(1)
-        ctx.sync()
-        Tg, qg = ctx.read_fields()
-        To, qo = oracle.step(case, T, q, case.U, case.V)
-        assert maxrel(Tg, To) <= 3e-5 and maxrel(qg, qo) <= 1e-5
-        T, q = Tg, qg
     ctx.close()
+    per_step(case, "f32", 3)
 
 
 def test_c3_full_size_sampled():
@@ -166,6 +194,13 @@ def test_c3_full_size_sampled():
     Tgs, qgs = Tg[:, cj, ci].T, qg[:, cj, ci].T
     assert np.max(np.abs(Tgs - To)) / np.max(np.abs(case.T)) <= 1e-5
     assert np.max(np.abs(qgs - qo)) / np.max(np.abs(case.q)) <= 1e-5
+    dyn = case.copy()
+    dyn.physics = False
+    Ts, _ = oracle.step_columns(dyn, case.T, case.q, case.U, case.V, ci, cj)
+    Tin = case.T[:, cj, ci].T
+    assert_increments(Tin, Ts, Tgs, To, what="C3 sampled columns")
+    assert_increments(Tin[3000:4000], Ts[3000:4000], Tgs[3000:4000], To[3000:4000],
+                      what="C3 flagged columns")
     w = case.h ** 2 * case.dz[:, None, None]
     assert len(m) == 1
     assert abs(e[-1] - np.sum(Tg * w)) / abs(e[-1]) < 1e-12

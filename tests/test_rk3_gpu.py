@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
+from increments import assert_increments, strong_physics
 from paper_1802_05839_gb300 import inputs, wx
 
 pytestmark = pytest.mark.gpu
@@ -16,6 +17,38 @@ RK = wx.WX_ADVECTION | wx.WX_PHYSICS | wx.WX_RK3
 
 def relmax(a, b):
     return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def rk3_dynamics(case, T, q):
+    """T* of the RK3 step: the oracle's three stages without the physics."""
+    dyn = case.copy()
+    dyn.physics = False
+    return oracle.step_rk3(dyn, T, q, case.U, case.V)[0]
+
+
+@pytest.mark.parametrize("near_singular", [False, True])
+def test_fp32_strong_physics_increments(near_singular):
+    """FP32 RK3 with a physics increment of ~1 K (near-singular columns:
+    several K; their elimination runs on the fly per column): increments
+    within 8 ulp of the oracle's, on all columns and the listed ones."""
+    case = inputs.round_to_f32(strong_physics(
+        inputs.paper_grid_case(70, 50, 58, seed=4, near_singular=near_singular)))
+    ctx = ctx_for(case, "f32")
+    T, q = case.T, case.q
+    listed = None if case.kappa_mult is None else \
+        np.broadcast_to((case.kappa_mult != 1.0)[None], (case.nz, case.ny, case.nx))
+    for s in range(3):
+        ctx.step(1)
+        ctx.sync()
+        Tg, qg = ctx.read_fields()
+        To, qo = oracle.step_rk3(case, T, q, case.U, case.V)
+        Ts = rk3_dynamics(case, T, q)
+        assert_increments(T, Ts, Tg, To, what=f"step {s}", resolve=0.01)
+        if listed is not None:
+            assert_increments(T, Ts, Tg, To, mask=listed, what=f"step {s}, listed", resolve=0.01)
+        assert relmax(qg, qo) <= 1e-5
+        T, q = Tg, qg
+    ctx.close()
 
 
 def ctx_for(case, dtype, flags=RK):
@@ -41,6 +74,9 @@ def test_every_step_matches_oracle(dtype, tol, shape, ns):
         Tg, qg = ctx.read_fields()
         To, qo = oracle.step_rk3(case, T, q, case.U, case.V)
         assert relmax(Tg, To) <= tol and relmax(qg, qo) <= tol
+        if dtype == "f32":  # increments; T* = the three-stage dynamics alone
+            Ts = rk3_dynamics(case, T, q)
+            assert_increments(T, Ts, Tg, To, what=f"RK3 {shape}")
         T, q = Tg, qg  # per-step error: the next oracle step starts from the GPU state
     assert ctx.last_launches() == 5  # 3 stage kernels, 1 combine, combine + physics
     ctx.close()
@@ -121,3 +157,4 @@ def test_paper_grid_full_size_fp32():
     ctx.close()
     To, qo = oracle.step_rk3(case, case.T, case.q, case.U, case.V)
     assert relmax(Tg, To) <= 1e-5 and relmax(qg, qo) <= 1e-5
+    assert_increments(case.T, rk3_dynamics(case, case.T, case.q), Tg, To, what="RK3 paper grid")

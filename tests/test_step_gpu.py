@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
+from increments import assert_increments, strong_physics
 from paper_1802_05839_gb300 import inputs, wx
 
 pytestmark = pytest.mark.gpu
@@ -65,6 +66,35 @@ def test_small_case_ten_steps_per_step(dtype):
         To, qo = oracle.step(case, T, q, case.U, case.V)
         assert maxrel(Tg, To) <= TOL[dtype], (s, maxrel(Tg, To))
         assert maxrel(qg, qo) <= TOL[dtype], (s, maxrel(qg, qo))
+        if dtype == "f32":  # the increments, element by element
+            Ts, _ = oracle.dynamics(case, T, q, case.U, case.V)
+            assert_increments(T, Ts, Tg, To, what=f"step {s}")
+        T, q = Tg, qg
+    ctx.close()
+
+
+@pytest.mark.parametrize("near_singular", [False, True])
+def test_f32_strong_physics_increments(near_singular):
+    """FP32 step on a case whose physics increment is ~1 K (a +-5 K level
+    zig-zag, ten times the vertical diffusivity, S0 = 100): the increments
+    T^{n+1} - T* and T^{n+1} - T^n within 8 ulp of max|T| of the oracle's,
+    which resolves the physics to a few 1e-3 of its size; with near-singular
+    columns this covers the FP32 side solve of the kappa_mult columns."""
+    case = inputs.round_to_f32(strong_physics(
+        inputs.paper_grid_case(96, 80, 58, seed=4, near_singular=near_singular)))
+    ctx = wx.Context(case.nx, case.ny, case.nz, "f32")
+    ctx.set_params(case)
+    ctx.load_fields(case.T, case.q, case.U, case.V)
+    T, q = case.T, case.q
+    for s in range(3):
+        ctx.step(1)
+        ctx.sync()
+        Tg, qg = ctx.read_fields()
+        To, qo = oracle.step(case, T, q, case.U, case.V)
+        Ts, _ = oracle.dynamics(case, T, q, case.U, case.V)
+        r = assert_increments(T, Ts, Tg, To, what=f"step {s}", resolve=0.01)
+        print(f"step {s}: {r['err_ulp']:.2f} ulp, rel to the physics increment {r['rel_phys']:.2e}")
+        assert maxrel(qg, qo) <= 1e-5
         T, q = Tg, qg
     ctx.close()
 
@@ -151,6 +181,11 @@ def test_paper_grid_full_size_sampled(dtype):
     scaleT, scaleq = np.max(np.abs(case.T)), np.max(np.abs(case.q))
     assert np.max(np.abs(Tgs - To)) / scaleT <= TOL[dtype]
     assert np.max(np.abs(qgs - qo)) / scaleq <= TOL[dtype]
+    if dtype == "f32":  # increments at the sampled columns (T* from the dynamics alone)
+        dyn = case.copy()
+        dyn.physics = False
+        Ts, _ = oracle.step_columns(dyn, case.T, case.q, case.U, case.V, ci, cj)
+        assert_increments(case.T[:, cj, ci].T, Ts, Tgs, To, what="paper grid, sampled columns")
     # whole-field properties at full size: finite, and q inside its old range
     assert np.isfinite(Tg).all() and np.isfinite(qg).all()
     assert qg.min() >= case.q.min() - 1e-7 and qg.max() <= case.q.max() + 1e-7

@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
+from increments import assert_increments, strong_physics
 from oracle import mlp as omlp
 from paper_1802_05839_gb300 import inputs, wx
 
@@ -58,6 +59,46 @@ def test_every_column_falling_back_gives_the_exact_step(near_singular):
     T, q = ctx.read_fields()
     To, qo = oracle.run(c, 3, c.T, c.q, c.U, c.V)
     assert relmax(T, To) <= 1e-5 and relmax(q, qo) <= 1e-5
+    ctx.close()
+    # step by step from the GPU's own state: the exact path's increments,
+    # on every column and on the near-singular ones alone
+    ctx = ctx_for(c, net, tol=0.0)
+    listed = None if c.kappa_mult is None else np.broadcast_to((c.kappa_mult != 1.0)[None], c.T.shape)
+    Tp, qp = c.T, c.q
+    for s in range(2):
+        ctx.step(1)
+        ctx.sync()
+        Tg, qg = ctx.read_fields()
+        To, _ = oracle.step(c, Tp, qp, c.U, c.V)
+        Ts, _ = oracle.dynamics(c, Tp, qp, c.U, c.V)
+        assert_increments(Tp, Ts, Tg, To, what=f"fallback step {s}")
+        if listed is not None:
+            assert_increments(Tp, Ts, Tg, To, mask=listed, what=f"fallback step {s}, listed")
+        Tp, qp = Tg, qg
+    ctx.close()
+    net.close()
+
+
+@pytest.mark.parametrize("near_singular", [False, True])
+def test_fallback_strong_physics_increments(near_singular):
+    """The exact path of the surrogate step (every column falls back) on a
+    case with a physics increment of ~1 K: increments within 8 ulp of the
+    oracle's, which resolves the FP32 solve and heating to a few 1e-3."""
+    c = inputs.round_to_f32(strong_physics(inputs.paper_grid_case(70, 50, NZ, seed=3,
+                                                                  near_singular=near_singular)))
+    net = random_net(c)
+    ctx = ctx_for(c, net, tol=0.0)
+    ctx.step(1)
+    ctx.sync()
+    assert ctx.surrogate_fallbacks() == c.nx * c.ny
+    Tg, qg = ctx.read_fields()
+    To, qo = oracle.step(c, c.T, c.q, c.U, c.V)
+    Ts, _ = oracle.dynamics(c, c.T, c.q, c.U, c.V)
+    assert_increments(c.T, Ts, Tg, To, what="fallback", resolve=0.01)
+    if near_singular:
+        listed = np.broadcast_to((c.kappa_mult != 1.0)[None], c.T.shape)
+        assert_increments(c.T, Ts, Tg, To, mask=listed, what="fallback, listed", resolve=0.01)
+    assert relmax(qg, qo) <= 1e-5
     ctx.close()
     net.close()
 

@@ -14,6 +14,7 @@ import numpy as np
 import pytest
 
 import oracle
+from increments import assert_increments
 from paper_1802_05839_gb300 import inputs, surrogate as S, wx
 
 pytestmark = pytest.mark.gpu
@@ -59,10 +60,19 @@ def test_surrogate_step_falls_back_outside_the_training_distribution(trained):
     ctx.set_params(c, flags=wx.WX_ADVECTION | wx.WX_PHYSICS | wx.WX_SURROGATE)
     ctx.load_fields(c.T, c.q, c.U, c.V)
     ctx.set_surrogate(m, 2e-2)
-    for _ in range(2):
+    listed = np.broadcast_to((c.kappa_mult != 1.0)[None], c.T.shape)
+    Tp, qp = c.T, c.q
+    for s in range(2):
         ctx.step(1)
         ctx.sync()
         assert ctx.surrogate_fallbacks() >= n_singular
+        Tg, qg = ctx.read_fields()
+        # the near-singular columns take the exact path: their increments
+        # within 8 ulp of the oracle's step from the same state
+        To, _ = oracle.step(c, Tp, qp, c.U, c.V)
+        Ts, _ = oracle.dynamics(c, Tp, qp, c.U, c.V)
+        assert_increments(Tp, Ts, Tg, To, mask=listed, what=f"step {s}, near-singular columns")
+        Tp, qp = Tg, qg
     T, q = ctx.read_fields()
     To, qo = oracle.run(c, 2, c.T, c.q, c.U, c.V)
     assert np.max(np.abs(T - To)) / np.max(np.abs(To)) <= 1e-5
