@@ -460,6 +460,21 @@ def variant_surrogate(steps, nx=1581, ny=1301, plain_ms=None, train_epochs=32):
     ctx.sync()
     fb = ctx.surrogate_fallbacks()
     launches = ctx.last_launches()
+    # the fallback fraction along a run from the initial state
+    ctx.load_fields(case.T, case.q, case.U, case.V)
+    fb_at, done = {}, 0
+    for mark in (1, 50, 100):
+        ctx.step(mark - done, stream=st)
+        done = mark
+        ctx.sync()
+        fb_at[str(mark)] = ctx.surrogate_fallbacks() / (nx * ny)
+    # the acceptance policy: exact fused steps while the network is declined,
+    # a probe of 16 rows every 8 steps
+    ctx.load_fields(case.T, case.q, case.U, case.V)
+    ctx.set_surrogate_policy(0.5, probe_every=8, probe_rows=16)
+    pol_ms = _time_steps(lambda: ctx.step(1, stream=st), steps, st)  # after its first decision
+    ctx.sync()
+    pol_launches = ctx.last_launches()
     ctx.close()
     # the network alone on every column of the grid (tensor-core roofline)
     rows = (nx * ny + 127) // 128 * 128
@@ -483,9 +498,16 @@ def variant_surrogate(steps, nx=1581, ny=1301, plain_ms=None, train_epochs=32):
                      "loss_last": hist[-1], "seconds": t2 - t1, "setup_seconds": t1 - t0},
            "network_forward": {"ms": fwd_ms, "tflops": tflops, "peak_tflops": tpk, "frac": tflops / tpk,
                                "flop_per_column_run": flop_col, "flop_per_column_alg": flop_alg},
-           "gpu_launches_per_step": launches}
+           "gpu_launches_per_step": launches,
+           "fallback_frac_at": fb_at,
+           "policy": {"min_accept": 0.5, "probe_every": 8, "probe_rows": 16, "ms_per_step": pol_ms,
+                      "steps": steps, "gpu_launches_last_step": pol_launches,
+                      "path": "wx_set_surrogate_policy: network steps while acceptance >= 0.5, else the fused "
+                              "exact step with a 16-row network probe every 8 steps; timed after 3 warm-up "
+                              "steps (the first two steps run the network before the first decision)"}}
     if plain_ms:
         out["vs_plain_step"] = ms / plain_ms
+        out["policy"]["vs_plain_step"] = pol_ms / plain_ms
     return out
 
 
@@ -624,6 +646,9 @@ def variants_summary(v):
                           "gemm_bf16_frac": r(sur.get("network_forward", {}).get("frac"), 3)}
         if "fallback_frac_at" in sur:
             s["surrogate"]["fallback_frac_at"] = {k: r(x, 3) for k, x in sur["fallback_frac_at"].items()}
+        if "policy" in sur:
+            s["surrogate"]["policy_ms"] = r(sur["policy"].get("ms_per_step"))
+            s["surrogate"]["policy_vs_plain"] = r(sur["policy"].get("vs_plain_step"), 3)
     return s
 
 

@@ -491,9 +491,26 @@ int wx_mlp_status(wx_mlp *m);
  * network must outlive the attachment; the context owns its own activation
  * buffers.  WX_SURROGATE excludes WX_SUMS. */
 int wx_set_surrogate(wx_ctx *c, wx_mlp *m, double fallback_tol);
-/* Columns the residual check sent to the exact path in the last step
- * (synchronises). */
+/* Columns the residual check sent to the exact path in the last step, or
+ * nx*ny when the acceptance policy ran that step exactly (synchronises). */
 int wx_surrogate_fallbacks(wx_ctx *c, long *n_fallback);
+/* Acceptance policy of WX_SURROGATE steps (the paper has no learned part;
+ * this keeps the method's exact physics as the fallback).  With
+ * min_accept = 0 (the default) the network runs on every step.  With
+ * min_accept in (0, 1], a step whose measured acceptance (columns accepted
+ * / columns) falls below min_accept switches the following steps to the
+ * exact fused step (dynamics and column physics in one kernel, as without
+ * WX_SURROGATE); every probe_every exact steps the network is evaluated on
+ * a band of probe_rows rows of the new state (the next band each time),
+ * counting the columns its residual checks would accept, and an acceptance
+ * of at least min_accept switches back to network steps.  A decision uses
+ * the counts of the step two before it, read back through pinned memory:
+ * no device synchronisation in the step, and the same sequence of steps
+ * always takes the same decisions.  The policy's measurements restart at
+ * every state load and at wx_set_surrogate.  min_accept in [0, 1],
+ * probe_every >= 1, probe_rows >= 1 (clamped to ny), else WX_EINVAL. */
+int wx_set_surrogate_policy(wx_ctx *c, double min_accept, int probe_every,
+                            int probe_rows);
 
 /* Free the context and its device memory.  NULL-safe. */
 void wx_destroy(wx_ctx *c);

@@ -169,6 +169,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Two 32-bit columns (col, col+1) of this thread's TMEM lane, from registers
+// (warp-wide: each thread of the warp writes its own lane of the warp's
+// lane quarter).  Asynchronous: tmem_wait_st before reading them back.
+__device__ __forceinline__ void tmem_st2(uint32_t taddr, float a, float b) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(taddr), "r"(__float_as_uint(a)),
+                 "r"(__float_as_uint(b))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // Shared-memory matrix descriptor of a K-major BF16 tile written by TMA with
 // 128-byte swizzle: 8-row x 128-byte swizzle atoms, 1024 bytes between atom
 // rows (stride byte offset), descriptor version 1, layout type 2 (128B).

@@ -198,10 +198,10 @@ extern "C" int wx_flagged_columns(const wx_ctx *c, long *n) {
 
 extern "C" int wx_set_step_config(wx_ctx *c, int ty, int kb, int stages, int ctas_per_sm, int prefetch) {
     if (!c) return WX_EINVAL;
-    if (!(ty == 1 || ty == 2 || ty == 4 || ty == 8) || !(kb == 2 || kb == 4) || stages < 3 || stages > 16 ||
-        ctas_per_sm < 1 || prefetch < 0 || prefetch > 64)
+    if (!(ty == 1 || ty == 2 || ty == 4 || ty == 8 || ty == 12) || !(kb == 2 || kb == 4) || stages < 3 ||
+        stages > 16 || ctas_per_sm < 1 || prefetch < 0 || prefetch > 64)
         return fail(c, WX_EINVAL,
-                    "wx_set_step_config: ty in {1,2,4,8}, kb in {2,4}, stages 3..16, ctas >= 1, prefetch 0..64");
+                    "wx_set_step_config: ty in {1,2,4,8,12}, kb in {2,4}, stages 3..16, ctas >= 1, prefetch 0..64");
     if (ty == 1 && kb == 4) return fail(c, WX_EUNSUPPORTED, "wx_set_step_config: ty = 1 with kb = 4 is not built");
     StepCfg g;
     g.ty = ty;
@@ -416,6 +416,7 @@ extern "C" int wx_load_fields(wx_ctx *c, const double *T, const double *q, const
     RC(launch_convert(c, dV, c->V, cols, 0));
     CK(cudaMemset(c->d_sums_count, 0, sizeof(long long)), "reset sums count");
     CK(cudaDeviceSynchronize(), "wx_load_fields");
+    reset_surrogate_policy(c);
     ++c->generation;
     c->fields_loaded = true;
     c->cfl_ok = false;
@@ -463,6 +464,7 @@ extern "C" int wx_load_state_f32(wx_ctx *c, const float *T, const float *q, int 
     RC(launch_pack_f32(c, dT, dq, c->fld[0], 0));
     CK(cudaMemset(c->d_sums_count, 0, sizeof(long long)), "reset sums count");
     CK(cudaDeviceSynchronize(), "wx_load_state_f32");
+    reset_surrogate_policy(c);
     ++c->generation;
     return WX_OK;
 }
@@ -512,6 +514,7 @@ extern "C" int wx_load_state_f32_async(wx_ctx *c, const float *T, const float *q
     c->cur = 0;
     RC(launch_pack_f32(c, sT, sq, c->fld[0], s));
     CK(cudaMemsetAsync(c->d_sums_count, 0, sizeof(long long), s), "reset sums count");
+    reset_surrogate_policy(c);
     ++c->generation;
     c->last_stream = s;
     return WX_OK;
@@ -544,7 +547,7 @@ extern "C" int wx_step(wx_ctx *c, int n_steps, void *stream) {
     long launches = 0;
     if (c->flags & WX_SURROGATE) {
         if (!c->sur) return fail(c, WX_ESTATE, "wx_step: WX_SURROGATE without an attached network");
-        for (int n = 0; n < n_steps; ++n) RC(launch_surrogate_step(c, s, &launches));
+        for (int n = 0; n < n_steps; ++n) RC(launch_surrogate_policy_step(c, s, &launches));
     } else if (c->flags & WX_RK3) {
         for (int n = 0; n < n_steps; ++n) RC(launch_rk3_step(c, s, &launches));
     } else {

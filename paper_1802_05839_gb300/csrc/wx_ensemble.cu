@@ -238,7 +238,7 @@ extern "C" int wx_ens_set_step_config(wx_ens *e, int ty, int kb, int stages, int
     g.stages = stages;
     g.ctas_per_sm = ctas_per_sm;
     g.prefetch = prefetch;
-    if (!(ty == 1 || ty == 2 || ty == 4 || ty == 8) || !(kb == 2 || kb == 4) || (ty == 1 && kb == 4) ||
+    if (!(ty == 1 || ty == 2 || ty == 4 || ty == 8 || ty == 12) || !(kb == 2 || kb == 4) || (ty == 1 && kb == 4) ||
         stages < 3 || stages > 16 || ctas_per_sm < 1 || prefetch < 0 || prefetch > 64)
         return efail(e, WX_EINVAL, "wx_ens_set_step_config: invalid configuration");
     const int rc = ens_apply_cfg(e, g);
@@ -343,7 +343,7 @@ static int tune_batch(wx_ctx *const *mem, int n, unsigned *status, const char *c
     bool any = false;
     const int iters = 4;
     for (int kb : {2, 4})
-        for (int ty : {2, 4, 8})
+        for (int ty : {2, 4, 8, 12})
             for (int st : {3, 4, 6, 8}) {
                 StepCfg g;
                 g.ty = ty;
@@ -356,7 +356,7 @@ static int tune_batch(wx_ctx *const *mem, int n, unsigned *status, const char *c
                 const int cmax = std::min(228 * 1024 / (bytes + 1024), 2048 / (32 * (ty + 1)));
                 for (int ctas = cmax; ctas >= std::max(1, cmax - 1); --ctas) {
                     g.ctas_per_sm = ctas;
-                    if (apply(g) != WX_OK) continue;
+                    if (!cfg_fits(mem[deepest], g, nullptr) || apply(g) != WX_OK) continue;
                     long l = 0;
                     bool ok = launch_batch(mem, n, g, status, s, &l, err) == WX_OK;  // warm-up
                     cudaEventRecord(e0, s);

@@ -122,19 +122,27 @@ struct SmemPlan {
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
+// TMEM column state of the FP32 step kernel: every consumer lane keeps F_k
+// of its two columns (2 nz <= 128 words) in its own TMEM lane; warps w,
+// w + 4 and w + 8 share a lane quarter and take 128 columns each, so a CTA
+// allocates 128 (4 consumer warps), 256 (8) or all 512 (12) columns.
+constexpr int kTmemMaxNz = 64;
+__host__ __device__ constexpr uint32_t kTmemCols(int ty) { return ty > 8 ? 512u : (ty > 4 ? 256u : 128u); }
+
 // Shared-memory plan of the step kernel: per-level table, TMA ring of
 // `stages` slots (kb planes x 2 fields x (ty+2) rows x kBoxX), per-thread
 // column state (F_k of the lane's two columns, plus their e_k for per-column
-// kappa), then full/empty mbarriers.
+// kappa; none when it lives in TMEM), then full/empty mbarriers and the
+// TMEM address.
 __host__ __device__ inline SmemPlan plan_smem(int nz, int ty, int stages, int kb, int t_bytes,
-                                              bool per_col) {
+                                              bool per_col, bool tmem = false) {
     SmemPlan p;
     const int nt = 32 * ty;
     p.tab_off = 0;
     p.ring_off = align_up(kTabRec * nz * 4 * t_bytes, 128);
     p.stage_bytes = align_up(kb * 2 * (ty + 2) * kBoxX * t_bytes, 128);
     p.state_off = align_up(p.ring_off + stages * p.stage_bytes, 128);
-    const int state = nz * nt * 2 * t_bytes * (per_col ? 2 : 1);
+    const int state = tmem ? 0 : nz * nt * 2 * t_bytes * (per_col ? 2 : 1);
     p.bar_off = align_up(p.state_off + state, 16);
     p.total = p.bar_off + 2 * stages * 8 + 16;
     return p;
@@ -195,8 +203,29 @@ struct wx_ctx {
     long sur_rows = 0;            // nx*ny rounded up to 128
     void *sur_X = nullptr, *sur_H[2] = {nullptr, nullptr};
     float *sur_Y = nullptr, *sur_lev = nullptr;  // [rows][128]; [2][nz] kappa_lev, alpha dz
-    unsigned long long *sur_nfb = nullptr;       // fallback columns of the last step
+    unsigned long long *sur_nfb = nullptr;       // [0] fallbacks of the last network step, [1] probe rejections
     unsigned sur_gen = ~0u;       // generation sur_lev was built for
+    // acceptance policy (wx_set_surrogate_policy): the network runs while
+    // its measured acceptance is at least sur_min_accept; otherwise steps
+    // are exact fused steps, and every sur_probe_every steps the network is
+    // probed on sur_probe_rows rows of the state.  Decisions use the counts
+    // of the step two before (read back through pinned memory and events).
+    double sur_min_accept = 0.0;
+    int sur_probe_every = 8, sur_probe_rows = 16;
+    int sur_mode = 0;             // 0: network steps, 1: exact steps
+    bool sur_last_exact = false;  // the last step ran no network
+    long long sur_step = 0, sur_next_probe = 0;
+    int sur_probe_row0 = 0;
+    static constexpr int kSurRing = 8;
+    struct SurRead {
+        long long step = -1;
+        long ncols = 0;
+        int slot = 0;
+    };
+    std::vector<SurRead> sur_reads;          // outstanding counts, oldest first
+    unsigned long long *sur_host = nullptr;  // pinned [kSurRing]
+    cudaEvent_t sur_ev[kSurRing] = {};
+    int sur_slot = 0;
 
     // sub-domain of a wx_dom: neighbours' face winds at the west column and
     // the south row (device, storage type; host FP64 copies for the CFL
@@ -240,6 +269,10 @@ int apply_cfg(wx_ctx *c, const StepCfg &g);
 int check_cfl(wx_ctx *c);
 // WX_SURROGATE (wx_mlp.cu)
 int launch_surrogate_step(wx_ctx *c, cudaStream_t s, long *launches);
+// one WX_SURROGATE step under the context's acceptance policy
+int launch_surrogate_policy_step(wx_ctx *c, cudaStream_t s, long *launches);
+// forget the policy's measurements (a new state was loaded)
+void reset_surrogate_policy(wx_ctx *c);
 void free_surrogate(wx_ctx *c);
 
 }  // namespace wx

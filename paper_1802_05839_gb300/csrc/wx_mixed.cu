@@ -108,10 +108,11 @@ __global__ void flag_factor_kernel(const double *lev, const double *km, const in
 // n64 columns (dominance ratio below the threshold), in FP32 for the rest --
 // then the FP32 back substitution plus the parked heating.  The column's T
 // (and its ghost copies) in the new state is overwritten; with sums, the
-// FP64 energy change of the column is recorded for the finalize kernel.
-// Both sweeps go kFixChunk levels at a time: a chunk's loads (coalesced
-// factors and parked values; the scattered old T) are issued before its
-// recurrence and stores, so that their latencies overlap.
+// column's own FP64 sum of T dz is recorded for the finalize kernel (the
+// step kernel leaves listed columns out of its T sums).  Both sweeps go
+// kFixChunk levels at a time: a chunk's loads (coalesced factors and parked
+// values) are issued before its recurrence and stores, so that their
+// latencies overlap.
 constexpr int kFixChunk = 8;
 
 template <typename F>
@@ -157,9 +158,9 @@ __global__ void __launch_bounds__(128, 6) mixed_fixup_kernel(const int *__restri
     const int ip = i + kGhostX;
     float *col0 = out + (size_t)(j + 1) * P;  // level 0 row of the column's T
     float x = 0.f;
-    float sE = 0.f, cE = 0.f;  // compensated sum of (T_new - T_old) dz
+    float sE = 0.f, cE = 0.f;  // compensated sum of T dz
     for (int k0 = 0; k0 < nz; k0 += kFixChunk) {
-        float fk[kFixChunk], ek[kFixChunk], hk[kFixChunk], old[kFixChunk];
+        float fk[kFixChunk], ek[kFixChunk], hk[kFixChunk];
 #pragma unroll
         for (int u = 0; u < kFixChunk; ++u) {
             const int k = k0 + u;
@@ -167,7 +168,6 @@ __global__ void __launch_bounds__(128, 6) mixed_fixup_kernel(const int *__restri
             ek[u] = in ? fe[(size_t)k * nflag + f] : 0.f;
             fk[u] = in ? r[k * st] : 0.f;
             hk[u] = in ? r[k * st + nflag] : 0.f;
-            old[u] = (in && corr) ? col0[k * lev + ip] : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < kFixChunk; ++u) {
@@ -177,14 +177,15 @@ __global__ void __launch_bounds__(128, 6) mixed_fixup_kernel(const int *__restri
             const float tn = x + hk[u];
             float *row = col0 + k * lev;
             if (corr) {
-                // tn and the old value are close, so their FP32 difference is
-                // exact; the product with dz (hi + lo) and the sum are
-                // compensated (exact product error, TwoSum)
-                const float d = tn - old[u];
-                const float dzh = dz2[k].z, dzl = dz2[k].w;  // dz as hi + lo floats
-                const float p = d * dzh, pe = fmaf(d, dzh, -p) + d * dzl;
-                const float s1 = sE + p, bp = s1 - sE;
-                cE += ((sE - (s1 - bp)) + (p - bp)) + pe;
+                // T dz with dz as hi + lo floats: exact product error and
+                // TwoSum, written as round-to-nearest intrinsics so that
+                // nothing is contracted
+                const float dzh = dz2[k].z, dzl = dz2[k].w;
+                const float p = __fmul_rn(tn, dzh);
+                const float pe = __fmaf_rn(tn, dzl, __fmaf_rn(tn, dzh, -p));
+                const float s1 = __fadd_rn(sE, p), bp = __fsub_rn(s1, sE);
+                const float e = __fadd_rn(__fsub_rn(sE, __fsub_rn(s1, bp)), __fsub_rn(p, bp));
+                cE = __fadd_rn(cE, __fadd_rn(e, pe));
                 sE = s1;
             }
             row[ip] = tn;

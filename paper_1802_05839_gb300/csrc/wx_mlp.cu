@@ -967,7 +967,7 @@ __global__ void __launch_bounds__(kFeatThreads) sur_features_kernel(const float 
                                                                     const float *__restrict__ lev,
                                                                     const float *__restrict__ norm,
                                                                     __nv_bfloat16 *__restrict__ X, long ncol,
-                                                                    long rows) {
+                                                                    long rows, long c0) {
     __shared__ float tile[kSB * kFS];
     __shared__ float smean[kInP], sinv[kInP], sfa[kInP], sfb[kInP], skm[kSB];
     const long r0 = (long)blockIdx.x * kSB;
@@ -978,16 +978,16 @@ __global__ void __launch_bounds__(kFeatThreads) sur_features_kernel(const float 
         sfa[d] = (f >= kCS && f < 3 * kNZ) ? lev[f - kCS] : 0.f;
         sfb[d] = (f >= 3 * kNZ && f < kIn) ? lev[kNZ + f - 3 * kNZ] : 0.f;
     }
-    for (int e = threadIdx.x; e < kSB; e += blockDim.x) skm[e] = (km && r0 + e < ncol) ? km[r0 + e] : 1.f;
+    for (int e = threadIdx.x; e < kSB; e += blockDim.x) skm[e] = (km && r0 + e < ncol) ? km[c0 + r0 + e] : 1.f;
     {
         constexpr int G = kFeatThreads / kSB, PER = kCS / G;
         static_assert(kFeatThreads % kSB == 0 && kCS % G == 0, "plane split");
         const int u = threadIdx.x % kSB, g = threadIdx.x / kSB;
-        const long c = r0 + u;
+        const long c = r0 + u, cg = c0 + c;  // row of X, column of the grid
         const size_t plane = (size_t)R * P;
         float v[PER];
         if (c < ncol) {
-            const int j = (int)(c / nx), i = (int)(c - (long)j * nx);
+            const int j = (int)(cg / nx), i = (int)(cg - (long)j * nx);
             const float *src = fld + (size_t)(j + 1) * P + i + kGhostX;
 #pragma unroll
             for (int n = 0; n < PER; ++n) v[n] = src[(size_t)(g + n * G) * plane];
@@ -1079,7 +1079,8 @@ __global__ void __launch_bounds__(kApplyThreads) sur_apply_kernel(float *__restr
                                                         const float *__restrict__ norm, float dt, float S0,
                                                         float tol, long ncol,
                                                         unsigned long long *__restrict__ n_fallback,
-                                                        unsigned *__restrict__ status) {
+                                                        unsigned *__restrict__ status, long c0,
+                                                        int count_only) {
     extern __shared__ __align__(16) float dsm[];
     float *tile = dsm;                  // [kSB][kTS] T* | q*; T* is overwritten by T^{n+1}
     float *ysm = dsm + kSB * kTS;       // [kSB][kYS] outputs, then scratch
@@ -1120,7 +1121,7 @@ __global__ void __launch_bounds__(kApplyThreads) sur_apply_kernel(float *__restr
             }
         }
     }
-    stage_columns<kApplyThreads, kTS>(tile, fld, r0, ncol, nx, P, plane);
+    stage_columns<kApplyThreads, kTS>(tile, fld, c0 + r0, c0 + ncol, nx, P, plane);
     __syncthreads();
     const long c = r0 + t;
     bool reject = false, ok = true;
@@ -1128,7 +1129,7 @@ __global__ void __launch_bounds__(kApplyThreads) sur_apply_kernel(float *__restr
         float *yr = ysm + t * kYS;
         float *ts = tile + t * kTS, *qs = ts + kNZ;
         for (int o = 0; o < kOut; ++o) yr[o] = fmaf(yr[o], sso[o], smo[o]);  // H_k | r_k
-        const float s = km ? km[c] : 1.f;
+        const float s = km ? km[c0 + c] : 1.f;
         // rho_vd: (A v - T*)_k = (v_k - T*_k) + a_k (v_{k-1} - v_k) + c_k (v_{k+1} - v_k)
         // with v = T* + dt r; level differences of T* first (exact in FP32
         // for neighbouring values) so that dt r never rounds against T ~ 300
@@ -1152,7 +1153,9 @@ __global__ void __launch_bounds__(kApplyThreads) sur_apply_kernel(float *__restr
         const float rvd = den > 0.f ? sqrtf(num / den) : (num == 0.f ? 0.f : INFINITY);
         const float rH = absorbed > 0.f ? fabsf(sumH - absorbed) / absorbed : (sumH == 0.f ? 0.f : INFINITY);
         reject = !(finite && rvd <= tol && rH <= tol);
-        if (!reject) {
+        if (count_only) {
+            // acceptance probe: the verdict alone
+        } else if (!reject) {
             for (int k = 0; k < kNZ; ++k) ts[k] = ts[k] + dt * (yr[kNZ + k] + yr[k]);
         } else {
             // exact column: forward elimination (c'_k, d'_k in the row's
@@ -1179,10 +1182,12 @@ __global__ void __launch_bounds__(kApplyThreads) sur_apply_kernel(float *__restr
     const int nrej = __syncthreads_count(reject);
     if (!__syncthreads_and(ok) && t == 0) atomicOr(status, ST_NONFINITE);
     if (t == 0 && nrej) atomicAdd(n_fallback, (unsigned long long)nrej);
+    if (count_only) return;
     const int u = t % kSB, half = t / kSB;
     const long cu = r0 + u;
     if (cu < ncol) {
-        const int j = (int)(cu / nx), i = (int)(cu - (long)j * nx);
+        const long cg = c0 + cu;
+        const int j = (int)(cg / nx), i = (int)(cg - (long)j * nx);
         float *col = fld + (size_t)(j + 1) * P + i + kGhostX;
         const float *ts = tile + u * kTS;
 #pragma unroll 4
@@ -1198,7 +1203,10 @@ __global__ void __launch_bounds__(kApplyThreads) sur_apply_kernel(float *__restr
     }
 }
 
+static void free_policy(wx_ctx *c);
+
 void free_surrogate(wx_ctx *c) {
+    free_policy(c);
     for (void *p : {c->sur_X, c->sur_H[0], c->sur_H[1], (void *)c->sur_Y, (void *)c->sur_lev, (void *)c->sur_nfb})
         if (p) cudaFree(p);
     c->sur_X = c->sur_H[0] = c->sur_H[1] = nullptr;
@@ -1208,58 +1216,33 @@ void free_surrogate(wx_ctx *c) {
     c->sur_rows = 0;
 }
 
-int launch_surrogate_step(wx_ctx *c, cudaStream_t s, long *launches) {
+// The network on the raster columns [c0, c0 + ncol) of state buffer f,
+// which holds T* and q* there: features, the four GEMMs, the residual
+// checks.  count_only counts the rejected columns into *counter and writes
+// nothing; otherwise accepted predictions and exact fallbacks become
+// T^{n+1} and *counter counts the fallbacks.
+static int run_network(wx_ctx *c, float *f, long c0, long ncol, bool count_only, unsigned long long *counter,
+                       cudaStream_t s, long *launches) {
     wx_mlp *m = c->sur;
-    if (c->sur_gen != c->generation) {
-        // per-level feature inputs from this context's parameters
-        std::vector<float> lev(2 * kNZ);
-        for (int k = 0; k < kNZ; ++k) {
-            lev[k] = (float)c->kappa_lev[k];
-            lev[kNZ + k] = (float)(c->alpha[k] * c->dz[k]);
-        }
-        cudaError_t e = cudaMemcpy(c->sur_lev, lev.data(), lev.size() * 4, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) {
-            c->err = std::string("surrogate levels: ") + cudaGetErrorString(e);
-            return WX_ECUDA;
-        }
-        c->sur_gen = c->generation;
-    }
-    // 1. dynamics only: T*, q* land in the new buffer (which becomes current)
-    const unsigned saved = c->flags;
-    c->flags = saved & WX_ADVECTION;
-    int rc = launch_step(c, s, launches);
-    c->flags = saved;
-    if (rc != WX_OK) return rc;
-    float *f = reinterpret_cast<float *>(c->fld[c->cur]);
-    const long ncol = (long)c->nx * c->ny, rows = c->sur_rows;
-    cudaMemsetAsync(c->sur_nfb, 0, sizeof(unsigned long long), s);
-    // 2. features
-    sur_features_kernel<<<(unsigned)((rows + kSB - 1) / kSB), kFeatThreads, 0, s>>>(f, c->nx, c->P, c->R, (const float *)c->kmult,
-                                                               c->sur_lev, m->norm,
-                                                               reinterpret_cast<__nv_bfloat16 *>(c->sur_X), ncol, rows);
-    // 3. the network (persistent GEMMs over all rows)
+    const long rows = (ncol + 127) / 128 * 128;
+    cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    sur_features_kernel<<<(unsigned)((rows + kSB - 1) / kSB), kFeatThreads, 0, s>>>(
+        f, c->nx, c->P, c->R, (const float *)c->kmult, c->sur_lev, m->norm,
+        reinterpret_cast<__nv_bfloat16 *>(c->sur_X), ncol, rows, c0);
     std::string err;
-    const long chunk = rows;
-    for (long r0 = 0; r0 < rows; r0 += chunk) {
-        const int M = (int)std::min(chunk, rows - r0);
-        const __nv_bfloat16 *X = reinterpret_cast<const __nv_bfloat16 *>(c->sur_X) + r0 * kXW;
-        __nv_bfloat16 *H0 = reinterpret_cast<__nv_bfloat16 *>(c->sur_H[0]) + r0 * kHid;
-        __nv_bfloat16 *H1 = reinterpret_cast<__nv_bfloat16 *>(c->sur_H[1]) + r0 * kHid;
-        rc = gemm(X, m->Wb[0], M, kHid, kXW, EPI_GELU, m->b[0], nullptr, H0, nullptr, c->d_status, s, err);
-        if (rc == WX_OK)
-            rc = gemm(H0, m->Wb[1], M, kHid, kHid, EPI_GELU, m->b[1], nullptr, H1, nullptr, c->d_status, s, err);
-        if (rc == WX_OK)
-            rc = gemm(H1, m->Wb[2], M, kHid, kHid, EPI_GELU, m->b[2], nullptr, H0, nullptr, c->d_status, s, err);
-        if (rc == WX_OK)
-            rc = gemm(H0, m->Wb[3], M, kOutP, kHid, EPI_F32, m->b[3], nullptr, c->sur_Y + r0 * kOutP, nullptr,
-                      c->d_status, s, err);
-        if (rc != WX_OK) {
-            c->err = err;
-            return rc;
-        }
-        *launches += 4;
+    const int M = (int)rows;
+    const __nv_bfloat16 *X = reinterpret_cast<const __nv_bfloat16 *>(c->sur_X);
+    __nv_bfloat16 *H0 = reinterpret_cast<__nv_bfloat16 *>(c->sur_H[0]);
+    __nv_bfloat16 *H1 = reinterpret_cast<__nv_bfloat16 *>(c->sur_H[1]);
+    int rc = gemm(X, m->Wb[0], M, kHid, kXW, EPI_GELU, m->b[0], nullptr, H0, nullptr, c->d_status, s, err);
+    if (rc == WX_OK) rc = gemm(H0, m->Wb[1], M, kHid, kHid, EPI_GELU, m->b[1], nullptr, H1, nullptr, c->d_status, s, err);
+    if (rc == WX_OK) rc = gemm(H1, m->Wb[2], M, kHid, kHid, EPI_GELU, m->b[2], nullptr, H0, nullptr, c->d_status, s, err);
+    if (rc == WX_OK)
+        rc = gemm(H0, m->Wb[3], M, kOutP, kHid, EPI_F32, m->b[3], nullptr, c->sur_Y, nullptr, c->d_status, s, err);
+    if (rc != WX_OK) {
+        c->err = err;
+        return rc;
     }
-    // 4. residual checks, fallback, T^{n+1}
     constexpr int apply_smem = kSB * (kTS + kYS) * (int)sizeof(float);
     {   // a per-device function attribute: set on every launch (cheap)
         cudaError_t e = cudaFuncSetAttribute(sur_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, apply_smem);
@@ -1270,14 +1253,147 @@ int launch_surrogate_step(wx_ctx *c, cudaStream_t s, long *launches) {
     }
     sur_apply_kernel<<<(unsigned)((ncol + kSB - 1) / kSB), kApplyThreads, apply_smem, s>>>(
         f, c->nx, c->ny, c->P, c->R, (const float *)c->kmult, (const Q4<float> *)c->tab, c->sur_Y, m->norm,
-        (float)c->dt, (float)c->S0, (float)c->sur_tol, ncol, c->sur_nfb, c->d_status);
-    *launches += 2;
+        (float)c->dt, (float)c->S0, (float)c->sur_tol, ncol, counter, c->d_status, c0, count_only ? 1 : 0);
+    *launches += 6;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         c->err = std::string("surrogate kernels: ") + cudaGetErrorString(e);
         return WX_ECUDA;
     }
     return WX_OK;
+}
+
+static int surrogate_levels(wx_ctx *c) {
+    if (c->sur_gen == c->generation) return WX_OK;
+    // per-level feature inputs from this context's parameters
+    std::vector<float> lev(2 * kNZ);
+    for (int k = 0; k < kNZ; ++k) {
+        lev[k] = (float)c->kappa_lev[k];
+        lev[kNZ + k] = (float)(c->alpha[k] * c->dz[k]);
+    }
+    cudaError_t e = cudaMemcpy(c->sur_lev, lev.data(), lev.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        c->err = std::string("surrogate levels: ") + cudaGetErrorString(e);
+        return WX_ECUDA;
+    }
+    c->sur_gen = c->generation;
+    return WX_OK;
+}
+
+int launch_surrogate_step(wx_ctx *c, cudaStream_t s, long *launches) {
+    int rc = surrogate_levels(c);
+    if (rc != WX_OK) return rc;
+    // 1. dynamics only: T*, q* land in the new buffer (which becomes current)
+    const unsigned saved = c->flags;
+    c->flags = saved & WX_ADVECTION;
+    rc = launch_step(c, s, launches);
+    c->flags = saved;
+    if (rc != WX_OK) return rc;
+    // 2. features, the network, residual checks, fallback, T^{n+1}
+    return run_network(c, reinterpret_cast<float *>(c->fld[c->cur]), 0, (long)c->nx * c->ny, false, c->sur_nfb, s,
+                       launches);
+}
+
+// ------------------------------------------------- the acceptance policy
+void reset_surrogate_policy(wx_ctx *c) {
+    for (const auto &r : c->sur_reads) cudaEventSynchronize(c->sur_ev[r.slot]);
+    c->sur_reads.clear();
+    c->sur_mode = 0;
+    c->sur_last_exact = false;
+    c->sur_step = c->sur_next_probe = 0;
+    c->sur_probe_row0 = 0;
+}
+
+static void free_policy(wx_ctx *c) {
+    reset_surrogate_policy(c);
+    for (auto &ev : c->sur_ev)
+        if (ev) {
+            cudaEventDestroy(ev);
+            ev = nullptr;
+        }
+    if (c->sur_host) cudaFreeHost(c->sur_host);
+    c->sur_host = nullptr;
+}
+
+// The counts of the steps up to `upto` decide the mode: network steps while
+// the acceptance is at least the policy's minimum, exact steps otherwise.
+static int resolve_reads(wx_ctx *c, long long upto, long long now) {
+    while (!c->sur_reads.empty() && c->sur_reads.front().step <= upto) {
+        const wx_ctx::SurRead r = c->sur_reads.front();
+        c->sur_reads.erase(c->sur_reads.begin());
+        if (cudaEventSynchronize(c->sur_ev[r.slot]) != cudaSuccess) {
+            c->err = "surrogate policy: reading an acceptance count failed";
+            return WX_ECUDA;
+        }
+        const double accept = 1.0 - (double)c->sur_host[r.slot] / (double)r.ncols;
+        if (accept >= c->sur_min_accept) {
+            c->sur_mode = 0;
+        } else if (c->sur_mode == 0) {
+            c->sur_mode = 1;
+            c->sur_next_probe = now + c->sur_probe_every;
+        }
+    }
+    return WX_OK;
+}
+
+static int record_count(wx_ctx *c, long long step, long ncols, const unsigned long long *counter, cudaStream_t s) {
+    if ((int)c->sur_reads.size() >= wx_ctx::kSurRing) {
+        const int rc = resolve_reads(c, c->sur_reads.front().step, step);
+        if (rc != WX_OK) return rc;
+    }
+    const int slot = c->sur_slot;
+    c->sur_slot = (slot + 1) % wx_ctx::kSurRing;
+    if (cudaMemcpyAsync(&c->sur_host[slot], counter, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaEventRecord(c->sur_ev[slot], s) != cudaSuccess) {
+        c->err = "surrogate policy: enqueueing an acceptance count failed";
+        return WX_ECUDA;
+    }
+    c->sur_reads.push_back({step, ncols, slot});
+    return WX_OK;
+}
+
+int launch_surrogate_policy_step(wx_ctx *c, cudaStream_t s, long *launches) {
+    if (c->sur_min_accept <= 0.0) {  // no policy: the network runs every step
+        c->sur_last_exact = false;
+        return launch_surrogate_step(c, s, launches);
+    }
+    if (!c->sur_host) {
+        bool ok = cudaHostAlloc((void **)&c->sur_host, wx_ctx::kSurRing * sizeof(unsigned long long),
+                                cudaHostAllocDefault) == cudaSuccess;
+        for (auto &ev : c->sur_ev) ok = ok && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            free_policy(c);
+            c->err = "surrogate policy: pinned count buffer or events unavailable";
+            return WX_ENOMEM;
+        }
+    }
+    const long long n = c->sur_step;
+    int rc = resolve_reads(c, n - 2, n);
+    if (rc != WX_OK) return rc;
+    c->sur_step = n + 1;
+    if (c->sur_mode == 0) {
+        c->sur_last_exact = false;
+        rc = launch_surrogate_step(c, s, launches);
+        return rc == WX_OK ? record_count(c, n, (long)c->nx * c->ny, c->sur_nfb, s) : rc;
+    }
+    // exact step: the fused kernel with the column physics
+    c->sur_last_exact = true;
+    rc = launch_step(c, s, launches);
+    if (rc != WX_OK || n < c->sur_next_probe) return rc;
+    // probe: the network on a band of rows of the new state, verdicts only
+    rc = surrogate_levels(c);
+    if (rc != WX_OK) return rc;
+    const int rows = std::min(c->sur_probe_rows, c->ny);
+    int j0 = c->sur_probe_row0;
+    if (j0 + rows > c->ny) j0 = 0;
+    c->sur_probe_row0 = (j0 + rows) % c->ny;
+    c->sur_next_probe = n + c->sur_probe_every;
+    const long ncol = (long)rows * c->nx;
+    rc = run_network(c, reinterpret_cast<float *>(c->fld[c->cur]), (long)j0 * c->nx, ncol, true, c->sur_nfb + 1, s,
+                     launches);
+    return rc == WX_OK ? record_count(c, n, ncol, c->sur_nfb + 1, s) : rc;
 }
 
 }  // namespace wx
@@ -1303,8 +1419,8 @@ extern "C" int wx_set_surrogate(wx_ctx *c, wx_mlp *m, double fallback_tol) {
               cudaMalloc(&c->sur_H[1], rows * kHid * 2) == cudaSuccess &&
               cudaMalloc((void **)&c->sur_Y, rows * kOutP * 4) == cudaSuccess &&
               cudaMalloc((void **)&c->sur_lev, 2 * kNZ * 4) == cudaSuccess &&
-              cudaMalloc((void **)&c->sur_nfb, sizeof(unsigned long long)) == cudaSuccess &&
-              cudaMemset(c->sur_nfb, 0, sizeof(unsigned long long)) == cudaSuccess;
+              cudaMalloc((void **)&c->sur_nfb, 2 * sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMemset(c->sur_nfb, 0, 2 * sizeof(unsigned long long)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_surrogate(c);
@@ -1330,6 +1446,20 @@ extern "C" int wx_surrogate_fallbacks(wx_ctx *c, long *n_fallback) {
         c->err = "wx_surrogate_fallbacks: device error";
         return WX_ECUDA;
     }
-    *n_fallback = (long)n;
+    // an exact step (the policy skipped the network) computed every column exactly
+    *n_fallback = c->sur_last_exact ? (long)c->nx * c->ny : (long)n;
+    return WX_OK;
+}
+
+extern "C" int wx_set_surrogate_policy(wx_ctx *c, double min_accept, int probe_every, int probe_rows) {
+    if (!c) return WX_EINVAL;
+    if (!(min_accept >= 0.0 && min_accept <= 1.0) || probe_every < 1 || probe_rows < 1) {
+        c->err = "wx_set_surrogate_policy: min_accept in [0, 1], probe_every >= 1, probe_rows >= 1";
+        return WX_EINVAL;
+    }
+    reset_surrogate_policy(c);
+    c->sur_min_accept = min_accept;
+    c->sur_probe_every = probe_every;
+    c->sur_probe_rows = probe_rows;
     return WX_OK;
 }

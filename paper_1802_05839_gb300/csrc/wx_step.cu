@@ -120,10 +120,14 @@ __device__ __forceinline__ void consumer_sync(int nthreads) {
 // and pulls slabs PF stages ahead into L2, so the next tile's loads overlap
 // the current tile's stores.  KMODE 0: kappa_mult = 1 everywhere (the
 // elimination coefficients come from the table); KMODE 1: per-column
-// kappa_mult, eliminated on the fly.
-template <typename T, int TY, int KB, int KMODE, bool PHYS, bool SUMS>
+// kappa_mult, eliminated on the fly; KMODE 2: table path, listed columns
+// parked for the side solve.  TMF: the column state F_k lives in each
+// lane's TMEM row instead of shared memory (FP32, nz <= 64), which leaves
+// room for twelve consumer warps and a six-stage ring on one SM.
+template <typename T, int TY, int KB, int KMODE, bool PHYS, bool SUMS, bool TMF>
 __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_constant__ Members<T> ms, const int S,
                                                              const int PF) {
+    static_assert(!TMF || (std::is_same<T, float>::value && KMODE != 1), "TMEM column state: FP32 table paths");
     using PK = Pk<T>;
     using V = typename PK::V;
     using R4 = Q4<T>;
@@ -132,7 +136,7 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
     extern __shared__ __align__(128) unsigned char smem[];
 
     const int tx = threadIdx.x, wy = threadIdx.y;
-    const SmemPlan pl = plan_smem(ms.nz_max, TY, S, KB, (int)sizeof(T), KMODE == 1);  // e_k per column
+    const SmemPlan pl = plan_smem(ms.nz_max, TY, S, KB, (int)sizeof(T), KMODE == 1, TMF);  // e_k per column
     R4 *tab = reinterpret_cast<R4 *>(smem + pl.tab_off);
     T *ring = reinterpret_cast<T *>(smem + pl.ring_off);
     V *stF = reinterpret_cast<V *>(smem + pl.state_off);  // [nz][NT] F of the 2 columns
@@ -150,6 +154,7 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
     };
 
     const int tid_all = tx + 32 * wy;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(empty + S);  // TMEM base address
     if (tid_all == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
@@ -157,7 +162,16 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
         }
         fence_mbar_init();
     }
+    if (TMF && wy == 0) {  // the column state of every consumer lane lives in TMEM
+        tmem_alloc(tslot, kTmemCols(TY));
+        tmem_relinquish();
+    }
+    if (TMF) tc_fence_before();
     __syncthreads();
+    if (TMF) tc_fence_after();
+    // this thread's lane (its warp's lane quarter) and column group in TMEM:
+    // warps w and w + 4 share a quarter and take 128 columns each
+    const uint32_t trow = TMF ? *tslot + ((uint32_t)(32 * (wy & 3)) << 16) + ((uint32_t)(wy >> 2) << 7) : 0u;
 
     // ---------------- producer warp: stage g of a tile covers planes
     // z0 = nz - (g+1)*KB .. z0+KB-1, top of the column first
@@ -322,7 +336,13 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
         V chk = PK::dup(T(0));
         ColSum2<T> sumQ, sumT;
         T *qp = a.out + fld + (size_t)(j + 1) * a.P + (i0 + kGhostX) + (size_t)(nz - 1) * lev;  // q, top
-        V *Fp = stF + (nz - 1) * NT + tid;                                                     // F, top
+        // F_k of the lane's two columns: its TMEM lane, or shared memory
+        auto putF = [&](int k, V v) {
+            if constexpr (TMF)
+                tmem_st2(trow + 2 * k, v.x, v.y);
+            else
+                stF[k * NT + tid] = v;
+        };
 
         // phi* for one field at level k: two short FMA chains, summed
         auto stencil = [&](const T *pf, V cur, V prv, V nxt, V cCk, V wu, V wd) -> V {
@@ -418,14 +438,13 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
                     }
                 }
                 // F_{k+1} = f_{k+1} + h_{k+1} + e_{k+1} h_k  (complete now)
-                if (k + 1 < nz) Fp[NT] = PK::fma(e_up, hk, PK::add(f_up, h_up));
+                if (k + 1 < nz) putF(k + 1, PK::fma(e_up, hk, PK::add(f_up, h_up)));
                 f_up = fk;
                 h_up = hk;
                 e_up = ek;
             } else {
-                *Fp = Ts;
+                putF(k, Ts);
             }
-            Fp -= NT;
         };
 
         // stage g holds levels z0 .. z0+KB-1 (sub-planes 0..KB-1), z0 =
@@ -464,41 +483,36 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
             run_pass1(std::true_type{});
         else
             run_pass1(std::false_type{});
-        if (PHYS) stF[tid] = PK::add(f_up, h_up);  // F_0 = f_0 + h_0
+        if (PHYS) putF(0, PK::add(f_up, h_up));  // F_0 = f_0 + h_0
 
         // ------------- pass 2 (bottom up): T^{n+1}_k = F_k - e_k T^{n+1}_{k-1}
         V Tprev = PK::dup(T(0));
-        if (!edge) {
-            T *tp = a.out + (size_t)(j + 1) * a.P + (i0 + kGhostX);  // T plane, level 0
-#pragma unroll 4
-            for (int k = 0; k < nz; ++k) {
-                const R4 Fr = tF[k];
-                V tn = stF[k * NT + tid];
-                if (PHYS) {
-                    const V ne = (KMODE != 1) ? V{Fr.x, Fr.y} : stE[k * NT + tid];
-                    tn = PK::fma(ne, Tprev, tn);
-                    Tprev = tn;
-                }
-                *reinterpret_cast<V *>(tp) = tn;
-                tp += lev;
+        T *tp = a.out + (size_t)(j + 1) * a.P + (i0 + kGhostX);  // T plane, level 0
+        // listed columns (KMODE 2 with physics) are finished by the side
+        // solve, which sums their final T itself: their table-path T stays
+        // out of the sums
+        constexpr bool SIDE = KMODE == 2 && PHYS;
+        const V lmask = V{(SIDE && fl[0] >= 0) ? T(0) : T(1), (SIDE && fl[1] >= 0) ? T(0) : T(1)};
+        auto back = [&](auto edge_tag, int k, V tn) {
+            constexpr bool EDGE = decltype(edge_tag)::value;
+            const R4 Fr = tF[k];
+            if (PHYS) {
+                const V ne = (KMODE != 1) ? V{Fr.x, Fr.y} : stE[k * NT + tid];
+                tn = PK::fma(ne, Tprev, tn);
+                Tprev = tn;
+            }
+            if (!EDGE) {
+                *reinterpret_cast<V *>(tp + (size_t)k * lev) = tn;
                 if (SUMS)
-                    sumT.add(tn, Fr.z, Fr.w);
+                    sumT.add(SIDE ? PK::mul(tn, lmask) : tn, Fr.z, Fr.w);
                 else
                     chk = PK::add(chk, tn);
+                return;
             }
-        } else {
-            for (int k = 0; k < nz; ++k) {
-                const R4 Fr = tF[k];
-                V tn = stF[k * NT + tid];
-                if (PHYS) {
-                    const V ne = (KMODE != 1) ? V{Fr.x, Fr.y} : stE[k * NT + tid];
-                    tn = PK::fma(ne, Tprev, tn);
-                    Tprev = tn;
-                }
-                T *row = a.out + k * lev + (size_t)(j + 1) * a.P;
-                if (va) row[i0 + kGhostX] = tn.x;
-                if (vb) row[i0 + 1 + kGhostX] = tn.y;
-                if (!a.halo) {
+            T *row = a.out + k * lev + (size_t)(j + 1) * a.P;
+            if (va) row[i0 + kGhostX] = tn.x;
+            if (vb) row[i0 + 1 + kGhostX] = tn.y;
+            if (!a.halo) {
                 if (va && i0 == 0) row[kGhostX + nx] = tn.x;
                 if (vb && i0 + 1 == nx - 1) row[kGhostX - 1] = tn.y;
                 if (va && i0 == nx - 1) row[kGhostX - 1] = tn.x;
@@ -512,20 +526,39 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
                     if (va) g[i0 + kGhostX] = tn.x;
                     if (vb) g[i0 + 1 + kGhostX] = tn.y;
                 }
-                }
-                const V tm = V{va ? tn.x : T(0), vb ? tn.y : T(0)};
-                if (SUMS)
-                    sumT.add(tm, Fr.z, Fr.w);
-                else
-                    chk = PK::add(chk, tm);
             }
-        }
+            const V tm = V{va ? tn.x : T(0), vb ? tn.y : T(0)};
+            if (SUMS)
+                sumT.add(SIDE ? PK::mul(tm, lmask) : tm, Fr.z, Fr.w);
+            else
+                chk = PK::add(chk, tm);
+        };
+        auto run_pass2 = [&](auto edge_tag) {
+            if constexpr (TMF) {
+                // F of 8 levels per TMEM load (16 columns of the lane)
+                tmem_wait_st();
+                for (int k0 = 0; k0 < nz; k0 += 8) {
+                    float fv[16];
+                    tmem_ld16(trow + 2 * k0, fv);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (k0 + u < nz) back(edge_tag, k0 + u, V{fv[2 * u], fv[2 * u + 1]});
+                }
+            } else {
+#pragma unroll 4
+                for (int k = 0; k < nz; ++k) back(edge_tag, k, stF[k * NT + tid]);
+            }
+        };
+        if (edge)
+            run_pass2(std::true_type{});
+        else
+            run_pass2(std::false_type{});
 
         if (SUMS) {
             double mT = sumT.total(va, vb), mQ = sumQ.total(va, vb);
             if ((va || vb) && (!isfinite(mT) || !isfinite(mQ))) atomicOr(a.status, ST_NONFINITE);
             // deterministic per-tile reduction: warp tree, then warps in order
-            __shared__ double red[2 * 8];
+            __shared__ double red[2 * TY];
             mT = warp_sum(mT);
             mQ = warp_sum(mQ);
             if (tx == 0) {
@@ -548,6 +581,12 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
         }
     }
     if (!ok && tx == 0) atomicOr(ms.status, ST_TIMEOUT);
+    if constexpr (TMF) {  // every consumer is done with its lane: free the columns
+        tc_fence_before();
+        consumer_sync(NT);
+        tc_fence_after();
+        if (wy == 0) tmem_dealloc(*tslot, kTmemCols(TY));
+    }
 }
 
 // Fixed-order FP64 reduction of the per-tile partials (and of the side
@@ -758,13 +797,24 @@ int launch_columns(wx_ctx *c, const void *Ts, const void *qs, const void *km, vo
 // storage with kappa_mult eliminates per column on the fly.
 static bool mixed(const wx_ctx *c) { return (c->dtype == WX_MIXED || c->dtype == WX_F32) && c->n_list > 0; }
 static bool per_col(const wx_ctx *c) { return c->kmult != nullptr && c->dtype == WX_F64; }
+// The TMEM column-state variant: FP32 storage (table paths) with columns of
+// at most kTmemMaxNz levels, at the tile heights it is built for.
+static bool tmem_nz(int t_bytes, int nz, bool pc) { return t_bytes == 4 && !pc && nz <= kTmemMaxNz; }
+static bool tmem_shape(int ty, int kb) { return ty == 12 && kb == 4; }
+static bool use_tmem(const wx_ctx *c, const StepCfg &g) {
+    return tmem_nz(c->t_bytes, c->nz, per_col(c)) && tmem_shape(g.ty, g.kb);
+}
 
 bool cfg_fits(const wx_ctx *c, const StepCfg &cfg, int *smem_bytes) {
-    const SmemPlan p = plan_smem(c->nz, cfg.ty, cfg.stages, cfg.kb, c->t_bytes, per_col(c));
+    const bool tm = use_tmem(c, cfg);
+    const SmemPlan p = plan_smem(c->nz, cfg.ty, cfg.stages, cfg.kb, c->t_bytes, per_col(c), tm);
     if (smem_bytes) *smem_bytes = p.total;
-    // the per-SM budget: ctas_per_sm CTAs plus 1 KB runtime reserve each
+    if (cfg.ty == 12 && !tm) return false;  // twelve-row tiles exist with TMEM column state only
+    // the per-SM budget: ctas_per_sm CTAs plus 1 KB runtime reserve each;
+    // with TMEM column state, their columns within the SM's 512
     return cfg.stages >= 3 && (cfg.kb == 2 || cfg.kb == 4) && cfg.ctas_per_sm >= 1 && p.total <= 227 * 1024 &&
-           cfg.ctas_per_sm * (p.total + 1024) <= 228 * 1024;
+           cfg.ctas_per_sm * (p.total + 1024) <= 228 * 1024 &&
+           (!tm || cfg.ctas_per_sm * (int)kTmemCols(cfg.ty) <= 512);
 }
 
 StepCfg default_cfg(const wx_ctx *c) {
@@ -778,7 +828,8 @@ StepCfg default_cfg(const wx_ctx *c) {
     best.ctas_per_sm = 1;
     long best_score = -1;
     for (int kb : {2, 4}) {
-        for (int ty : {1, 2, 4, 8}) {
+        for (int ty : {1, 2, 4, 8, 12}) {
+            if (ty == 12 && !tmem_nz(c->t_bytes, c->nz, per_col(c))) continue;
             for (int st = 8; st >= 3; --st) {
                 StepCfg g;
                 g.ty = ty;
@@ -788,7 +839,9 @@ StepCfg default_cfg(const wx_ctx *c) {
                 g.ctas_per_sm = 1;
                 if (!cfg_fits(c, g, &bytes)) continue;
                 g.ctas_per_sm = std::min(228 * 1024 / (bytes + 1024), 2048 / (32 * (ty + 1)));
+                if (use_tmem(c, g)) g.ctas_per_sm = std::min(g.ctas_per_sm, 512 / (int)kTmemCols(ty));
                 const int warps = std::min(g.ctas_per_sm * ty, 16);
+                if (!cfg_fits(c, g, nullptr)) continue;
                 const long box = (long)kb * 2 * (ty + 2) * kBoxX * c->t_bytes;  // both fields
                 const long score = ((box >= 16384) ? 1L << 40 : 0) + ((long)warps << 20) + ((long)ty << 10) + st;
                 if (score > best_score) {
@@ -837,10 +890,10 @@ template <typename T> static void fill_member(const wx_ctx *c, Member<T> &M, lon
     M.gy = (c->ny + ty - 1) / ty;
 }
 
-template <typename T, int TY, int KB, int KMODE, bool PHYS, bool SUMS>
+template <typename T, int TY, int KB, int KMODE, bool PHYS, bool SUMS, bool TMF>
 static int launch_batch_t(wx_ctx *const *mem, int n, const StepCfg &cfg, int num_sms, unsigned *status,
                           cudaStream_t s, std::string &err) {
-    auto kern = step_kernel<T, TY, KB, KMODE, PHYS, SUMS>;
+    auto kern = step_kernel<T, TY, KB, KMODE, PHYS, SUMS, TMF>;
     Members<T> ms;
     long total = 0;
     int nz_max = 1;
@@ -853,13 +906,22 @@ static int launch_batch_t(wx_ctx *const *mem, int n, const StepCfg &cfg, int num
     ms.nz_max = nz_max;
     ms.total = total;
     ms.status = status;
-    const SmemPlan pl = plan_smem(nz_max, TY, cfg.stages, KB, (int)sizeof(T), KMODE == 1);
+    const SmemPlan pl = plan_smem(nz_max, TY, cfg.stages, KB, (int)sizeof(T), KMODE == 1, TMF);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.total);
     if (e != cudaSuccess) {
         err = std::string("smem attr: ") + cudaGetErrorString(e);
         return WX_ECUDA;
     }
-    const long resident = (long)num_sms * cfg.ctas_per_sm;
+    // persistent CTAs: no more than fit on the SMs at once (registers,
+    // shared memory, TMEM columns)
+    int fit = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kern, 32 * (TY + 1), pl.total);
+    if (e != cudaSuccess || fit < 1) {
+        err = std::string("step kernel occupancy: ") + (e != cudaSuccess ? cudaGetErrorString(e) : "no CTA fits");
+        return WX_ECUDA;
+    }
+    if (TMF) fit = std::min(fit, 512 / (int)kTmemCols(TY));
+    const long resident = (long)num_sms * std::min(cfg.ctas_per_sm, fit);
     dim3 grid((unsigned)std::max(1L, std::min(total, resident)));
     dim3 block(32, TY + 1);
     kern<<<grid, block, pl.total, s>>>(ms, cfg.stages, cfg.prefetch);
@@ -874,14 +936,21 @@ static int launch_batch_t(wx_ctx *const *mem, int n, const StepCfg &cfg, int num
 template <typename T, int KMODE, bool PHYS, bool SUMS>
 static int dispatch_ty(wx_ctx *const *mem, int n, const StepCfg &cfg, int sms, unsigned *st, cudaStream_t s,
                        std::string &err) {
+    int nz_max = 1;
+    for (int i = 0; i < n; ++i) nz_max = std::max(nz_max, mem[i]->nz);
+    if constexpr (std::is_same<T, float>::value && KMODE != 1) {
+        if (tmem_nz(4, nz_max, false) && tmem_shape(cfg.ty, cfg.kb)) {
+            return launch_batch_t<T, 12, 4, KMODE, PHYS, SUMS, true>(mem, n, cfg, sms, st, s, err);
+        }
+    }
     switch (cfg.ty * 10 + cfg.kb) {
-        case 12: return launch_batch_t<T, 1, 2, KMODE, PHYS, SUMS>(mem, n, cfg, sms, st, s, err);
-        case 22: return launch_batch_t<T, 2, 2, KMODE, PHYS, SUMS>(mem, n, cfg, sms, st, s, err);
-        case 42: return launch_batch_t<T, 4, 2, KMODE, PHYS, SUMS>(mem, n, cfg, sms, st, s, err);
-        case 82: return launch_batch_t<T, 8, 2, KMODE, PHYS, SUMS>(mem, n, cfg, sms, st, s, err);
-        case 24: return launch_batch_t<T, 2, 4, KMODE, PHYS, SUMS>(mem, n, cfg, sms, st, s, err);
-        case 44: return launch_batch_t<T, 4, 4, KMODE, PHYS, SUMS>(mem, n, cfg, sms, st, s, err);
-        case 84: return launch_batch_t<T, 8, 4, KMODE, PHYS, SUMS>(mem, n, cfg, sms, st, s, err);
+        case 12: return launch_batch_t<T, 1, 2, KMODE, PHYS, SUMS, false>(mem, n, cfg, sms, st, s, err);
+        case 22: return launch_batch_t<T, 2, 2, KMODE, PHYS, SUMS, false>(mem, n, cfg, sms, st, s, err);
+        case 42: return launch_batch_t<T, 4, 2, KMODE, PHYS, SUMS, false>(mem, n, cfg, sms, st, s, err);
+        case 82: return launch_batch_t<T, 8, 2, KMODE, PHYS, SUMS, false>(mem, n, cfg, sms, st, s, err);
+        case 24: return launch_batch_t<T, 2, 4, KMODE, PHYS, SUMS, false>(mem, n, cfg, sms, st, s, err);
+        case 44: return launch_batch_t<T, 4, 4, KMODE, PHYS, SUMS, false>(mem, n, cfg, sms, st, s, err);
+        case 84: return launch_batch_t<T, 8, 4, KMODE, PHYS, SUMS, false>(mem, n, cfg, sms, st, s, err);
         default: err = "unsupported tile rows / planes per stage"; return WX_EUNSUPPORTED;
     }
 }
@@ -908,7 +977,9 @@ static int dispatch_kmode(wx_ctx *const *mem, int n, const StepCfg &cfg, int sms
         if (any) return dispatch_flags<T, 2>(mem, n, cfg, sms, st, s, err);
     }
     if (!per_col(mem[0])) return dispatch_flags<T, 0>(mem, n, cfg, sms, st, s, err);
-    return dispatch_flags<T, 1>(mem, n, cfg, sms, st, s, err);
+    if constexpr (std::is_same<T, double>::value) return dispatch_flags<T, 1>(mem, n, cfg, sms, st, s, err);
+    err = "per-column elimination is built for FP64 storage only";
+    return WX_EUNSUPPORTED;
 }
 
 // The per-member kernels that follow the step kernel: the side solve of

@@ -126,6 +126,7 @@ SIGNATURES = [
     ("wx_pf_destroy", None, [_VP]),
     ("wx_pf_last_error", ctypes.c_char_p, [_VP]),
     ("wx_surrogate_fallbacks", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_long)]),
+    ("wx_set_surrogate_policy", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
     ("wx_destroy", None, [_VP]),
     ("wx_last_error", ctypes.c_char_p, [_VP]),
 ]
@@ -379,6 +380,11 @@ class Context:
         _check(lib().wx_set_surrogate(self.ptr, mlp.ptr if mlp is not None else None,
                                       float(fallback_tol)), self.ptr)
         self._mlp = mlp
+
+    def set_surrogate_policy(self, min_accept, probe_every=8, probe_rows=16):
+        """Run the network only while its acceptance is >= min_accept (0: always)."""
+        _check(lib().wx_set_surrogate_policy(self.ptr, float(min_accept), int(probe_every), int(probe_rows)),
+               self.ptr)
 
     def surrogate_fallbacks(self):
         n = ctypes.c_long()

@@ -103,6 +103,82 @@ def test_fallback_strong_physics_increments(near_singular):
     net.close()
 
 
+def test_policy_steps_exactly_while_the_network_declines():
+    """Acceptance policy (min_accept 0.5): every column falls back (tol 0),
+    so after the two steps the decision lags, steps run the fused exact
+    step (1 launch), plus a probe of the network on 8 rows every 4 steps
+    (6 more launches); every step stays within the FP32 bars of the
+    oracle's step from the same state."""
+    c = case(seed=5)
+    net = random_net(c)
+    ctx = ctx_for(c, net, tol=0.0)
+    ctx.set_surrogate_policy(0.5, probe_every=4, probe_rows=8)
+    launches = []
+    Tp, qp = c.T, c.q
+    for s in range(9):
+        ctx.step(1)
+        ctx.sync()
+        launches.append(ctx.last_launches())
+        assert ctx.surrogate_fallbacks() == c.nx * c.ny
+        Tg, qg = ctx.read_fields()
+        To, qo = oracle.step(c, Tp, qp, c.U, c.V)
+        assert relmax(Tg, To) <= 1e-5 and relmax(qg, qo) <= 1e-5
+        Ts, _ = oracle.dynamics(c, Tp, qp, c.U, c.V)
+        assert_increments(Tp, Ts, Tg, To, what=f"policy step {s}")
+        Tp, qp = Tg, qg
+    # steps 0, 1: network (7 launches); 2 onwards exact, probes at 6 and 10, ...
+    assert launches == [7, 7, 1, 1, 1, 1, 7, 1, 1], launches
+    ctx.close()
+    net.close()
+
+
+def _policy_run(c, net):
+    ctx = ctx_for(c, net, tol=1e30)
+    ctx.set_surrogate_policy(1.0, probe_every=1, probe_rows=8)
+    launches = []
+    for _ in range(6):
+        ctx.step(1)
+        launches.append(ctx.last_launches())
+    ctx.sync()
+    out = ctx.read_fields()
+    ctx.close()
+    return launches, out
+
+
+def test_policy_probe_returns_to_the_network():
+    """A band of rows with q = 0 fails the heating residual at any
+    tolerance, so a whole-grid step accepts fewer than all columns and the
+    policy (min_accept 1.0) turns to exact steps; the probe covers rows
+    0..7, where every column is accepted, and turns it back.  The same
+    sequence of steps takes the same decisions and gives the same state."""
+    c = case(seed=6)
+    c.q[:, c.ny // 2 - 6:c.ny // 2 + 6, :] = 0.0
+    net = random_net(c, std_out=0.1)
+    la, (Ta, qa) = _policy_run(c, net)
+    lb, (Tb, qb) = _policy_run(c, net)
+    # 0, 1 network; 2 exact (decided from step 0); 3, 4 exact + probe;
+    # 5 network again (decided from the probe of step 3)
+    assert la == [7, 7, 1, 7, 7, 7], la
+    assert la == lb and np.array_equal(Ta, Tb) and np.array_equal(qa, qb)
+    net.close()
+
+
+def test_policy_arguments():
+    c = case(nx=20, ny=16)
+    net = random_net(c)
+    ctx = ctx_for(c, net, tol=2e-2)
+    for bad in ((-0.1, 8, 16), (1.5, 8, 16), (0.5, 0, 16), (0.5, 8, 0)):
+        with pytest.raises(wx.WxError) as e:
+            ctx.set_surrogate_policy(*bad)
+        assert e.value.code == -1
+    ctx.set_surrogate_policy(0.0)  # off: the network runs on every step
+    ctx.step(2)
+    ctx.sync()
+    assert ctx.last_launches() == 14
+    ctx.close()
+    net.close()
+
+
 def test_accepted_predictions_match_the_mlp_oracle():
     c = case(seed=4)
     net = random_net(c, seed=12)
