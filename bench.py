@@ -599,12 +599,13 @@ def variant_ablation(steps=100):
 
 
 def variant_rk3(steps_f32=100, steps_f64=20, nx=1581, ny=1301, nz=58):
-    """WX_RK3 at the paper grid: three stage launches of the step kernel
-    (dynamics only), the stage-2 combine and the stage-3 combine fused with
-    the column physics.  HBM bytes per cell-step it moves by design:
-    3 x 16 (stages) + 32 (combine: read phi_n, E, phi_s, write) + 32 (fused
-    combine + physics: read phi_n, E, phi_s, write T, q) = 112 in FP32,
-    twice that in FP64."""
+    """WX_RK3 at the paper grid.  FP32 (TMEM variant): three stage launches
+    of the step kernel that write their stages themselves, the last fused
+    with the column physics: 16 + 24 + 24 = 64 HBM bytes per cell-step
+    (stage 1 reads and writes T, q; stages 2 and 3 also read phi^n).  FP64:
+    three stage launches (dynamics only), the stage-2 combine and the
+    stage-3 combine fused with the column physics: 3 x 16 + 32 + 32 = 112
+    bytes in FP32 units, 224 in FP64."""
     import torch
     from paper_1802_05839_gb300 import wx
     out = {}
@@ -618,7 +619,7 @@ def variant_rk3(steps_f32=100, steps_f64=20, nx=1581, ny=1301, nz=58):
         ctx.sync()
         launches = ctx.last_launches()
         ctx.close()
-        b = 112 if dtype == "f32" else 224
+        b = (64 if launches == 3 else 112) if dtype == "f32" else 224
         out[dtype] = {"ms_per_step": ms, "value": case.cells / (ms * 1e-3), "unit": "cell-steps/s",
                       "steps": steps, "gpu_launches_per_step": launches, "bytes_per_cell_step": b,
                       "hbm_frac": case.cells * b / (ms * 1e-3) / 1e9 / peaks()[0]}

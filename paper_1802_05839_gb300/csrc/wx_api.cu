@@ -73,6 +73,25 @@ int encode_tmap(wx_ctx *c, int which, int ty, int kb) {
     if (r != CUDA_SUCCESS) return fail(c, WX_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")");
     return WX_OK;
 }
+
+// The same tensor with boxes of a tile's interior: kTileX x ty x 2 fields x
+// kb planes, x start kGhostX + kTileX * bx (a multiple of 16 elements).
+int encode_tmap_interior(wx_ctx *c, int which, int ty, int kb, CUtensorMap *out) {
+    auto enc = tmap_encoder();
+    if (!enc) return fail(c, WX_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint64_t t = (cuuint64_t)c->t_bytes;
+    cuuint64_t dims[4] = {(cuuint64_t)c->P, (cuuint64_t)c->R, 2, (cuuint64_t)c->nz};
+    cuuint64_t strides[3] = {(cuuint64_t)c->P * t, (cuuint64_t)c->P * c->R * t, 2 * (cuuint64_t)c->P * c->R * t};
+    cuuint32_t box[4] = {(cuuint32_t)kTileX, (cuuint32_t)ty, 2, (cuuint32_t)kb};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUtensorMapDataType dt =
+        c->t_bytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    CUresult r = enc(out, dt, 4, c->fld[which], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(c, WX_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")");
+    return WX_OK;
+}
 }  // namespace wx
 
 namespace wx {
@@ -565,6 +584,7 @@ extern "C" int wx_sync(wx_ctx *c) {
     CK(cudaMemcpy(&st, c->d_status, sizeof st, cudaMemcpyDeviceToHost), "read status");
     if (st) CK(cudaMemset(c->d_status, 0, sizeof(unsigned)), "clear status");
     if (st & ST_TIMEOUT) return fail(c, WX_ETIMEOUT, "a bounded device wait timed out");
+    if (st & ST_BOUNDS) return fail(c, WX_ECUDA, "a kernel skipped an out-of-bounds access (bounds-checked build)");
     if (st & ST_NONFINITE) return fail(c, WX_ENONFINITE, "a step produced a non-finite value");
     if (st) return fail(c, WX_ECUDA, "device reported an invalid argument");
     return WX_OK;

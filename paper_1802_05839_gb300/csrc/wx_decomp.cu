@@ -24,24 +24,28 @@ using namespace wx;
 namespace {
 
 // One ghost strip of one block for a buffer parity: `n` cells per (k, f)
-// plane, read from src + p*src_plane + i*src_step and written to dst +
-// p*dst_plane + i*dst_step for plane p and cell i.
+// plane, read from src[src_off + p*src_plane + i*src_step] and written to
+// dst[dst_off + p*dst_plane + i*dst_step] for plane p and cell i.
 struct Strip {
-    const void *src;
-    void *dst;
+    const void *src;  // the source block's state buffer
+    void *dst;        // the receiving block's state buffer
+    long src_off, dst_off;  // first cell of the line in plane 0 (elements)
     long src_plane, dst_plane;
+    long long src_n, dst_n;  // elements of each buffer
     int n, src_step, dst_step, pad;
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256) halo_exchange_kernel(const Strip *__restrict__ strips, int nplanes) {
+__global__ void __launch_bounds__(256) halo_exchange_kernel(const Strip *__restrict__ strips, int nplanes,
+                                                            unsigned *__restrict__ status) {
     const Strip s = strips[blockIdx.x];
     const T *src = static_cast<const T *>(s.src);
     T *dst = static_cast<T *>(s.dst);
     const long total = (long)s.n * nplanes;
     for (long e = (long)blockIdx.y * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.y * blockDim.x) {
         const long p = e / s.n, i = e - p * s.n;
-        dst[p * s.dst_plane + i * s.dst_step] = src[p * s.src_plane + i * s.src_step];
+        const long so = s.src_off + p * s.src_plane + i * s.src_step, d = s.dst_off + p * s.dst_plane + i * s.dst_step;
+        if (WX_IN(so, s.src_n, status) && WX_IN(d, s.dst_n, status)) dst[d] = src[so];
     }
 }
 
@@ -128,10 +132,14 @@ static int build_strips(wx_dom *d) {
                 const long doff = col ? (long)1 * dc->P + kGhostX + pl[s].dst_line
                                       : (long)(pl[s].dst_line + 1) * dc->P + kGhostX;
                 Strip &st = h[((size_t)par * R + r) * 4 + s];
-                st.src = static_cast<const char *>(sc->fld[par]) + soff * sc->t_bytes;
-                st.dst = static_cast<char *>(dc->fld[par]) + doff * dc->t_bytes;
+                st.src = sc->fld[par];
+                st.dst = dc->fld[par];
+                st.src_off = soff;
+                st.dst_off = doff;
                 st.src_plane = (long)sc->plane_cells;
                 st.dst_plane = (long)dc->plane_cells;
+                st.src_n = (long long)(2 * sc->field_cells);
+                st.dst_n = (long long)(2 * dc->field_cells);
                 st.n = pl[s].len;
                 st.src_step = col ? sc->P : 1;
                 st.dst_step = col ? dc->P : 1;
@@ -157,9 +165,9 @@ static int launch_exchange(wx_dom *d, cudaStream_t s) {
     dim3 grid((unsigned)(4 * R), (unsigned)std::min<long>(per, 64));
     const Strip *st = d->d_strips + (size_t)par * 4 * R;
     if (d->blk[0]->t_bytes == 4)
-        halo_exchange_kernel<float><<<grid, 256, 0, s>>>(st, nplanes);
+        halo_exchange_kernel<float><<<grid, 256, 0, s>>>(st, nplanes, d->d_status);
     else
-        halo_exchange_kernel<double><<<grid, 256, 0, s>>>(st, nplanes);
+        halo_exchange_kernel<double><<<grid, 256, 0, s>>>(st, nplanes, d->d_status);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return dfail(d, WX_ECUDA, std::string("halo exchange kernel: ") + cudaGetErrorString(e));
     return WX_OK;
@@ -368,6 +376,7 @@ extern "C" int wx_dom_sync(wx_dom *d) {
         if (rc != WX_OK) return dfail(d, rc, "block " + std::to_string(r) + ": " + d->blk[r]->err);
     }
     if (st & ST_TIMEOUT) return dfail(d, WX_ETIMEOUT, "a bounded device wait timed out");
+    if (st & ST_BOUNDS) return dfail(d, WX_ECUDA, "the halo exchange skipped an out-of-bounds access");
     return WX_OK;
 }
 

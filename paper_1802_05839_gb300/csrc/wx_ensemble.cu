@@ -227,6 +227,7 @@ extern "C" int wx_ens_sync(wx_ens *e) {
         if (rc != WX_OK) return efail(e, rc, "member " + std::to_string(i) + ": " + e->mem[i]->err);
     }
     if (st & ST_TIMEOUT) return efail(e, WX_ETIMEOUT, "a bounded device wait timed out");
+    if (st & ST_BOUNDS) return efail(e, WX_ECUDA, "a kernel skipped an out-of-bounds access (bounds-checked build)");
     return WX_OK;
 }
 

@@ -43,7 +43,22 @@ enum { REC_A = 0, REC_B = 1, REC_C = 2, REC_D = 3, REC_E = 4, REC_F = 5 };
 template <typename T> struct alignas(4 * sizeof(T)) Q4 { T x, y, z, w; };
 
 // device status word bits
-enum : unsigned { ST_NONFINITE = 1u, ST_TIMEOUT = 2u, ST_BADARG = 4u };
+enum : unsigned { ST_NONFINITE = 1u, ST_TIMEOUT = 2u, ST_BADARG = 4u, ST_BOUNDS = 8u };
+
+// Range checks of the bounds-checked build (compiled with WX_BOUNDS_CHECK,
+// libwx_bounds.so): an access whose element offset is outside its buffer is
+// skipped and reported through the status word (ST_BOUNDS), never trapped.
+// In the release build every check is the constant true.
+__device__ __forceinline__ bool bounds_ok(long long off, long long n, unsigned *status) {
+    if (off >= 0 && off < n) return true;
+    atomicOr(status, ST_BOUNDS);
+    return false;
+}
+#ifdef WX_BOUNDS_CHECK
+#define WX_IN(off, n, status) ::wx::bounds_ok((long long)(off), (long long)(n), (status))
+#else
+#define WX_IN(off, n, status) true
+#endif
 
 // One level of the Thomas forward sweep of a column's implicit vertical
 // diffusion, (I - dt L_v) x = r with zero-flux ends, in a form in which
@@ -89,6 +104,7 @@ template <typename T> struct StepArgs {
     // filled by the halo exchange, so the step writes no ghost copies
     const T *Uw0, *Vs0;
     int halo;
+    long long out_n;              // elements of `out` (bounds-checked build)
 };
 
 // One member of a (possibly single-member) batch stepped by one launch:
@@ -97,6 +113,7 @@ template <typename T> struct StepArgs {
 constexpr int kMaxMembers = 16;
 template <typename T> struct alignas(64) Member {
     CUtensorMap tin;
+    CUtensorMap tbase;  // RK3 stage launches: the base state's interior boxes
     StepArgs<T> a;
     long tile0;
     int gx, gy;
@@ -134,13 +151,22 @@ __host__ __device__ constexpr uint32_t kTmemCols(int ty) { return ty > 8 ? 512u 
 // column state (F_k of the lane's two columns, plus their e_k for per-column
 // kappa; none when it lives in TMEM), then full/empty mbarriers and the
 // TMEM address.
+__host__ __device__ inline int box_bytes(int ty, int kb, int t_bytes) {
+    return align_up(kb * 2 * (ty + 2) * kBoxX * t_bytes, 128);
+}
+// A stage slot of an RK3 stage launch also holds the base state phi^n of
+// the tile's interior (kb planes x 2 fields x ty rows x kTileX), after the
+// halo box.
+__host__ __device__ inline int base_box_bytes(int ty, int kb, int t_bytes) {
+    return align_up(kb * 2 * ty * kTileX * t_bytes, 128);
+}
 __host__ __device__ inline SmemPlan plan_smem(int nz, int ty, int stages, int kb, int t_bytes,
-                                              bool per_col, bool tmem = false) {
+                                              bool per_col, bool tmem = false, bool rk_base = false) {
     SmemPlan p;
     const int nt = 32 * ty;
     p.tab_off = 0;
     p.ring_off = align_up(kTabRec * nz * 4 * t_bytes, 128);
-    p.stage_bytes = align_up(kb * 2 * (ty + 2) * kBoxX * t_bytes, 128);
+    p.stage_bytes = box_bytes(ty, kb, t_bytes) + (rk_base ? base_box_bytes(ty, kb, t_bytes) : 0);
     p.state_off = align_up(p.ring_off + stages * p.stage_bytes, 128);
     const int state = tmem ? 0 : nz * nt * 2 * t_bytes * (per_col ? 2 : 1);
     p.bar_off = align_up(p.state_off + state, 16);
@@ -168,6 +194,10 @@ struct wx_ctx {
     int stage_in = -1, stage_out = -1;
     double stage_dt = 0;
     const void *stage_tab = nullptr;
+    // a stage launch that writes phi^n + (E - phi_s) itself: the base buffer
+    // phi^n and its interior-box descriptor (-1: the stage writes E)
+    int stage_base = -1;
+    CUtensorMap tmap_rkbase;
 
     void *U = nullptr, *V = nullptr, *kmult = nullptr, *tab = nullptr;
     double *d_lev = nullptr;     // FP64 dz, kappa_lev, alpha [3][nz]
@@ -265,6 +295,8 @@ int setup_mixed(wx_ctx *c, const double *km64);
 int launch_mixed_fixup(wx_ctx *c, int dst, bool sums, cudaStream_t s);
 bool cfg_fits(const wx_ctx *c, const StepCfg &cfg, int *smem_bytes);
 int encode_tmap(wx_ctx *c, int which, int ty, int kb);
+// descriptor of the interior boxes (kTileX x ty x 2 x kb) of buffer `which`
+int encode_tmap_interior(wx_ctx *c, int which, int ty, int kb, CUtensorMap *out);
 int apply_cfg(wx_ctx *c, const StepCfg &g);
 int check_cfl(wx_ctx *c);
 // WX_SURROGATE (wx_mlp.cu)

@@ -144,10 +144,11 @@ __global__ void __launch_bounds__(128, 6) mixed_fixup_kernel(const int *__restri
                                                           const float *__restrict__ fe, float *__restrict__ side,
                                                           const Q4<float> *__restrict__ dz2, float *__restrict__ out,
                                                           double *__restrict__ corr, int nx, int ny, int nz, int P,
-                                                          int R) {
+                                                          int R, unsigned *__restrict__ status) {
     const long f = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nflag) return;
     const int col = list[f], i = col % nx, j = col / nx;
+    if (!WX_IN(col, (long long)nx * ny, status)) return;
     float *r = side + f;  // r[2k*nflag]: T*_k, overwritten by f_k; r[(2k+1)*nflag]: dt*H_k
     const size_t st = 2 * (size_t)nflag;
     if (f < n64)
@@ -157,6 +158,10 @@ __global__ void __launch_bounds__(128, 6) mixed_fixup_kernel(const int *__restri
     const size_t lev = (size_t)2 * R * P;
     const int ip = i + kGhostX;
     float *col0 = out + (size_t)(j + 1) * P;  // level 0 row of the column's T
+    const long long out_n = (long long)lev * nz;
+    auto put = [&](float *p, float v) {
+        if (WX_IN(p - out, out_n, status)) *p = v;
+    };
     float x = 0.f;
     float sE = 0.f, cE = 0.f;  // compensated sum of T dz
     for (int k0 = 0; k0 < nz; k0 += kFixChunk) {
@@ -188,11 +193,11 @@ __global__ void __launch_bounds__(128, 6) mixed_fixup_kernel(const int *__restri
                 cE = __fadd_rn(cE, __fadd_rn(e, pe));
                 sE = s1;
             }
-            row[ip] = tn;
-            if (i == 0) row[kGhostX + nx] = tn;
-            if (i == nx - 1) row[kGhostX - 1] = tn;
-            if (j == 0) out[k * lev + (size_t)(ny + 1) * P + ip] = tn;
-            if (j == ny - 1) out[k * lev + ip] = tn;
+            put(row + ip, tn);
+            if (i == 0) put(row + kGhostX + nx, tn);
+            if (i == nx - 1) put(row + kGhostX - 1, tn);
+            if (j == 0) put(out + k * lev + (size_t)(ny + 1) * P + ip, tn);
+            if (j == ny - 1) put(out + k * lev + ip, tn);
         }
     }
     if (corr) corr[f] = (double)sE + (double)cE;
@@ -203,7 +208,7 @@ int launch_mixed_fixup(wx_ctx *c, int dst, bool sums, cudaStream_t s) {
     mixed_fixup_kernel<<<(unsigned)((c->n_list + nt - 1) / nt), nt, 0, s>>>(
         c->flag_list, c->n_list, c->n_flag, (const double2 *)c->flag_fac, c->flag_e, c->flag_side,
         (const Q4<float> *)c->tab + REC_F * c->nz, (float *)c->fld[dst], sums ? c->flag_corr : nullptr, c->nx,
-        c->ny, c->nz, c->P, c->R);
+        c->ny, c->nz, c->P, c->R, c->d_status);
     WX_CK(cudaGetLastError(), "mixed fixup kernel");
     return WX_OK;
 }

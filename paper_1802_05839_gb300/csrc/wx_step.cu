@@ -124,10 +124,15 @@ __device__ __forceinline__ void consumer_sync(int nthreads) {
 // parked for the side solve.  TMF: the column state F_k lives in each
 // lane's TMEM row instead of shared memory (FP32, nz <= 64), which leaves
 // room for twelve consumer warps and a six-stage ring on one SM.
-template <typename T, int TY, int KB, int KMODE, bool PHYS, bool SUMS, bool TMF>
-__global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_constant__ Members<T> ms, const int S,
-                                                             const int PF) {
+// One CTA per SM is the design point (persistent, shared memory and TMEM
+// sized for it): the explicit minimum of 1 block lets ptxas use the whole
+// register budget of the block (128 registers at 416 threads) instead of
+// capping it for a second resident block and spilling.
+template <typename T, int TY, int KB, int KMODE, bool PHYS, bool SUMS, bool TMF, bool RKB>
+__global__ void __launch_bounds__(32 * (TY + 1), 1) step_kernel(const __grid_constant__ Members<T> ms, const int S,
+                                                                const int PF) {
     static_assert(!TMF || (std::is_same<T, float>::value && KMODE != 1), "TMEM column state: FP32 table paths");
+    static_assert(!RKB || (TMF && !SUMS), "RK3 stage launches: TMEM variant, no sums");
     using PK = Pk<T>;
     using V = typename PK::V;
     using R4 = Q4<T>;
@@ -136,7 +141,9 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
     extern __shared__ __align__(128) unsigned char smem[];
 
     const int tx = threadIdx.x, wy = threadIdx.y;
-    const SmemPlan pl = plan_smem(ms.nz_max, TY, S, KB, (int)sizeof(T), KMODE == 1, TMF);  // e_k per column
+    const SmemPlan pl = plan_smem(ms.nz_max, TY, S, KB, (int)sizeof(T), KMODE == 1, TMF, RKB);  // e_k per column
+    constexpr int PB = TY * kTileX;                                // elements per base (plane, field)
+    const int BOFF = box_bytes(TY, KB, (int)sizeof(T)) / (int)sizeof(T);  // base boxes within a slot
     R4 *tab = reinterpret_cast<R4 *>(smem + pl.tab_off);
     T *ring = reinterpret_cast<T *>(smem + pl.ring_off);
     V *stF = reinterpret_cast<V *>(smem + pl.state_off);  // [nz][NT] F of the 2 columns
@@ -177,7 +184,7 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
     // z0 = nz - (g+1)*KB .. z0+KB-1, top of the column first
     if (wy == TY) {
         if (tx == 0 && (long)blockIdx.x < total) {
-            const uint32_t tx_bytes = (uint32_t)(KB * 2 * PL * sizeof(T));
+            const uint32_t tx_bytes = (uint32_t)((KB * 2 * PL + (RKB ? KB * 2 * PB : 0)) * sizeof(T));
             int slot = 0, fill = 0;
             long issued = 0;
             bool ok = true;
@@ -221,6 +228,9 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
                     }
                     mbar_arrive_expect_tx(&full[slot], tx_bytes);
                     tma_load_4d(ring + slot * SC, &M.tin, &full[slot], x0, y0, 0, nz - (g + 1) * KB);
+                    if (RKB)  // phi^n of the tile's interior, same planes
+                        tma_load_4d(ring + slot * SC + BOFF, &M.tbase, &full[slot], x0 + kBoxX0, y0 + 1, 0,
+                                    nz - (g + 1) * KB);
                     ++issued;
                     if (++slot == S) {
                         slot = 0;
@@ -237,6 +247,14 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
     }
 
     // ---------------- consumers: two adjacent columns per lane
+    // stores into a member's new state (range-checked in the bounds-checked
+    // build, plain stores otherwise)
+    auto put = [&](const StepArgs<T> &ar, T *p, T v) {
+        if (WX_IN(p - ar.out, ar.out_n, ar.status)) *p = v;
+    };
+    auto put2 = [&](const StepArgs<T> &ar, T *p, V v) {
+        if (WX_IN(p - ar.out + 1, ar.out_n, ar.status)) *reinterpret_cast<V *>(p) = v;
+    };
     const int tid = tx + 32 * wy;
     const int ctr = (wy + 1) * kBoxX + kBoxX0 + 2 * tx;  // column pair in a staged plane (8-byte aligned)
     const T zero = T(0);
@@ -258,7 +276,8 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
         const int i0 = (t % M.gx) * kTileX + 2 * tx, j = (t / M.gx) * TY + wy;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-            const bool v = (i0 + c < nx) && (j < ny) && M.a.advection;
+            const bool v = (i0 + c < nx) && (j < ny) && M.a.advection &&
+                           WX_IN((long long)j * nx + i0 + c, (long long)nx * ny, M.a.status);
             const int ic = v ? i0 + c : 0, jc = v ? j : 0;
             wd.v[4 * c + 0] = v ? M.a.U[(size_t)jc * nx + ic] : T(0);
             const T *uw = (ic == 0 && M.a.Uw0) ? M.a.Uw0 + jc : M.a.U + (size_t)jc * nx + (ic == 0 ? nx - 1 : ic - 1);
@@ -313,8 +332,9 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
                 c5[c][0] = T(1) - T(4) * a.dh -
                            a.dth * (fmax(ue, zero) - fmin(uw, zero) + fmax(vn, zero) - fmin(vs, zero));
                 const bool v = c ? vb : va;
-                k1[c] = (KMODE == 1 && a.kmult && v) ? a.kmult[(size_t)j * nx + i0 + c] : T(1);
-                fl[c] = (KMODE == 2 && v && a.flag_idx) ? a.flag_idx[(size_t)j * nx + i0 + c] : -1;
+                const bool inb = v && WX_IN((long long)j * nx + i0 + c, (long long)nx * ny, a.status);
+                k1[c] = (KMODE == 1 && a.kmult && v && inb) ? a.kmult[(size_t)j * nx + i0 + c] : T(1);
+                fl[c] = (KMODE == 2 && v && a.flag_idx && inb) ? a.flag_idx[(size_t)j * nx + i0 + c] : -1;
             }
             cC = V{c5[0][0], c5[1][0]};
             cE = V{c5[0][1], c5[1][1]};
@@ -338,10 +358,11 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
         T *qp = a.out + fld + (size_t)(j + 1) * a.P + (i0 + kGhostX) + (size_t)(nz - 1) * lev;  // q, top
         // F_k of the lane's two columns: its TMEM lane, or shared memory
         auto putF = [&](int k, V v) {
-            if constexpr (TMF)
-                tmem_st2(trow + 2 * k, v.x, v.y);
-            else
+            if constexpr (TMF) {
+                if (WX_IN(2 * k + 1, 128, a.status)) tmem_st2(trow + 2 * k, v.x, v.y);  // k is warp-uniform
+            } else {
                 stF[k * NT + tid] = v;
+            }
         };
 
         // phi* for one field at level k: two short FMA chains, summed
@@ -359,13 +380,18 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
         };
 
         // one level; EDGE selects the masked store path with ghost copies
-        auto level = [&](auto edge_tag, int k, const T *pk, V nT, V nQ) {
+        auto level = [&](auto edge_tag, int k, const T *pk, const T *pb, V nT, V nQ) {
             constexpr bool EDGE = decltype(edge_tag)::value;
             const R4 A = tA[k], B = tB[k];
             const V wu = V{A.x, A.y}, wd = V{A.z, A.w};
             const V cCk = PK::add(cC, V{B.x, B.y});
-            const V Ts = stencil(pk, curT, prvT, nT, cCk, wu, wd);
-            const V Qs = stencil(pk + PL, curQ, prvQ, nQ, cCk, wu, wd);
+            V Ts = stencil(pk, curT, prvT, nT, cCk, wu, wd);
+            V Qs = stencil(pk + PL, curQ, prvQ, nQ, cCk, wu, wd);
+            if (RKB) {  // RK3 stage: phi^n + (E - phi_s), E = phi_s + c dt L(phi_s)
+                const V bT = *reinterpret_cast<const V *>(pb), bQ = *reinterpret_cast<const V *>(pb + PB);
+                Ts = PK::add(bT, PK::fma(curT, m1, Ts));
+                Qs = PK::add(bQ, PK::fma(curQ, m1, Qs));
+            }
             prvT = curT;
             prvQ = curQ;
             curT = nT;
@@ -373,24 +399,24 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
 
             // q^{n+1} = q*
             if (!EDGE) {
-                *reinterpret_cast<V *>(qp) = Qs;
+                put2(a, qp, Qs);
             } else {
                 T *row = a.out + k * lev + fld + (size_t)(j + 1) * a.P;
-                if (va) row[i0 + kGhostX] = Qs.x;
-                if (vb) row[i0 + 1 + kGhostX] = Qs.y;
+                if (va) put(a, row + (i0 + kGhostX), Qs.x);
+                if (vb) put(a, row + (i0 + 1 + kGhostX), Qs.y);
                 if (!a.halo) {  // periodic ghost copies (a sub-domain's come from the exchange)
-                if (va && i0 == 0) row[kGhostX + nx] = Qs.x;
-                if (vb && i0 + 1 == nx - 1) row[kGhostX - 1] = Qs.y;
-                if (va && i0 == nx - 1) row[kGhostX - 1] = Qs.x;
+                if (va && i0 == 0) put(a, row + (kGhostX + nx), Qs.x);
+                if (vb && i0 + 1 == nx - 1) put(a, row + (kGhostX - 1), Qs.y);
+                if (va && i0 == nx - 1) put(a, row + (kGhostX - 1), Qs.x);
                 if (j == 0) {  // bottom row -> top ghost row
                     T *g = a.out + k * lev + fld + (size_t)(ny + 1) * a.P;
-                    if (va) g[i0 + kGhostX] = Qs.x;
-                    if (vb) g[i0 + 1 + kGhostX] = Qs.y;
+                    if (va) put(a, g + (i0 + kGhostX), Qs.x);
+                    if (vb) put(a, g + (i0 + 1 + kGhostX), Qs.y);
                 }
                 if (j == ny - 1) {  // top row -> bottom ghost row
                     T *g = a.out + k * lev + fld;
-                    if (va) g[i0 + kGhostX] = Qs.x;
-                    if (vb) g[i0 + 1 + kGhostX] = Qs.y;
+                    if (va) put(a, g + (i0 + kGhostX), Qs.x);
+                    if (vb) put(a, g + (i0 + 1 + kGhostX), Qs.y);
                 }
                 }
             }
@@ -428,11 +454,11 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
                 }
                 if (KMODE == 2) {  // listed columns: T* and dt*H for the side solve, [k][2][n]
                     float *sd = a.side + (size_t)k * 2 * a.n_list;
-                    if (fl[0] >= 0) {
+                    if (fl[0] >= 0 && WX_IN(fl[0], a.n_list, a.status)) {
                         sd[fl[0]] = (float)Ts.x;
                         sd[a.n_list + fl[0]] = (float)hk.x;
                     }
-                    if (fl[1] >= 0) {
+                    if (fl[1] >= 0 && WX_IN(fl[1], a.n_list, a.status)) {
                         sd[fl[1]] = (float)Ts.y;
                         sd[a.n_list + fl[1]] = (float)hk.y;
                     }
@@ -471,7 +497,7 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
                         nT = *reinterpret_cast<const V *>(pn + ctr);
                         nQ = *reinterpret_cast<const V *>(pn + PL + ctr);
                     }
-                    level(edge_tag, k, pa + s * 2 * PL, nT, nQ);
+                    level(edge_tag, k, pa + s * 2 * PL, pa + BOFF + (s * 2 * TY + wy) * kTileX + 2 * tx, nT, nQ);
                 }
                 __syncwarp();
                 if (tx == 0) mbar_arrive(&empty[slot]);
@@ -502,7 +528,7 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
                 Tprev = tn;
             }
             if (!EDGE) {
-                *reinterpret_cast<V *>(tp + (size_t)k * lev) = tn;
+                put2(a, tp + (size_t)k * lev, tn);
                 if (SUMS)
                     sumT.add(SIDE ? PK::mul(tn, lmask) : tn, Fr.z, Fr.w);
                 else
@@ -510,21 +536,21 @@ __global__ void __launch_bounds__(32 * (TY + 1)) step_kernel(const __grid_consta
                 return;
             }
             T *row = a.out + k * lev + (size_t)(j + 1) * a.P;
-            if (va) row[i0 + kGhostX] = tn.x;
-            if (vb) row[i0 + 1 + kGhostX] = tn.y;
+            if (va) put(a, row + (i0 + kGhostX), tn.x);
+            if (vb) put(a, row + (i0 + 1 + kGhostX), tn.y);
             if (!a.halo) {
-                if (va && i0 == 0) row[kGhostX + nx] = tn.x;
-                if (vb && i0 + 1 == nx - 1) row[kGhostX - 1] = tn.y;
-                if (va && i0 == nx - 1) row[kGhostX - 1] = tn.x;
+                if (va && i0 == 0) put(a, row + (kGhostX + nx), tn.x);
+                if (vb && i0 + 1 == nx - 1) put(a, row + (kGhostX - 1), tn.y);
+                if (va && i0 == nx - 1) put(a, row + (kGhostX - 1), tn.x);
                 if (j == 0) {
                     T *g = a.out + k * lev + (size_t)(ny + 1) * a.P;
-                    if (va) g[i0 + kGhostX] = tn.x;
-                    if (vb) g[i0 + 1 + kGhostX] = tn.y;
+                    if (va) put(a, g + (i0 + kGhostX), tn.x);
+                    if (vb) put(a, g + (i0 + 1 + kGhostX), tn.y);
                 }
                 if (j == ny - 1) {
                     T *g = a.out + k * lev;
-                    if (va) g[i0 + kGhostX] = tn.x;
-                    if (vb) g[i0 + 1 + kGhostX] = tn.y;
+                    if (va) put(a, g + (i0 + kGhostX), tn.x);
+                    if (vb) put(a, g + (i0 + 1 + kGhostX), tn.y);
                 }
             }
             const V tm = V{va ? tn.x : T(0), vb ? tn.y : T(0)};
@@ -820,7 +846,10 @@ bool cfg_fits(const wx_ctx *c, const StepCfg &cfg, int *smem_bytes) {
 StepCfg default_cfg(const wx_ctx *c) {
     // The TMA unit of an SM completes boxes at a roughly fixed rate, so big
     // boxes (4 planes) and tall tiles come first; then the most resident
-    // consumer warps per SM (capped at 16), then the deeper ring (3..8 slots).
+    // consumer warps per SM (capped at 16), then the deeper ring (3..6
+    // slots: measured at the paper grid, a ring that leaves the SM less
+    // than ~30 KB of L1 -- 7 slots of twelve-row boxes, 231 KB -- runs 40%
+    // slower than 6).
     StepCfg best;
     best.ty = 1;
     best.stages = 3;
@@ -830,7 +859,7 @@ StepCfg default_cfg(const wx_ctx *c) {
     for (int kb : {2, 4}) {
         for (int ty : {1, 2, 4, 8, 12}) {
             if (ty == 12 && !tmem_nz(c->t_bytes, c->nz, per_col(c))) continue;
-            for (int st = 8; st >= 3; --st) {
+            for (int st = 6; st >= 3; --st) {
                 StepCfg g;
                 g.ty = ty;
                 g.stages = st;
@@ -863,6 +892,7 @@ template <typename T> static void fill_member(const wx_ctx *c, Member<T> &M, lon
     const int src = stage ? c->stage_in : c->cur, dst = stage ? c->stage_out : 1 - c->cur;
     const double dt = stage ? c->stage_dt : c->dt;
     M.tin = c->tmap[src];
+    if (stage && c->stage_base >= 0) M.tbase = c->tmap_rkbase;
     StepArgs<T> &a = M.a;
     a.out = reinterpret_cast<T *>(c->fld[dst]);
     a.U = (const T *)c->U;
@@ -885,28 +915,43 @@ template <typename T> static void fill_member(const wx_ctx *c, Member<T> &M, lon
     a.Uw0 = (const T *)c->Uw0;
     a.Vs0 = (const T *)c->Vs0;
     a.halo = c->halo ? 1 : 0;
+    a.out_n = (long long)(2 * c->field_cells);
     M.tile0 = tile0;
     M.gx = (c->nx + kTileX - 1) / kTileX;
     M.gy = (c->ny + ty - 1) / ty;
 }
 
-template <typename T, int TY, int KB, int KMODE, bool PHYS, bool SUMS, bool TMF>
+template <typename T, int TY, int KB, int KMODE, bool PHYS, bool SUMS, bool TMF, bool RKB = false>
 static int launch_batch_t(wx_ctx *const *mem, int n, const StepCfg &cfg, int num_sms, unsigned *status,
                           cudaStream_t s, std::string &err) {
-    auto kern = step_kernel<T, TY, KB, KMODE, PHYS, SUMS, TMF>;
+    auto kern = step_kernel<T, TY, KB, KMODE, PHYS, SUMS, TMF, RKB>;
     Members<T> ms;
     long total = 0;
     int nz_max = 1;
-    for (int i = 0; i < n; ++i) {
-        fill_member<T>(mem[i], ms.m[i], total, TY);
-        total += (long)ms.m[i].gx * ms.m[i].gy;
+    // the work list takes the members with the deepest (costliest) tiles
+    // first, larger grids first among equals, so that the persistent CTAs'
+    // last round-robin passes run the cheapest tiles and end together
+    int ord[kMaxMembers];
+    for (int i = 0; i < n; ++i) ord[i] = i;
+    std::stable_sort(ord, ord + n, [&](int x, int y) {
+        if (mem[x]->nz != mem[y]->nz) return mem[x]->nz > mem[y]->nz;
+        return (long)mem[x]->nx * mem[x]->ny > (long)mem[y]->nx * mem[y]->ny;
+    });
+    for (int k = 0; k < n; ++k) {
+        const int i = ord[k];
+        fill_member<T>(mem[i], ms.m[k], total, TY);
+        total += (long)ms.m[k].gx * ms.m[k].gy;
         nz_max = std::max(nz_max, mem[i]->nz);
     }
     ms.n = n;
     ms.nz_max = nz_max;
     ms.total = total;
     ms.status = status;
-    const SmemPlan pl = plan_smem(nz_max, TY, cfg.stages, KB, (int)sizeof(T), KMODE == 1, TMF);
+    // an RK3 stage's slots also hold the base boxes: as many as fit
+    int stages = cfg.stages;
+    while (RKB && stages > 2 && plan_smem(nz_max, TY, stages, KB, (int)sizeof(T), false, TMF, true).total > 227 * 1024)
+        --stages;
+    const SmemPlan pl = plan_smem(nz_max, TY, stages, KB, (int)sizeof(T), KMODE == 1, TMF, RKB);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.total);
     if (e != cudaSuccess) {
         err = std::string("smem attr: ") + cudaGetErrorString(e);
@@ -924,7 +969,7 @@ static int launch_batch_t(wx_ctx *const *mem, int n, const StepCfg &cfg, int num
     const long resident = (long)num_sms * std::min(cfg.ctas_per_sm, fit);
     dim3 grid((unsigned)std::max(1L, std::min(total, resident)));
     dim3 block(32, TY + 1);
-    kern<<<grid, block, pl.total, s>>>(ms, cfg.stages, cfg.prefetch);
+    kern<<<grid, block, pl.total, s>>>(ms, stages, cfg.prefetch);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         err = std::string("step kernel: ") + cudaGetErrorString(e);
@@ -940,8 +985,15 @@ static int dispatch_ty(wx_ctx *const *mem, int n, const StepCfg &cfg, int sms, u
     for (int i = 0; i < n; ++i) nz_max = std::max(nz_max, mem[i]->nz);
     if constexpr (std::is_same<T, float>::value && KMODE != 1) {
         if (tmem_nz(4, nz_max, false) && tmem_shape(cfg.ty, cfg.kb)) {
+            if constexpr (!SUMS)
+                if (mem[0]->stage_base >= 0)  // an RK3 stage writing phi^n + (E - phi_s)
+                    return launch_batch_t<T, 12, 4, KMODE, PHYS, SUMS, true, true>(mem, n, cfg, sms, st, s, err);
             return launch_batch_t<T, 12, 4, KMODE, PHYS, SUMS, true>(mem, n, cfg, sms, st, s, err);
         }
+    }
+    if (mem[0]->stage_base >= 0) {
+        err = "RK3 stage launches with a base state need the TMEM variant";
+        return WX_EUNSUPPORTED;
     }
     switch (cfg.ty * 10 + cfg.kb) {
         case 12: return launch_batch_t<T, 1, 2, KMODE, PHYS, SUMS, false>(mem, n, cfg, sms, st, s, err);
@@ -1157,7 +1209,41 @@ template <typename T> static int rk_physics(wx_ctx *c, int A, int B, int C, cuda
     return WX_OK;
 }
 
+// RK3 on the TMEM variant: three stage launches of the step kernel, each
+// writing its stage's state itself (the base state phi^n rides in the same
+// TMA ring as the stage input), the last fused with the column physics:
+//   stage 1: B <- step_{dt/3}(A)                     (phi1)
+//   stage 2: C <- A + (step_{dt/2}(B) - B)           (phi2)
+//   stage 3: B <- physics(A + (step_{dt}(C) - C))    (q^{n+1} = q3)
+// followed by the side solve of listed columns.  Per cell and step: 16 B,
+// then 24 B twice (read phi_s and phi^n, write), 64 B in all.
+static int launch_rk3_fused(wx_ctx *c, cudaStream_t s, long *launches) {
+    const int A = c->cur, B = 1 - c->cur, C = 2;
+    const size_t tbytes = (size_t)c->nz * kTabRec * 4 * c->t_bytes;
+    int rc = encode_tmap_interior(c, A, c->cfg.ty, c->cfg.kb, &c->tmap_rkbase);
+    if (rc != WX_OK) return rc;
+    const unsigned saved = c->flags;
+    const int in[3] = {A, B, C}, out[3] = {B, C, B};
+    const double dts[3] = {c->dt / 3.0, c->dt / 2.0, c->dt};
+    for (int st = 0; st < 3 && rc == WX_OK; ++st) {
+        c->stage_in = in[st];
+        c->stage_out = out[st];
+        c->stage_dt = dts[st];
+        c->stage_tab = (const char *)c->tab_rk + st * tbytes;
+        c->stage_base = st == 0 ? -1 : A;
+        c->flags = st == 2 ? saved : (saved & WX_ADVECTION);
+        rc = launch_step(c, s, launches);
+    }
+    c->stage_in = c->stage_out = c->stage_base = -1;
+    c->stage_tab = nullptr;
+    c->flags = saved;
+    if (rc != WX_OK) return rc;
+    c->cur = B;
+    return WX_OK;
+}
+
 int launch_rk3_step(wx_ctx *c, cudaStream_t s, long *launches) {
+    if (use_tmem(c, c->cfg)) return launch_rk3_fused(c, s, launches);
     const int A = c->cur, B = 1 - c->cur, C = 2;
     const size_t tbytes = (size_t)c->nz * kTabRec * 4 * c->t_bytes;
     const unsigned saved = c->flags;

@@ -13,7 +13,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libwx.so")
+# WX_LIBRARY names another build of the same ABI to load instead (the
+# bounds-checked libwx_bounds.so); it must exist as well
+LIB_PATH = os.environ.get("WX_LIBRARY") or os.path.join(HERE, "libwx.so")
 
 WX_F32, WX_F64, WX_MIXED = 0, 1, 2
 WX_ADVECTION, WX_PHYSICS, WX_SUMS, WX_SURROGATE, WX_RK3 = 1, 2, 4, 8, 16

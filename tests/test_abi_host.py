@@ -43,6 +43,17 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(lib, n), f"{n} declared in include/ but not exported"
 
 
+def test_bounds_checked_library_builds_and_exports_every_symbol():
+    """The debug build with WX_BOUNDS_CHECK compiles (it is built beside
+    libwx.so) and exports the same ABI."""
+    from paper_1802_05839_gb300 import build
+    if not os.path.exists(build.LIB_BOUNDS):
+        build.build(bounds=True)
+    L = ctypes.CDLL(build.LIB_BOUNDS)
+    for n in sorted(declared_functions()):
+        assert hasattr(L, n), f"{n} missing from the bounds-checked library"
+
+
 def test_binding_covers_every_declared_symbol():
     bound = {n for n, _, _ in wx.SIGNATURES}
     missing = declared_functions() - bound

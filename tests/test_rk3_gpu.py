@@ -78,7 +78,13 @@ def test_every_step_matches_oracle(dtype, tol, shape, ns):
             Ts = rk3_dynamics(case, T, q)
             assert_increments(T, Ts, Tg, To, what=f"RK3 {shape}")
         T, q = Tg, qg  # per-step error: the next oracle step starts from the GPU state
-    assert ctx.last_launches() == 5  # 3 stage kernels, 1 combine, combine + physics
+    # the TMEM variant (twelve-row tiles, FP32, nz <= 64): 3 stage kernels
+    # writing their stages themselves (+ the side solve of near-singular
+    # columns); otherwise 3 stage kernels, 1 combine, combine + physics
+    fused = dtype == "f32" and ctx.step_config()["ty"] == 12
+    assert ctx.last_launches() == ((4 if ns else 3) if fused else 5)
+    if shape == (70, 50, 58) and dtype == "f32":
+        assert fused  # the paper's level count takes the fused path
     ctx.close()
 
 
