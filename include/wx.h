@@ -185,6 +185,13 @@ int wx_set_step_config(wx_ctx *c, int ty, int kb, int stages, int ctas_per_sm,
 int wx_get_step_config(const wx_ctx *c, int *ty, int *kb, int *stages,
                        int *ctas_per_sm, int *prefetch, int *smem_bytes);
 
+/* The current T and q as device FP32 columns, T[col][k] and q[col][k] with
+ * col = j*nx + i and k = 0 (bottom) .. nz-1, i.e. [nx*ny][nz] (an FP64
+ * context rounds to FP32); either output may be NULL.  The column layout of
+ * wx_physics_columns and the network's features.  Asynchronous on the
+ * stream; WX_ESTATE before any load. */
+int wx_read_columns_f32(wx_ctx *c, float *T, float *q, void *cuda_stream);
+
 /* WX_MIXED: number of columns flagged for the FP64 elimination (dominance
  * ratio below dd_threshold), 0 for other contexts. */
 int wx_flagged_columns(const wx_ctx *c, long *n_flagged);
@@ -479,6 +486,23 @@ int wx_mlp_train_step(wx_mlp *m, const void *X, const float *Yt, int M,
 /* WX_OK, or WX_ETIMEOUT if a bounded device wait of a GEMM gave up since the
  * last call (synchronises). */
 int wx_mlp_status(wx_mlp *m);
+/* Physical-unit outputs of M rows of normalised outputs Y [M][128]:
+ * out[r][o] = Y[r][o] std_out[o] + mean_out[o] for the 116 outputs (out
+ * [M][116], device FP32).  Asynchronous. */
+int wx_mlp_denormalize(wx_mlp *m, const float *Y, long M, float *out,
+                       void *cuda_stream);
+
+/* Device data movement for the training driver (no arithmetic of the
+ * method): element conversion of n values FP32 -> FP64 (to_f64 = 1) or
+ * FP64 -> FP32 (0, round to nearest); and a row gather dst[r] = src[idx[r]]
+ * of n rows of row_bytes bytes (a multiple of 16, both arrays 16-byte
+ * aligned; idx device int32; an index outside [0, src_rows) gives a zero
+ * row).  Asynchronous; WX_EINVAL for bad arguments, message in
+ * wx_mlp_last_error(). */
+int wx_convert(const void *src, void *dst, long n, int to_f64,
+               void *cuda_stream);
+int wx_gather_rows(const void *src, long src_rows, long row_bytes,
+                   const int *idx, long n, void *dst, void *cuda_stream);
 
 /* Attach (m != NULL) or detach (NULL) a trained network to an FP32 context
  * with nz = 58.  With WX_SURROGATE in the flags, each wx_step then runs the

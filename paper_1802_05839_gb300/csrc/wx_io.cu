@@ -142,4 +142,64 @@ int launch_convert(wx_ctx *c, const double *src, void *dst, size_t n, cudaStream
     return WX_OK;
 }
 
+// The state as FP32 columns dst[col][k], col = j nx + i: a block stages the
+// planes of 32 consecutive columns (each level's read coalesced along x),
+// then writes each column's nz values contiguously.
+template <typename T>
+__global__ void __launch_bounds__(kIoThreads) columns_out_kernel(const T *__restrict__ src, float *__restrict__ Tdst,
+                                                                 float *__restrict__ qdst, int nx, int nz, int P,
+                                                                 int R, long ncol) {
+    extern __shared__ float cs[];  // [nz][33]
+    const long c0 = (long)blockIdx.x * 32;
+    for (int f = 0; f < 2; ++f) {
+        float *dst = f ? qdst : Tdst;
+        if (!dst) continue;
+        __syncthreads();
+        for (int e = threadIdx.x; e < nz * 32; e += blockDim.x) {
+            const int k = e / 32, u = e % 32;
+            const long c = c0 + u;
+            float v = 0.f;
+            if (c < ncol) {
+                const int j = (int)(c / nx), i = (int)(c - (long)j * nx);
+                v = (float)src[((size_t)(2 * k + f) * R + j + 1) * P + kGhostX + i];
+            }
+            cs[k * 33 + u] = v;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < nz * 32; e += blockDim.x) {
+            const int u = e / nz, k = e - u * nz;
+            const long c = c0 + u;
+            if (c < ncol) dst[c * nz + k] = cs[k * 33 + u];
+        }
+    }
+}
+
 }  // namespace wx
+
+using namespace wx;
+
+extern "C" int wx_read_columns_f32(wx_ctx *c, float *T, float *q, void *stream) {
+    if (!c) return WX_EINVAL;
+    if (!c->fields_loaded) {
+        c->err = "wx_read_columns_f32: no fields loaded";
+        return WX_ESTATE;
+    }
+    const long ncol = (long)c->nx * c->ny;
+    if (ncol == 0 || (!T && !q)) return WX_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned blocks = (unsigned)((ncol + 31) / 32);
+    const size_t smem = (size_t)c->nz * 33 * sizeof(float);
+    if (c->t_bytes == 4)
+        columns_out_kernel<float><<<blocks, kIoThreads, smem, s>>>((const float *)c->fld[c->cur], T, q, c->nx,
+                                                                   c->nz, c->P, c->R, ncol);
+    else
+        columns_out_kernel<double><<<blocks, kIoThreads, smem, s>>>((const double *)c->fld[c->cur], T, q, c->nx,
+                                                                    c->nz, c->P, c->R, ncol);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        c->err = std::string("columns kernel: ") + cudaGetErrorString(e);
+        return WX_ECUDA;
+    }
+    c->last_stream = s;
+    return WX_OK;
+}

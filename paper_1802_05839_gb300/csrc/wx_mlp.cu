@@ -872,6 +872,77 @@ static int mlp_backward(wx_mlp *m, const __nv_bfloat16 *X, const float *Yt, int 
 }
 }  // namespace wx
 
+namespace wx {
+template <typename S, typename D>
+__global__ void convert_any_kernel(const S *__restrict__ src, D *__restrict__ dst, long n) {
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+        dst[e] = (D)src[e];
+}
+
+// Rows of 16-byte words: dst row r = src row idx[r] (a zero row where the
+// index is outside [0, src_rows)).
+__global__ void gather_rows_kernel(const uint4 *__restrict__ src, long src_rows, long words,
+                                   const int *__restrict__ idx, long n, uint4 *__restrict__ dst) {
+    const long total = n * words;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const long r = e / words, w = e - r * words;
+        const long sr = idx[r];
+        dst[e] = (sr >= 0 && sr < src_rows) ? src[sr * words + w] : make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+// Physical-unit outputs out[r][o] = Y[r][o] std_out[o] + mean_out[o], o < kOut.
+__global__ void denormalize_kernel(const float *__restrict__ Y, const float *__restrict__ norm, long M,
+                                   float *__restrict__ out) {
+    const long total = M * kOut;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const long r = e / kOut;
+        const int o = (int)(e - r * kOut);
+        out[e] = fmaf(Y[r * kOutP + o], norm[3 * kInP + o], norm[2 * kInP + o]);
+    }
+}
+
+static unsigned grid_of(long n) {
+    const long b = (n + 255) / 256;
+    return (unsigned)(b < 1 ? 1 : (b > 65535 * 4 ? 65535 * 4 : b));
+}
+}  // namespace wx
+
+extern "C" int wx_convert(const void *src, void *dst, long n, int to_f64, void *stream) {
+    if (n < 0 || (n > 0 && (!src || !dst))) return mfail(nullptr, WX_EINVAL, "wx_convert: bad arguments");
+    if (n == 0) return WX_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (to_f64)
+        convert_any_kernel<float, double><<<grid_of(n), 256, 0, s>>>((const float *)src, (double *)dst, n);
+    else
+        convert_any_kernel<double, float><<<grid_of(n), 256, 0, s>>>((const double *)src, (float *)dst, n);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? WX_OK : mfail(nullptr, WX_ECUDA, std::string("wx_convert: ") + cudaGetErrorString(e));
+}
+
+extern "C" int wx_gather_rows(const void *src, long src_rows, long row_bytes, const int *idx, long n, void *dst,
+                              void *stream) {
+    if (n < 0 || src_rows < 0 || row_bytes <= 0 || row_bytes % 16 || (n > 0 && (!src || !idx || !dst)) ||
+        (reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) % 16)
+        return mfail(nullptr, WX_EINVAL, "wx_gather_rows: rows of a multiple of 16 bytes, 16-byte aligned arrays");
+    if (n == 0) return WX_OK;
+    const long words = row_bytes / 16;
+    gather_rows_kernel<<<grid_of(n * words), 256, 0, (cudaStream_t)stream>>>(
+        (const uint4 *)src, src_rows, words, idx, n, (uint4 *)dst);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? WX_OK
+                            : mfail(nullptr, WX_ECUDA, std::string("wx_gather_rows: ") + cudaGetErrorString(e));
+}
+
+extern "C" int wx_mlp_denormalize(wx_mlp *m, const float *Y, long M, float *out, void *stream) {
+    if (!m) return mfail(nullptr, WX_EINVAL, "wx_mlp_denormalize: no network");
+    if (M < 0 || (M > 0 && (!Y || !out))) return mfail(m, WX_EINVAL, "wx_mlp_denormalize: bad arguments");
+    if (M == 0) return WX_OK;
+    denormalize_kernel<<<grid_of(M * kOut), 256, 0, (cudaStream_t)stream>>>(Y, m->norm, M, out);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? WX_OK : mfail(m, WX_ECUDA, std::string("wx_mlp_denormalize: ") + cudaGetErrorString(e));
+}
+
 extern "C" int wx_mlp_forward(wx_mlp *m, const void *X, int M, float *Y, void *stream) {
     if (!m || !X || !Y) return mfail(m, WX_EINVAL, "wx_mlp_forward: NULL");
     if (M <= 0 || M % 128) return mfail(m, WX_EINVAL, "wx_mlp_forward: M must be a positive multiple of 128");

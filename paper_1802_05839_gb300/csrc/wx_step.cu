@@ -128,11 +128,12 @@ __device__ __forceinline__ void consumer_sync(int nthreads) {
 // sized for it): the explicit minimum of 1 block lets ptxas use the whole
 // register budget of the block (128 registers at 416 threads) instead of
 // capping it for a second resident block and spilling.
-template <typename T, int TY, int KB, int KMODE, bool PHYS, bool SUMS, bool TMF, bool RKB>
+template <typename T, int TY, int KB, int KMODE, bool PHYS, bool SUMS, bool TMF, bool RKB, bool HALO>
 __global__ void __launch_bounds__(32 * (TY + 1), 1) step_kernel(const __grid_constant__ Members<T> ms, const int S,
                                                                 const int PF) {
     static_assert(!TMF || (std::is_same<T, float>::value && KMODE != 1), "TMEM column state: FP32 table paths");
     static_assert(!RKB || (TMF && !SUMS), "RK3 stage launches: TMEM variant, no sums");
+    static_assert(!HALO || (TMF && !RKB), "decomposed blocks: TMEM variant");
     using PK = Pk<T>;
     using V = typename PK::V;
     using R4 = Q4<T>;
@@ -263,6 +264,10 @@ __global__ void __launch_bounds__(32 * (TY + 1), 1) step_kernel(const __grid_con
     uint32_t par = 0;
     bool ok = true;
     int cur_member = -1;
+    // a decomposed block's four ghost-line descriptors, staged with the
+    // table and read (volatile) only where a border tile stores its edges,
+    // so that they hold no registers across the level loops
+    __shared__ GhostLine<T> ghs[HALO ? 4 : 1];
 
     // face winds of a tile's two columns (a, b): Ue, Uw, Vn, Vs each
     struct Winds {
@@ -301,6 +306,7 @@ __global__ void __launch_bounds__(32 * (TY + 1), 1) step_kernel(const __grid_con
         if (mi != cur_member) {  // stage the member's per-level table
             consumer_sync(NT);
             for (int e = tid; e < kTabRec * nz; e += NT) tab[e] = a.tab[e];
+            if (HALO && tid < 4) ghs[tid] = a.g[tid];
             consumer_sync(NT);
             cur_member = mi;
         }
@@ -310,10 +316,15 @@ __global__ void __launch_bounds__(32 * (TY + 1), 1) step_kernel(const __grid_con
         const int bx = t % gx, by = t / gx;
         const int i0 = bx * kTileX + 2 * tx, j = by * TY + wy;
         const bool va = (i0 < nx) && (j < ny), vb = (i0 + 1 < nx) && (j < ny);
-        // masked stores for ragged tiles, plus the periodic ghost copies of
-        // border tiles (a decomposed block's ghosts come from the exchange)
-        const bool edge = a.halo ? ((bx == gx - 1 && nx % kTileX) || (by == gy - 1 && ny % TY))
-                                 : (bx == 0 || bx == gx - 1 || by == 0 || by == gy - 1);
+        // tile kind: 0 inner (whole 64 x TY columns, no edge), 1 a whole
+        // border tile (paired stores plus the ghost copies of its edge
+        // lanes and rows), 2 a ragged tile (masked stores plus ghost copies)
+        const bool ragged = (bx == gx - 1 && nx % kTileX) || (by == gy - 1 && ny % TY);
+        const int kind = ragged ? 2 : ((bx == 0 || bx == gx - 1 || by == 0 || by == gy - 1) ? 1 : 0);
+        // this lane's ghost duties: column 0 (x), column nx-1 (x or y)
+        const bool gc0 = va && i0 == 0, gclx = va && i0 == nx - 1, gcly = vb && i0 + 1 == nx - 1;
+        const bool gwarp = __any_sync(0xffffffffu, gc0 || gclx || gcly);  // warp-uniform
+        const size_t rowoff = (size_t)(j + 1) * a.P + (i0 + kGhostX);
 
         // per-column coefficients of the horizontal operator, paired (a, b)
         const Winds wc = wnext;
@@ -355,7 +366,66 @@ __global__ void __launch_bounds__(32 * (TY + 1), 1) step_kernel(const __grid_con
         V f_up = PK::dup(T(0)), h_up = PK::dup(T(0)), e_up = PK::dup(T(0));  // level k+1
         V chk = PK::dup(T(0));
         ColSum2<T> sumQ, sumT;
-        T *qp = a.out + fld + (size_t)(j + 1) * a.P + (i0 + kGhostX) + (size_t)(nz - 1) * lev;  // q, top
+        // A level's new pair of field f into the new state (kind as above),
+        // then its copies into the ghost lines the tile's edges feed: this
+        // grid's periodic ghost ring, or a decomposed block's neighbours'.
+        // element x (row j of g[0..1], column i of g[2..3]) of level k, field f
+        auto gslot = [&](int d, int k, int f, long long x) -> T * {
+            const volatile GhostLine<T> &g = ghs[d];
+            return g.buf + (g.off + k * g.lev + f * g.fld + x * (d < 2 ? (long long)g.P : 1ll));
+        };
+        auto gput = [&](int d, int k, int f, long long x, T v) {
+            T *p = gslot(d, k, f, x);
+            if (WX_IN(p - ghs[d].buf, ghs[d].n, a.status)) *p = v;
+        };
+        auto emit = [&](auto kind_tag, int k, int f, V v) {
+            constexpr int KIND = decltype(kind_tag)::value;
+            T *dst = a.out + (size_t)k * lev + (size_t)f * fld + rowoff;
+            if (KIND != 2) {
+                put2(a, dst, v);
+            } else {
+                if (va) put(a, dst, v.x);
+                if (vb) put(a, dst + 1, v.y);
+            }
+            if (KIND == 0) return;
+            if constexpr (!HALO) {
+                // this grid's periodic ghost ring, addressed from dst: column 0
+                // -> ghost column nx, column nx-1 -> ghost column -1, row 0 ->
+                // ghost row ny+1, row ny-1 -> ghost row 0
+                if (gwarp) {
+                    if (gc0) put(a, dst + nx, v.x);
+                    if (gclx) put(a, dst - nx, v.x);
+                    if (gcly) put(a, dst + 1 - nx, v.y);
+                }
+                for (int r = 0; r < 2; ++r) {  // warp-uniform; both rows when ny = 1
+                    if (j != (r == 0 ? 0 : ny - 1)) continue;
+                    T *g = r == 0 ? dst + (size_t)ny * a.P : dst - (size_t)ny * a.P;
+                    if (KIND != 2) {
+                        put2(a, g, v);
+                    } else {
+                        if (va) put(a, g, v.x);
+                        if (vb) put(a, g + 1, v.y);
+                    }
+                }
+            } else {
+                // a decomposed block: the ghost lines of its neighbours' new states
+                if (gwarp) {
+                    if (gc0) gput(0, k, f, j, v.x);
+                    if (gclx) gput(1, k, f, j, v.x);
+                    if (gcly) gput(1, k, f, j, v.y);
+                }
+                for (int r = 0; r < 2; ++r) {  // row 0 -> g[2], row ny-1 -> g[3]
+                    if (j != (r == 0 ? 0 : ny - 1)) continue;
+                    if (KIND != 2) {
+                        T *p = gslot(2 + r, k, f, i0);
+                        if (WX_IN(p - ghs[2 + r].buf + 1, ghs[2 + r].n, a.status)) *reinterpret_cast<V *>(p) = v;
+                    } else {
+                        if (va) gput(2 + r, k, f, i0, v.x);
+                        if (vb) gput(2 + r, k, f, i0 + 1, v.y);
+                    }
+                }
+            }
+        };
         // F_k of the lane's two columns: its TMEM lane, or shared memory
         auto putF = [&](int k, V v) {
             if constexpr (TMF) {
@@ -381,7 +451,7 @@ __global__ void __launch_bounds__(32 * (TY + 1), 1) step_kernel(const __grid_con
 
         // one level; EDGE selects the masked store path with ghost copies
         auto level = [&](auto edge_tag, int k, const T *pk, const T *pb, V nT, V nQ) {
-            constexpr bool EDGE = decltype(edge_tag)::value;
+            constexpr bool EDGE = decltype(edge_tag)::value == 2;  // masked (ragged) tile
             const R4 A = tA[k], B = tB[k];
             const V wu = V{A.x, A.y}, wd = V{A.z, A.w};
             const V cCk = PK::add(cC, V{B.x, B.y});
@@ -398,29 +468,7 @@ __global__ void __launch_bounds__(32 * (TY + 1), 1) step_kernel(const __grid_con
             curQ = nQ;
 
             // q^{n+1} = q*
-            if (!EDGE) {
-                put2(a, qp, Qs);
-            } else {
-                T *row = a.out + k * lev + fld + (size_t)(j + 1) * a.P;
-                if (va) put(a, row + (i0 + kGhostX), Qs.x);
-                if (vb) put(a, row + (i0 + 1 + kGhostX), Qs.y);
-                if (!a.halo) {  // periodic ghost copies (a sub-domain's come from the exchange)
-                if (va && i0 == 0) put(a, row + (kGhostX + nx), Qs.x);
-                if (vb && i0 + 1 == nx - 1) put(a, row + (kGhostX - 1), Qs.y);
-                if (va && i0 == nx - 1) put(a, row + (kGhostX - 1), Qs.x);
-                if (j == 0) {  // bottom row -> top ghost row
-                    T *g = a.out + k * lev + fld + (size_t)(ny + 1) * a.P;
-                    if (va) put(a, g + (i0 + kGhostX), Qs.x);
-                    if (vb) put(a, g + (i0 + 1 + kGhostX), Qs.y);
-                }
-                if (j == ny - 1) {  // top row -> bottom ghost row
-                    T *g = a.out + k * lev + fld;
-                    if (va) put(a, g + (i0 + kGhostX), Qs.x);
-                    if (vb) put(a, g + (i0 + 1 + kGhostX), Qs.y);
-                }
-                }
-            }
-            qp -= lev;
+            emit(edge_tag, k, 1, Qs);
             const V Qm = EDGE ? V{va ? Qs.x : T(0), vb ? Qs.y : T(0)} : Qs;
             if (SUMS)
                 sumQ.add(Qm, tF[k].z, tF[k].w);
@@ -505,55 +553,31 @@ __global__ void __launch_bounds__(32 * (TY + 1), 1) step_kernel(const __grid_con
                 par = npar;
             }
         };
-        if (edge)
-            run_pass1(std::true_type{});
+        if (kind == 0)
+            run_pass1(std::integral_constant<int, 0>{});
+        else if (kind == 1)
+            run_pass1(std::integral_constant<int, 1>{});
         else
-            run_pass1(std::false_type{});
+            run_pass1(std::integral_constant<int, 2>{});
         if (PHYS) putF(0, PK::add(f_up, h_up));  // F_0 = f_0 + h_0
 
         // ------------- pass 2 (bottom up): T^{n+1}_k = F_k - e_k T^{n+1}_{k-1}
         V Tprev = PK::dup(T(0));
-        T *tp = a.out + (size_t)(j + 1) * a.P + (i0 + kGhostX);  // T plane, level 0
         // listed columns (KMODE 2 with physics) are finished by the side
         // solve, which sums their final T itself: their table-path T stays
         // out of the sums
         constexpr bool SIDE = KMODE == 2 && PHYS;
         const V lmask = V{(SIDE && fl[0] >= 0) ? T(0) : T(1), (SIDE && fl[1] >= 0) ? T(0) : T(1)};
         auto back = [&](auto edge_tag, int k, V tn) {
-            constexpr bool EDGE = decltype(edge_tag)::value;
+            constexpr bool EDGE = decltype(edge_tag)::value == 2;  // masked (ragged) tile
             const R4 Fr = tF[k];
             if (PHYS) {
                 const V ne = (KMODE != 1) ? V{Fr.x, Fr.y} : stE[k * NT + tid];
                 tn = PK::fma(ne, Tprev, tn);
                 Tprev = tn;
             }
-            if (!EDGE) {
-                put2(a, tp + (size_t)k * lev, tn);
-                if (SUMS)
-                    sumT.add(SIDE ? PK::mul(tn, lmask) : tn, Fr.z, Fr.w);
-                else
-                    chk = PK::add(chk, tn);
-                return;
-            }
-            T *row = a.out + k * lev + (size_t)(j + 1) * a.P;
-            if (va) put(a, row + (i0 + kGhostX), tn.x);
-            if (vb) put(a, row + (i0 + 1 + kGhostX), tn.y);
-            if (!a.halo) {
-                if (va && i0 == 0) put(a, row + (kGhostX + nx), tn.x);
-                if (vb && i0 + 1 == nx - 1) put(a, row + (kGhostX - 1), tn.y);
-                if (va && i0 == nx - 1) put(a, row + (kGhostX - 1), tn.x);
-                if (j == 0) {
-                    T *g = a.out + k * lev + (size_t)(ny + 1) * a.P;
-                    if (va) put(a, g + (i0 + kGhostX), tn.x);
-                    if (vb) put(a, g + (i0 + 1 + kGhostX), tn.y);
-                }
-                if (j == ny - 1) {
-                    T *g = a.out + k * lev;
-                    if (va) put(a, g + (i0 + kGhostX), tn.x);
-                    if (vb) put(a, g + (i0 + 1 + kGhostX), tn.y);
-                }
-            }
-            const V tm = V{va ? tn.x : T(0), vb ? tn.y : T(0)};
+            emit(edge_tag, k, 0, tn);
+            const V tm = EDGE ? V{va ? tn.x : T(0), vb ? tn.y : T(0)} : tn;
             if (SUMS)
                 sumT.add(SIDE ? PK::mul(tm, lmask) : tm, Fr.z, Fr.w);
             else
@@ -575,10 +599,12 @@ __global__ void __launch_bounds__(32 * (TY + 1), 1) step_kernel(const __grid_con
                 for (int k = 0; k < nz; ++k) back(edge_tag, k, stF[k * NT + tid]);
             }
         };
-        if (edge)
-            run_pass2(std::true_type{});
+        if (kind == 0)
+            run_pass2(std::integral_constant<int, 0>{});
+        else if (kind == 1)
+            run_pass2(std::integral_constant<int, 1>{});
         else
-            run_pass2(std::false_type{});
+            run_pass2(std::integral_constant<int, 2>{});
 
         if (SUMS) {
             double mT = sumT.total(va, vb), mQ = sumQ.total(va, vb);
@@ -831,6 +857,8 @@ static bool use_tmem(const wx_ctx *c, const StepCfg &g) {
     return tmem_nz(c->t_bytes, c->nz, per_col(c)) && tmem_shape(g.ty, g.kb);
 }
 
+bool feeds_neighbours(const wx_ctx *c) { return c->halo && use_tmem(c, c->cfg); }
+
 bool cfg_fits(const wx_ctx *c, const StepCfg &cfg, int *smem_bytes) {
     const bool tm = use_tmem(c, cfg);
     const SmemPlan p = plan_smem(c->nz, cfg.ty, cfg.stages, cfg.kb, c->t_bytes, per_col(c), tm);
@@ -914,17 +942,35 @@ template <typename T> static void fill_member(const wx_ctx *c, Member<T> &M, lon
     a.n_list = c->n_list;
     a.Uw0 = (const T *)c->Uw0;
     a.Vs0 = (const T *)c->Vs0;
-    a.halo = c->halo ? 1 : 0;
     a.out_n = (long long)(2 * c->field_cells);
+    // ghost lines fed by this grid's edges: its own periodic ghost ring, or
+    // (a decomposed block) its neighbours' -- western, eastern, southern,
+    // northern -- in their new states (every block steps with the same
+    // buffer parity)
+    for (int d = 0; d < 4; ++d) {
+        const wx_ctx *t = (c->halo && c->nbr[d]) ? c->nbr[d] : c;
+        const int tdst = t == c ? dst : 1 - t->cur;
+        GhostLine<T> &g = a.g[d];
+        g.buf = reinterpret_cast<T *>(t->fld[tdst]);
+        g.P = t->P;
+        g.fld = (long long)t->R * t->P;
+        g.lev = 2 * g.fld;
+        g.n = (long long)(2 * t->field_cells);
+        g.off = d == 0 ? (long long)t->P + kGhostX + t->nx        // east ghost column, rows from 1
+              : d == 1 ? (long long)t->P + kGhostX - 1            // west ghost column
+              : d == 2 ? (long long)(t->ny + 1) * t->P + kGhostX  // top ghost row
+                       : (long long)kGhostX;                      // bottom ghost row
+    }
     M.tile0 = tile0;
     M.gx = (c->nx + kTileX - 1) / kTileX;
     M.gy = (c->ny + ty - 1) / ty;
 }
 
-template <typename T, int TY, int KB, int KMODE, bool PHYS, bool SUMS, bool TMF, bool RKB = false>
+template <typename T, int TY, int KB, int KMODE, bool PHYS, bool SUMS, bool TMF, bool RKB = false,
+          bool HALO = false>
 static int launch_batch_t(wx_ctx *const *mem, int n, const StepCfg &cfg, int num_sms, unsigned *status,
                           cudaStream_t s, std::string &err) {
-    auto kern = step_kernel<T, TY, KB, KMODE, PHYS, SUMS, TMF, RKB>;
+    auto kern = step_kernel<T, TY, KB, KMODE, PHYS, SUMS, TMF, RKB, HALO>;
     Members<T> ms;
     long total = 0;
     int nz_max = 1;
@@ -988,6 +1034,8 @@ static int dispatch_ty(wx_ctx *const *mem, int n, const StepCfg &cfg, int sms, u
             if constexpr (!SUMS)
                 if (mem[0]->stage_base >= 0)  // an RK3 stage writing phi^n + (E - phi_s)
                     return launch_batch_t<T, 12, 4, KMODE, PHYS, SUMS, true, true>(mem, n, cfg, sms, st, s, err);
+            if (mem[0]->halo)  // decomposed blocks feeding their neighbours' ghost lines
+                return launch_batch_t<T, 12, 4, KMODE, PHYS, SUMS, true, false, true>(mem, n, cfg, sms, st, s, err);
             return launch_batch_t<T, 12, 4, KMODE, PHYS, SUMS, true>(mem, n, cfg, sms, st, s, err);
         }
     }

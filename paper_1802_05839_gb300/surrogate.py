@@ -4,8 +4,10 @@ Data: columns (T*, q*, kappa_mult) of seeded synthetic states after the
 dynamics of one step, with their exact column-physics tendencies from the
 library's column kernel (wx_physics_columns).  Training: minibatches of the
 normalised rows through wx_mlp_train_step (forward, backward and Adam in the
-library's kernels), cosine-decayed learning rate.  PyTorch only holds device
-memory and reorders rows between calls.
+library's kernels), cosine-decayed learning rate.  Every transpose, cast,
+row gather and denormalisation runs in the library (wx_read_columns_f32,
+wx_convert, wx_gather_rows, wx_mlp_denormalize); PyTorch only allocates
+device memory, and the minibatch order is a seeded host permutation.
 """
 from __future__ import annotations
 
@@ -21,23 +23,30 @@ def _torch():
     return torch
 
 
-def state_columns(ctx, nx, ny, nz=NZ):
-    """The context's current fields as device FP32 columns [nx*ny][nz]."""
+def state_columns(ctx, nx, ny, nz=NZ, out=None):
+    """The context's current fields as device FP32 columns [nx*ny][nz]
+    (into `out` = (T, q) views when given)."""
     torch = _torch()
-    T = torch.empty(nz, ny, nx, dtype=torch.float64, device="cuda")
-    q = torch.empty_like(T)
-    ctx.read_fields_into(T, q)
+    if out is None:
+        out = (torch.empty(nx * ny, nz, dtype=torch.float32, device="cuda"),
+               torch.empty(nx * ny, nz, dtype=torch.float32, device="cuda"))
+    ctx.read_columns_into(out[0], out[1])
     ctx.sync()
-    to_cols = lambda a: a.reshape(nz, -1).t().contiguous().float()
-    return to_cols(T), to_cols(q)
+    return out
 
 
-def case_columns(case, adv_steps):
+def case_columns(case, adv_steps, out=None):
     """(T*, q*, kappa_mult or None, tend) of every column of `case` after
     `adv_steps` full FP32 steps and the dynamics of one more (device FP32
-    tensors; the tendencies computed in FP64 from the FP32 inputs)."""
+    tensors, written into `out` = (Ts, qs, km, tend) views when given; the
+    tendencies computed in FP64 from the FP32 inputs)."""
     torch = _torch()
     nx, ny, nz = case.nx, case.ny, case.nz
+    n = nx * ny
+    if out is None:
+        f32 = lambda *sh: torch.empty(*sh, dtype=torch.float32, device="cuda")
+        out = (f32(n, nz), f32(n, nz), f32(n) if case.kappa_mult is not None else None, f32(n, 2, nz))
+    Ts, qs, km, tend32 = out
     ctx = wx.Context(nx, ny, nz, "f32")
     try:
         ctx.set_params(case)
@@ -46,24 +55,29 @@ def case_columns(case, adv_steps):
             ctx.step(adv_steps)
         ctx.set_params(case, flags=wx.WX_ADVECTION)
         ctx.step(1)
-        Ts, qs = state_columns(ctx, nx, ny, nz)
+        state_columns(ctx, nx, ny, nz, (Ts, qs))
     finally:
         ctx.close()
-    km = None
-    if case.kappa_mult is not None:
-        km = torch.from_numpy(np.ascontiguousarray(case.kappa_mult, np.float32).reshape(-1)).cuda()
+    if km is not None:
+        km.copy_(torch.from_numpy(np.ascontiguousarray(case.kappa_mult, np.float32).reshape(-1)))
     # Targets from the FP64 column kernel: T** - T* is ~1e-4 K, a few FP32
     # ulps of T ~ 280 K, so FP32 targets would be mostly rounding noise.
+    f64 = lambda a: None if a is None else torch.empty(a.shape, dtype=torch.float64, device="cuda")
+    Ts64, qs64, km64 = f64(Ts), f64(qs), f64(km)
+    for a, b in ((Ts, Ts64), (qs, qs64), (km, km64)):
+        if a is not None:
+            wx.wx_convert(a, b)
     c64 = wx.Context(nx, ny, nz, "f64")
     try:
         c64.set_params(case)
         Tout = torch.empty(Ts.shape, dtype=torch.float64, device="cuda")
-        tend = torch.empty(Ts.shape[0], 2, nz, dtype=torch.float64, device="cuda")
-        c64.physics_columns(Ts.double(), qs.double(), km.double() if km is not None else None, Tout, tend)
+        tend = torch.empty(n, 2, nz, dtype=torch.float64, device="cuda")
+        c64.physics_columns(Ts64, qs64, km64, Tout, tend)
         c64.sync()
     finally:
         c64.close()
-    return Ts, qs, km, tend.float()
+    wx.wx_convert(tend, tend32)
+    return Ts, qs, km, tend32
 
 
 CONFIG_SEED = 12345  # the model configuration (kappa_lev profile) served
@@ -74,17 +88,17 @@ def dataset(seeds, nx=256, ny=256, near_singular=False, max_adv=50, config_seed=
     seed (one shared model configuration), advanced (7 seed) mod
     (max_adv + 1) steps first."""
     torch = _torch()
-    parts = []
-    for s in seeds:
+    seeds = list(seeds)
+    n = nx * ny
+    f32 = lambda *sh: torch.empty(*sh, dtype=torch.float32, device="cuda")
+    Ts, qs, tend = f32(len(seeds) * n, NZ), f32(len(seeds) * n, NZ), f32(len(seeds) * n, 2, NZ)
+    km = f32(len(seeds) * n) if near_singular else None
+    for p, s in enumerate(seeds):  # each state's columns straight into its rows
         case = inputs.round_to_f32(inputs.paper_grid_case(nx, ny, NZ, seed=s, near_singular=near_singular,
                                                           config_seed=config_seed))
-        parts.append(case_columns(case, (7 * s) % (max_adv + 1)))
-    Ts = torch.cat([p[0] for p in parts])
-    qs = torch.cat([p[1] for p in parts])
-    km = None
-    if near_singular:
-        km = torch.cat([p[2] if p[2] is not None else torch.ones(p[0].shape[0], device="cuda") for p in parts])
-    tend = torch.cat([p[3] for p in parts])
+        rows = slice(p * n, (p + 1) * n)
+        case_columns(case, (7 * s) % (max_adv + 1),
+                     (Ts[rows], qs[rows], km[rows] if km is not None else None, tend[rows]))
     return Ts, qs, km, tend
 
 
@@ -108,18 +122,22 @@ def train(mlp, X, Yt, n_rows, epochs=4, batch=4096, lr0=1e-3, seed=0, log=None):
     """Adam on shuffled minibatches of the first n_rows rows; returns the
     per-epoch mean loss (device losses read once per epoch)."""
     torch = _torch()
-    g = torch.Generator(device="cpu").manual_seed(seed)
+    rng = np.random.default_rng(seed)  # the minibatch order: a seeded host permutation
     nb = n_rows // batch
     total = epochs * nb
     loss = torch.zeros(max(nb, 1), dtype=torch.float32, device="cuda")
+    Xb = torch.empty(batch, X.shape[1], dtype=X.dtype, device="cuda")
+    Yb = torch.empty(batch, Yt.shape[1], dtype=Yt.dtype, device="cuda")
     hist = []
     step = 0
     for ep in range(epochs):
-        perm = torch.randperm(n_rows, generator=g).cuda()
+        perm = torch.from_numpy(rng.permutation(n_rows).astype(np.int32)).cuda()
         for b in range(nb):
             idx = perm[b * batch:(b + 1) * batch]
             lr = 0.5 * lr0 * (1.0 + np.cos(np.pi * step / total))
-            mlp.train_step(X.index_select(0, idx), Yt.index_select(0, idx), lr, loss=loss[b:])
+            wx.wx_gather_rows(X, idx, Xb)
+            wx.wx_gather_rows(Yt, idx, Yb)
+            mlp.train_step(Xb, Yb, lr, loss=loss[b:])
             step += 1
         hist.append(float(loss[:nb].mean().item()))
         if log:
@@ -133,10 +151,9 @@ def predict(mlp, X):
     torch = _torch()
     Y = torch.empty(X.shape[0], wx.MLP_OUT_PAD, dtype=torch.float32, device="cuda")
     mlp.forward(X, Y)
-    _, _, mo, so = mlp.get_norm()
-    mo = torch.from_numpy(mo).cuda()
-    so = torch.from_numpy(so).cuda()
-    return Y[:, :wx.MLP_OUT] * so + mo
+    P = torch.empty(X.shape[0], wx.MLP_OUT, dtype=torch.float32, device="cuda")
+    mlp.denormalize(Y, P)
+    return P
 
 
 def tendency_error(mlp, Ts, qs, km, tend):
@@ -144,7 +161,8 @@ def tendency_error(mlp, Ts, qs, km, tend):
     all columns: (both halves, heating only, vertical diffusion only)."""
     X, _ = rows(mlp, Ts, qs, km)
     n = Ts.shape[0]
-    P = predict(mlp, X)[:n].double()
-    Y = tend.reshape(n, -1).double()
-    rel = lambda a, b: float((a - b).norm() / b.norm())
+    # an evaluation on the host in FP64 (not part of the method)
+    P = predict(mlp, X)[:n].cpu().numpy().astype(np.float64)
+    Y = tend.reshape(n, -1).cpu().numpy().astype(np.float64)
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
     return rel(P, Y), rel(P[:, :NZ], Y[:, :NZ]), rel(P[:, NZ:], Y[:, NZ:])

@@ -129,6 +129,10 @@ SIGNATURES = [
     ("wx_pf_last_error", ctypes.c_char_p, [_VP]),
     ("wx_surrogate_fallbacks", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_long)]),
     ("wx_set_surrogate_policy", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
+    ("wx_read_columns_f32", ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    ("wx_mlp_denormalize", ctypes.c_int, [_VP, _VP, ctypes.c_long, _VP, _VP]),
+    ("wx_convert", ctypes.c_int, [_VP, _VP, ctypes.c_long, ctypes.c_int, _VP]),
+    ("wx_gather_rows", ctypes.c_int, [_VP, ctypes.c_long, ctypes.c_long, _VP, ctypes.c_long, _VP, _VP]),
     ("wx_destroy", None, [_VP]),
     ("wx_last_error", ctypes.c_char_p, [_VP]),
 ]
@@ -323,6 +327,14 @@ class Context:
         q = _dev(q, "float64", self._n3(), "q", optional=True)
         _check(lib().wx_read_fields_device(self.ptr, _dptr(T), _dptr(q), _stream_ptr(stream)),
                self.ptr)
+
+    def read_columns_into(self, T, q, stream=None):
+        """Device FP32 columns [nx*ny][nz] of T and q (torch tensors, either
+        may be None), asynchronous on `stream`."""
+        n = self._n3()
+        T = _dev(T, "float32", n, "T", optional=True, exact=True)
+        q = _dev(q, "float32", n, "q", optional=True, exact=True)
+        _check(lib().wx_read_columns_f32(self.ptr, _dptr(T), _dptr(q), _stream_ptr(stream)), self.ptr)
 
     def step(self, n_steps=1, stream=None):
         _check(lib().wx_step(self.ptr, int(n_steps), _stream_ptr(stream)), self.ptr)
@@ -613,6 +625,13 @@ class MLP:
         _mcheck(lib().wx_mlp_gradients(self.ptr, _dptr(X), _dptr(Yt), X.shape[0], _dptr(loss),
                                        _stream_ptr(stream)))
 
+    def denormalize(self, Y, out, stream=None):
+        """out [M][116] = Y[:, :116] * std_out + mean_out (device FP32)."""
+        M = int(Y.shape[0])
+        Y = _dev(Y, "float32", M * MLP_OUT_PAD, "Y", exact=True)
+        out = _dev(out, "float32", M * MLP_OUT, "out", exact=True)
+        _mcheck(lib().wx_mlp_denormalize(self.ptr, _dptr(Y), M, _dptr(out), _stream_ptr(stream)))
+
     def train_step(self, X, Yt, lr, loss=None, stream=None):
         M, X = self._rows(X)
         Yt = _dev(Yt, "float32", M * MLP_OUT_PAD, "Yt")
@@ -786,3 +805,31 @@ class Decomposition:
         """Launch configuration of block r (all blocks share it)."""
         b = _Member(_VP(lib().wx_dom_block(self.ptr, int(r))), 0, 0, 0, self.dtype)
         return b.step_config()
+
+
+def wx_convert(src, dst, stream=None):
+    """dst = src converted between FP32 and FP64 (device tensors of one size)."""
+    n = src.numel()
+    to64 = str(dst.dtype) == "torch.float64"
+    src = _dev(src, "float32" if to64 else "float64", n, "src", exact=True)
+    dst = _dev(dst, "float64" if to64 else "float32", n, "dst", exact=True)
+    code = lib().wx_convert(_dptr(src), _dptr(dst), n, int(to64), _stream_ptr(stream))
+    if code != 0:
+        raise WxError(code, lib().wx_mlp_last_error().decode())
+
+
+def wx_gather_rows(src, idx, dst, stream=None):
+    """dst[r] = src[idx[r]] for rows of a 2-D device tensor (row bytes a
+    multiple of 16); idx a device int32 tensor (an index outside src's rows
+    gives a zero row)."""
+    n = int(idx.numel())
+    rb = src.shape[1] * src.element_size()
+    if dst.dtype != src.dtype or dst.shape[1] != src.shape[1] or dst.shape[0] < n:
+        raise ValueError("wx_gather_rows: dst must hold n rows of src's type and width")
+    idx = _dev(idx, "int32", n, "idx", exact=True)
+    if not (src.is_contiguous() and dst.is_contiguous()) or not (src.is_cuda and dst.is_cuda):
+        raise ValueError("wx_gather_rows: contiguous CUDA tensors required")
+    code = lib().wx_gather_rows(_dptr(src), int(src.shape[0]), rb, _dptr(idx), n, _dptr(dst),
+                                _stream_ptr(stream))
+    if code != 0:
+        raise WxError(code, lib().wx_mlp_last_error().decode())
