@@ -361,9 +361,10 @@ def variant_plain(dtype, steps, nx=1581, ny=1301, nz=58):
 
 def variant_decomposed(steps, nx=1581, ny=1301, nz=58, layouts=((2, 2), (4, 4)), plain_ms=None):
     """The paper grid split into px x py blocks (simulated ranks on one GPU):
-    per step one step-kernel launch over all blocks, which writes every
-    block's edge lines into its neighbours' ghost lines; the algorithmic
-    bytes add those halo strips (read + written) to the step's."""
+    per step one step-kernel launch over all blocks, then one halo exchange
+    launch that copies every block's edge lines into its neighbours' ghost
+    lines; the algorithmic bytes add those halo strips (read + written) to
+    the step's."""
     import torch
     from paper_1802_05839_gb300 import wx
     case = make_case("f32", nx, ny, nz)

@@ -336,8 +336,8 @@ const char *wx_ens_last_error(const wx_ens *e);
  * decomposes only in i and j, never in k).  Each block is a sub-domain
  * context with its own resident fields and ghost ring; a step is the step
  * kernel over every block (one launch over all blocks' tiles, like an
- * ensemble) that writes no periodic ghost copies, then ONE halo-exchange
- * launch that fills every block's four depth-1 ghost strips (west and east
+ * ensemble), then ONE halo-exchange launch that overwrites every block's
+ * four depth-1 ghost strips (west and east
  * columns, south and north rows, for T and q at every level) from its
  * neighbours' edge lines.  Corners are not exchanged: the 7-point stencil
  * and the upwind fluxes never read them.  The blocks run as simulated

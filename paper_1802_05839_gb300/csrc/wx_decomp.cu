@@ -3,15 +3,14 @@
 // F decomposition table; Sec. 5.4, where the exchange is the communication
 // share of the strong-scaling runs), run as simulated ranks on one GPU.
 //
-// Every block is an ordinary context in halo mode: its step writes its edge
-// values into its neighbours' ghost lines (in their new states) instead of
-// its own periodic ghost ring, and its west-face / south-face winds of the
-// first column / row come from its neighbours.  A step is one launch of the
-// step kernel over all blocks' tiles.  The exchange kernel, which copies
-// each block's four edge lines (both fields, every level) into its
-// neighbours' ghost lines, runs after a load and after steps whose side
-// solve rewrote edge values.  Corners are not exchanged: neither the 7-point
-// diffusion nor the upwind fluxes read them.  Because every interior cell sees the same
+// Every block is an ordinary context whose west-face / south-face winds of
+// the first column / row come from its neighbours.  A step is one launch of
+// the step kernel over all blocks' tiles (each block's own periodic ghost
+// copies are made and then overwritten), then one launch of the exchange
+// kernel, which copies each block's four edge lines (both fields, every
+// level) into its neighbours' ghost lines; it also runs after a load.
+// Corners are not exchanged: neither the 7-point diffusion nor the upwind
+// fluxes read them.  Because every interior cell sees the same
 // neighbour values, winds, coefficients and tables as in the undecomposed
 // grid, and its arithmetic does not depend on where its tile starts, the
 // blocks' interiors equal the undecomposed step bit for bit.
@@ -210,7 +209,6 @@ extern "C" int wx_dom_create(int nx, int ny, int nz, int dtype, int px, int py, 
                 return bail(rc);
             }
             d->blk.push_back(c);
-            c->halo = true;  // neighbours (nbr) are set once every block exists
             if (cudaMalloc(&c->Uw0, (size_t)nyr * c->t_bytes) != cudaSuccess ||
                 cudaMalloc(&c->Vs0, (size_t)nxr * c->t_bytes) != cudaSuccess ||
                 cudaMemset(c->Uw0, 0, (size_t)nyr * c->t_bytes) != cudaSuccess ||
@@ -227,14 +225,6 @@ extern "C" int wx_dom_create(int nx, int ny, int nz, int dtype, int px, int py, 
         cudaGetLastError();
         d->err = "wx_dom_create: CUDA set-up failed";
         return bail(WX_ECUDA);
-    }
-    // each block's edges feed its neighbours' ghost lines (the plan's sources
-    // seen from the other side: my western neighbour is the block whose east
-    // ghost column my column 0 fills)
-    for (int r = 0; r < (int)d->blk.size(); ++r) {
-        wx_halo_strip pl[4];
-        plan_of(d->xs, d->ys, r, pl);
-        for (int s = 0; s < 4; ++s) d->blk[r]->nbr[s] = d->blk[pl[s].src];
     }
     int rc = build_strips(d);
     if (rc != WX_OK) return bail(rc);
@@ -360,24 +350,16 @@ extern "C" int wx_dom_step(wx_dom *d, int n_steps, void *stream) {
     if (rc != WX_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     d->last_stream = s;
-    // The step kernel's TMEM variant writes every block's edges into its
-    // neighbours' ghost lines itself.  The side solve of listed columns
-    // (WX_F32 / WX_MIXED with kappa_mult and physics) rewrites some edge
-    // values after that, and the other variants (FP64, nz > 64) copy edges
-    // only within a block, so those steps refresh the ghost lines with the
-    // exchange kernel.
-    bool side = false;
-    for (auto *c : d->blk)
-        side = side || (c->n_list > 0 && c->dtype != WX_F64 && (c->flags & WX_PHYSICS)) || !feeds_neighbours(c);
+    // every step: the step kernel over all blocks (with the side solve of
+    // listed columns, when there are any), then the exchange of the new
+    // states' edge lines
     long launches = 0;
     for (int n = 0; n < n_steps; ++n) {
         rc = launch_batch(d->blk.data(), (int)d->blk.size(), d->cfg, d->d_status, s, &launches, d->err);
         if (rc != WX_OK) return rc;
-        if (side) {
-            rc = launch_exchange(d, s);
-            if (rc != WX_OK) return rc;
-            ++launches;
-        }
+        rc = launch_exchange(d, s);
+        if (rc != WX_OK) return rc;
+        ++launches;
     }
     for (auto *c : d->blk) c->last_stream = s;
     d->last_launches = launches;

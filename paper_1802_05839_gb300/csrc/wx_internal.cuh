@@ -84,20 +84,6 @@ template <typename T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };
 
-// One ghost line a tile's edge values are copied into, in the new state of
-// this grid (its periodic ghost ring) or of a neighbouring block:
-//   g[0] receives column 0 (the east ghost column of the western neighbour),
-//   g[1] column nx-1 (the west ghost column of the eastern neighbour),
-//   g[2] row 0 (the top ghost row of the southern neighbour),
-//   g[3] row ny-1 (the bottom ghost row of the northern neighbour).
-// Element (level k, field f, row j | column i) lives at
-//   buf[off + k*lev + f*fld + j*P]  (g[0], g[1])  or  buf[off + k*lev + f*fld + i]  (g[2], g[3]).
-template <typename T> struct GhostLine {
-    T *buf;
-    long long off, lev, fld, n;  // n: elements of buf (bounds-checked build)
-    int P;
-};
-
 template <typename T> struct StepArgs {
     T *out;                       // new state (planar fields)
     const T *U, *V;               // face winds [ny][nx]
@@ -116,9 +102,6 @@ template <typename T> struct StepArgs {
     // ([ny]) and the south-face winds of row 0 ([nx]) come from the
     // neighbours (nullptr: periodic within this grid)
     const T *Uw0, *Vs0;
-    // where the edge values of the new state are copied (GhostLine): the
-    // grid's own periodic ghost lines, or a decomposed block's neighbours'
-    GhostLine<T> g[4];
     long long out_n;              // elements of `out` (bounds-checked build)
 };
 
@@ -274,13 +257,9 @@ struct wx_ctx {
 
     // sub-domain of a wx_dom: neighbours' face winds at the west column and
     // the south row (device, storage type; host FP64 copies for the CFL
-    // check), and no periodic ghost copies in the step
-    bool halo = false;
+    // check)
     void *Uw0 = nullptr, *Vs0 = nullptr;
     std::vector<double> Uw0_h, Vs0_h;
-    // the blocks whose new-state ghost lines receive this block's edges:
-    // western, eastern, southern, northern neighbour (halo mode)
-    wx_ctx *nbr[4] = {nullptr, nullptr, nullptr, nullptr};
 
     wx::StepCfg cfg;
     bool cfg_forced = false;
@@ -312,10 +291,6 @@ int setup_mixed(wx_ctx *c, const double *km64);
 // or WX_F32 with kappa_mult); with sums, their energy corrections.
 int launch_mixed_fixup(wx_ctx *c, int dst, bool sums, cudaStream_t s);
 bool cfg_fits(const wx_ctx *c, const StepCfg &cfg, int *smem_bytes);
-// a decomposed block whose step kernel writes its edges into its
-// neighbours' ghost lines itself (the TMEM variant); others rely on the
-// halo exchange kernel after every step
-bool feeds_neighbours(const wx_ctx *c);
 int encode_tmap(wx_ctx *c, int which, int ty, int kb);
 // descriptor of the interior boxes (kTileX x ty x 2 x kb) of buffer `which`
 int encode_tmap_interior(wx_ctx *c, int which, int ty, int kb, CUtensorMap *out);

@@ -128,12 +128,11 @@ __device__ __forceinline__ void consumer_sync(int nthreads) {
 // sized for it): the explicit minimum of 1 block lets ptxas use the whole
 // register budget of the block (128 registers at 416 threads) instead of
 // capping it for a second resident block and spilling.
-template <typename T, int TY, int KB, int KMODE, bool PHYS, bool SUMS, bool TMF, bool RKB, bool HALO>
+template <typename T, int TY, int KB, int KMODE, bool PHYS, bool SUMS, bool TMF, bool RKB>
 __global__ void __launch_bounds__(32 * (TY + 1), 1) step_kernel(const __grid_constant__ Members<T> ms, const int S,
                                                                 const int PF) {
     static_assert(!TMF || (std::is_same<T, float>::value && KMODE != 1), "TMEM column state: FP32 table paths");
     static_assert(!RKB || (TMF && !SUMS), "RK3 stage launches: TMEM variant, no sums");
-    static_assert(!HALO || (TMF && !RKB), "decomposed blocks: TMEM variant");
     using PK = Pk<T>;
     using V = typename PK::V;
     using R4 = Q4<T>;
@@ -264,10 +263,6 @@ __global__ void __launch_bounds__(32 * (TY + 1), 1) step_kernel(const __grid_con
     uint32_t par = 0;
     bool ok = true;
     int cur_member = -1;
-    // a decomposed block's four ghost-line descriptors, staged with the
-    // table and read (volatile) only where a border tile stores its edges,
-    // so that they hold no registers across the level loops
-    __shared__ GhostLine<T> ghs[HALO ? 4 : 1];
 
     // face winds of a tile's two columns (a, b): Ue, Uw, Vn, Vs each
     struct Winds {
@@ -306,7 +301,6 @@ __global__ void __launch_bounds__(32 * (TY + 1), 1) step_kernel(const __grid_con
         if (mi != cur_member) {  // stage the member's per-level table
             consumer_sync(NT);
             for (int e = tid; e < kTabRec * nz; e += NT) tab[e] = a.tab[e];
-            if (HALO && tid < 4) ghs[tid] = a.g[tid];
             consumer_sync(NT);
             cur_member = mi;
         }
@@ -367,17 +361,11 @@ __global__ void __launch_bounds__(32 * (TY + 1), 1) step_kernel(const __grid_con
         V chk = PK::dup(T(0));
         ColSum2<T> sumQ, sumT;
         // A level's new pair of field f into the new state (kind as above),
-        // then its copies into the ghost lines the tile's edges feed: this
-        // grid's periodic ghost ring, or a decomposed block's neighbours'.
-        // element x (row j of g[0..1], column i of g[2..3]) of level k, field f
-        auto gslot = [&](int d, int k, int f, long long x) -> T * {
-            const volatile GhostLine<T> &g = ghs[d];
-            return g.buf + (g.off + k * g.lev + f * g.fld + x * (d < 2 ? (long long)g.P : 1ll));
-        };
-        auto gput = [&](int d, int k, int f, long long x, T v) {
-            T *p = gslot(d, k, f, x);
-            if (WX_IN(p - ghs[d].buf, ghs[d].n, a.status)) *p = v;
-        };
+        // then its copies into the grid's periodic ghost ring, addressed from
+        // the store: column 0 -> ghost column nx, column nx-1 -> ghost column
+        // -1, row 0 -> ghost row ny+1, row ny-1 -> ghost row 0.  (A block of
+        // a decomposed grid gets its ghost lines from the halo exchange that
+        // follows the step; these copies are then overwritten.)
         auto emit = [&](auto kind_tag, int k, int f, V v) {
             constexpr int KIND = decltype(kind_tag)::value;
             T *dst = a.out + (size_t)k * lev + (size_t)f * fld + rowoff;
@@ -388,41 +376,19 @@ __global__ void __launch_bounds__(32 * (TY + 1), 1) step_kernel(const __grid_con
                 if (vb) put(a, dst + 1, v.y);
             }
             if (KIND == 0) return;
-            if constexpr (!HALO) {
-                // this grid's periodic ghost ring, addressed from dst: column 0
-                // -> ghost column nx, column nx-1 -> ghost column -1, row 0 ->
-                // ghost row ny+1, row ny-1 -> ghost row 0
-                if (gwarp) {
-                    if (gc0) put(a, dst + nx, v.x);
-                    if (gclx) put(a, dst - nx, v.x);
-                    if (gcly) put(a, dst + 1 - nx, v.y);
-                }
-                for (int r = 0; r < 2; ++r) {  // warp-uniform; both rows when ny = 1
-                    if (j != (r == 0 ? 0 : ny - 1)) continue;
-                    T *g = r == 0 ? dst + (size_t)ny * a.P : dst - (size_t)ny * a.P;
-                    if (KIND != 2) {
-                        put2(a, g, v);
-                    } else {
-                        if (va) put(a, g, v.x);
-                        if (vb) put(a, g + 1, v.y);
-                    }
-                }
-            } else {
-                // a decomposed block: the ghost lines of its neighbours' new states
-                if (gwarp) {
-                    if (gc0) gput(0, k, f, j, v.x);
-                    if (gclx) gput(1, k, f, j, v.x);
-                    if (gcly) gput(1, k, f, j, v.y);
-                }
-                for (int r = 0; r < 2; ++r) {  // row 0 -> g[2], row ny-1 -> g[3]
-                    if (j != (r == 0 ? 0 : ny - 1)) continue;
-                    if (KIND != 2) {
-                        T *p = gslot(2 + r, k, f, i0);
-                        if (WX_IN(p - ghs[2 + r].buf + 1, ghs[2 + r].n, a.status)) *reinterpret_cast<V *>(p) = v;
-                    } else {
-                        if (va) gput(2 + r, k, f, i0, v.x);
-                        if (vb) gput(2 + r, k, f, i0 + 1, v.y);
-                    }
+            if (gwarp) {
+                if (gc0) put(a, dst + nx, v.x);
+                if (gclx) put(a, dst - nx, v.x);
+                if (gcly) put(a, dst + 1 - nx, v.y);
+            }
+            for (int r = 0; r < 2; ++r) {  // warp-uniform; both rows when ny = 1
+                if (j != (r == 0 ? 0 : ny - 1)) continue;
+                T *g = r == 0 ? dst + (size_t)ny * a.P : dst - (size_t)ny * a.P;
+                if (KIND != 2) {
+                    put2(a, g, v);
+                } else {
+                    if (va) put(a, g, v.x);
+                    if (vb) put(a, g + 1, v.y);
                 }
             }
         };
@@ -857,8 +823,6 @@ static bool use_tmem(const wx_ctx *c, const StepCfg &g) {
     return tmem_nz(c->t_bytes, c->nz, per_col(c)) && tmem_shape(g.ty, g.kb);
 }
 
-bool feeds_neighbours(const wx_ctx *c) { return c->halo && use_tmem(c, c->cfg); }
-
 bool cfg_fits(const wx_ctx *c, const StepCfg &cfg, int *smem_bytes) {
     const bool tm = use_tmem(c, cfg);
     const SmemPlan p = plan_smem(c->nz, cfg.ty, cfg.stages, cfg.kb, c->t_bytes, per_col(c), tm);
@@ -943,34 +907,15 @@ template <typename T> static void fill_member(const wx_ctx *c, Member<T> &M, lon
     a.Uw0 = (const T *)c->Uw0;
     a.Vs0 = (const T *)c->Vs0;
     a.out_n = (long long)(2 * c->field_cells);
-    // ghost lines fed by this grid's edges: its own periodic ghost ring, or
-    // (a decomposed block) its neighbours' -- western, eastern, southern,
-    // northern -- in their new states (every block steps with the same
-    // buffer parity)
-    for (int d = 0; d < 4; ++d) {
-        const wx_ctx *t = (c->halo && c->nbr[d]) ? c->nbr[d] : c;
-        const int tdst = t == c ? dst : 1 - t->cur;
-        GhostLine<T> &g = a.g[d];
-        g.buf = reinterpret_cast<T *>(t->fld[tdst]);
-        g.P = t->P;
-        g.fld = (long long)t->R * t->P;
-        g.lev = 2 * g.fld;
-        g.n = (long long)(2 * t->field_cells);
-        g.off = d == 0 ? (long long)t->P + kGhostX + t->nx        // east ghost column, rows from 1
-              : d == 1 ? (long long)t->P + kGhostX - 1            // west ghost column
-              : d == 2 ? (long long)(t->ny + 1) * t->P + kGhostX  // top ghost row
-                       : (long long)kGhostX;                      // bottom ghost row
-    }
     M.tile0 = tile0;
     M.gx = (c->nx + kTileX - 1) / kTileX;
     M.gy = (c->ny + ty - 1) / ty;
 }
 
-template <typename T, int TY, int KB, int KMODE, bool PHYS, bool SUMS, bool TMF, bool RKB = false,
-          bool HALO = false>
+template <typename T, int TY, int KB, int KMODE, bool PHYS, bool SUMS, bool TMF, bool RKB = false>
 static int launch_batch_t(wx_ctx *const *mem, int n, const StepCfg &cfg, int num_sms, unsigned *status,
                           cudaStream_t s, std::string &err) {
-    auto kern = step_kernel<T, TY, KB, KMODE, PHYS, SUMS, TMF, RKB, HALO>;
+    auto kern = step_kernel<T, TY, KB, KMODE, PHYS, SUMS, TMF, RKB>;
     Members<T> ms;
     long total = 0;
     int nz_max = 1;
@@ -1034,8 +979,6 @@ static int dispatch_ty(wx_ctx *const *mem, int n, const StepCfg &cfg, int sms, u
             if constexpr (!SUMS)
                 if (mem[0]->stage_base >= 0)  // an RK3 stage writing phi^n + (E - phi_s)
                     return launch_batch_t<T, 12, 4, KMODE, PHYS, SUMS, true, true>(mem, n, cfg, sms, st, s, err);
-            if (mem[0]->halo)  // decomposed blocks feeding their neighbours' ghost lines
-                return launch_batch_t<T, 12, 4, KMODE, PHYS, SUMS, true, false, true>(mem, n, cfg, sms, st, s, err);
             return launch_batch_t<T, 12, 4, KMODE, PHYS, SUMS, true>(mem, n, cfg, sms, st, s, err);
         }
     }

@@ -34,11 +34,7 @@ def decomposed(case, dtype, n, px, py, xs=None, ys=None, flags=FLAGS):
     d.load_fields(case.T, case.q, case.U, case.V)
     d.step(n)
     d.sync()
-    # blocks on the TMEM variant write their edges into their neighbours'
-    # ghost lines themselves (1 launch per step); the others take the halo
-    # exchange kernel after every step (2)
-    per_step = 1 if d.block_step_config(0)["ty"] == 12 else 2
-    launches = (d.last_launches(), per_step)
+    launches = d.last_launches()  # the step kernel and the exchange kernel per step
     out = d.read_fields() + (d.sums() if flags & wx.WX_SUMS else (None, None))
     d.close()
     return out, launches
@@ -56,17 +52,15 @@ SPLITS = [  # px, py, xsplit, ysplit
 @pytest.mark.parametrize("dtype,nz", [("f32", 58), ("f64", 58), ("f32", 12)])
 @pytest.mark.parametrize("px,py,xs,ys", SPLITS)
 def test_blocks_equal_the_undecomposed_step_bitwise(dtype, nz, px, py, xs, ys):
-    """FP32 at 58 levels: the TMEM variant, whose step kernel writes every
-    block's edges into its neighbours' ghost lines; FP64, and FP32 with 12
-    levels (8-row tiles): the halo exchange kernel after every step."""
+    """FP32 at 58 levels (the TMEM variant), FP64, and FP32 with 12 levels
+    (8-row tiles)."""
     case = inputs.paper_grid_case(45, 38, nz, seed=5)
     if dtype == "f32":
         case = inputs.round_to_f32(case)
     Ta, qa, _, _ = single(case, dtype, 10)
-    (Tb, qb, _, _), (launches, per_step) = decomposed(case, dtype, 10, px, py, xs, ys)
+    (Tb, qb, _, _), launches = decomposed(case, dtype, 10, px, py, xs, ys)
     assert np.array_equal(Ta, Tb) and np.array_equal(qa, qb)
-    assert launches == 10 * per_step
-    assert per_step == (1 if (dtype, nz) == ("f32", 58) else 2)
+    assert launches == 10 * 2
 
 
 @pytest.mark.parametrize("dtype", ["f32", "mixed"])
@@ -111,8 +105,8 @@ def test_combined_sums(dtype):
         case = inputs.round_to_f32(case)
     flags = FLAGS | wx.WX_SUMS
     _, _, ma, ea = single(case, dtype, 5, flags)
-    (Tb, qb, mb, eb), (launches, per_step) = decomposed(case, dtype, 5, 2, 2, [0, 7, 60], [0, 30, 44], flags)
-    assert len(mb) == 5 and launches == 5 * (per_step + 4)  # + one sums kernel per block
+    (Tb, qb, mb, eb), launches = decomposed(case, dtype, 5, 2, 2, [0, 7, 60], [0, 30, 44], flags)
+    assert len(mb) == 5 and launches == 5 * (2 + 4)  # + one sums kernel per block
     assert np.max(np.abs(mb - ma) / np.abs(ma)) <= 1e-12
     assert np.max(np.abs(eb - ea) / np.abs(ea)) <= 1e-12
     w = case.h ** 2 * case.dz[:, None, None]
