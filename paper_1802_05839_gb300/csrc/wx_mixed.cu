@@ -103,58 +103,49 @@ __global__ void flag_factor_kernel(const double *lev, const double *km, const in
     }
 }
 
-// One thread per listed column (warps of listed work only): the elimination
-// from the top of the T* the step kernel parked -- in FP64 for the first
-// n64 columns (dominance ratio below the threshold), in FP32 for the rest --
-// then the FP32 back substitution plus the parked heating.  The column's T
-// (and its ghost copies) in the new state is overwritten; with sums, the
-// column's own FP64 sum of T dz is recorded for the finalize kernel (the
-// step kernel leaves listed columns out of its T sums).  Both sweeps go
-// kFixChunk levels at a time: a chunk's loads (coalesced factors and parked
-// values) are issued before its recurrence and stores, so that their
-// latencies overlap.
-constexpr int kFixChunk = 8;
+// Both sweeps go kSideChunk levels at a time: a chunk's loads (coalesced
+// factors and parked values) are issued before its recurrence and stores,
+// so that their latencies overlap.
+constexpr int kSideChunk = 8;
 
+// Elimination from the top, f_k = (T*_k - c_k f_{k+1}) / m_k with the
+// column's precomputed (1/m_k, c_k/m_k): in FP64 (F = double) for weakly
+// dominant columns, else in FP32.  r[k*st] holds T*_k; f_k (rounded to
+// FP32) goes to fo[k*fst] (shared memory, or r itself).
 template <typename F>
-__device__ __forceinline__ void eliminate_from_top(const double2 *__restrict__ fac, float *__restrict__ r, long nflag,
-                                                   long f, size_t st, int nz) {
+__device__ __forceinline__ void side_eliminate(const double2 *__restrict__ fac, const float *r, long nflag, long f,
+                                               size_t st, int nz, float *fo, size_t fst) {
     F fu = F(0);
-    for (int k0 = nz - 1; k0 >= 0; k0 -= kFixChunk) {
-        double2 c2[kFixChunk];
-        float ts[kFixChunk];
+    for (int k0 = nz - 1; k0 >= 0; k0 -= kSideChunk) {
+        double2 c2[kSideChunk];
+        float ts[kSideChunk];
 #pragma unroll
-        for (int u = 0; u < kFixChunk; ++u) {
+        for (int u = 0; u < kSideChunk; ++u) {
             const int k = k0 - u;
             c2[u] = k >= 0 ? fac[(size_t)k * nflag + f] : make_double2(0.0, 0.0);
             ts[u] = k >= 0 ? r[k * st] : 0.f;
         }
 #pragma unroll
-        for (int u = 0; u < kFixChunk; ++u) {
+        for (int u = 0; u < kSideChunk; ++u) {
             const int k = k0 - u;
             if (k >= 0) {
                 fu = fma(-(F)c2[u].y, fu, (F)c2[u].x * (F)ts[u]);  // (T*_k - c_k f_{k+1}) / m_k
-                r[k * st] = (float)fu;
+                fo[k * fst] = (float)fu;
             }
         }
     }
 }
 
-__global__ void __launch_bounds__(128, 6) mixed_fixup_kernel(const int *__restrict__ list, long nflag, long n64,
-                                                          const double2 *__restrict__ fac,
-                                                          const float *__restrict__ fe, float *__restrict__ side,
-                                                          const Q4<float> *__restrict__ dz2, float *__restrict__ out,
-                                                          double *__restrict__ corr, int nx, int ny, int nz, int P,
-                                                          int R, unsigned *__restrict__ status) {
-    const long f = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= nflag) return;
-    const int col = list[f], i = col % nx, j = col / nx;
-    if (!WX_IN(col, (long long)nx * ny, status)) return;
-    float *r = side + f;  // r[2k*nflag]: T*_k, overwritten by f_k; r[(2k+1)*nflag]: dt*H_k
-    const size_t st = 2 * (size_t)nflag;
-    if (f < n64)
-        eliminate_from_top<double>(fac, r, nflag, f, st, nz);  // weakly dominant: FP64
-    else
-        eliminate_from_top<float>(fac, r, nflag, f, st, nz);   // other kappa_mult != 1 columns
+// Back substitution from the bottom, x_k = f_k - e_k x_{k-1}, then T = x + dt*H
+// into the column (i, j) of the new state `out` and its periodic ghost
+// copies; with corr, the column's sum of T dz (dz as hi + lo floats, exact
+// product error and TwoSum written as round-to-nearest intrinsics so that
+// nothing is contracted) goes to corr[f].
+__device__ __forceinline__ void side_back(const float *__restrict__ fe, const float *r, long nflag, long f,
+                                          size_t st, const float *fi, size_t fst, int nz,
+                                          const Q4<float> *__restrict__ dz2,
+                                          float *__restrict__ out, int nx, int ny, int P, int R, int i, int j,
+                                          double *__restrict__ corr, unsigned *status) {
     const size_t lev = (size_t)2 * R * P;
     const int ip = i + kGhostX;
     float *col0 = out + (size_t)(j + 1) * P;  // level 0 row of the column's T
@@ -164,27 +155,24 @@ __global__ void __launch_bounds__(128, 6) mixed_fixup_kernel(const int *__restri
     };
     float x = 0.f;
     float sE = 0.f, cE = 0.f;  // compensated sum of T dz
-    for (int k0 = 0; k0 < nz; k0 += kFixChunk) {
-        float fk[kFixChunk], ek[kFixChunk], hk[kFixChunk];
+    for (int k0 = 0; k0 < nz; k0 += kSideChunk) {
+        float fk[kSideChunk], ek[kSideChunk], hk[kSideChunk];
 #pragma unroll
-        for (int u = 0; u < kFixChunk; ++u) {
+        for (int u = 0; u < kSideChunk; ++u) {
             const int k = k0 + u;
             const bool in = k < nz;
             ek[u] = in ? fe[(size_t)k * nflag + f] : 0.f;
-            fk[u] = in ? r[k * st] : 0.f;
+            fk[u] = in ? fi[k * fst] : 0.f;
             hk[u] = in ? r[k * st + nflag] : 0.f;
         }
 #pragma unroll
-        for (int u = 0; u < kFixChunk; ++u) {
+        for (int u = 0; u < kSideChunk; ++u) {
             const int k = k0 + u;
             if (k >= nz) break;
             x = fmaf(-ek[u], x, fk[u]);
             const float tn = x + hk[u];
             float *row = col0 + k * lev;
             if (corr) {
-                // T dz with dz as hi + lo floats: exact product error and
-                // TwoSum, written as round-to-nearest intrinsics so that
-                // nothing is contracted
                 const float dzh = dz2[k].z, dzl = dz2[k].w;
                 const float p = __fmul_rn(tn, dzh);
                 const float pe = __fmaf_rn(tn, dzl, __fmaf_rn(tn, dzh, -p));
@@ -203,9 +191,61 @@ __global__ void __launch_bounds__(128, 6) mixed_fixup_kernel(const int *__restri
     if (corr) corr[f] = (double)sE + (double)cE;
 }
 
+// The whole side solve of listed column f (column index col = j*nx + i);
+// fb[k*fst] holds f_k between the sweeps.
+__device__ __forceinline__ void side_column(const int *__restrict__ list, long nflag, long n64,
+                                            const double2 *__restrict__ fac, const float *__restrict__ fe,
+                                            const float *__restrict__ side, const Q4<float> *__restrict__ dz2,
+                                            float *__restrict__ out, double *__restrict__ corr, int nx, int ny,
+                                            int nz, int P, int R, long f, float *fb, size_t fst, unsigned *status) {
+    const int col = list[f], i = col % nx, j = col / nx;
+    if (!WX_IN(col, (long long)nx * ny, status)) return;
+    const float *r = side + f;  // r[2k*nflag]: T*_k; r[(2k+1)*nflag]: dt*H_k
+    const size_t st = 2 * (size_t)nflag;
+    if (f < n64)
+        side_eliminate<double>(fac, r, nflag, f, st, nz, fb, fst);  // weakly dominant: FP64
+    else
+        side_eliminate<float>(fac, r, nflag, f, st, nz, fb, fst);   // other kappa_mult != 1 columns
+    side_back(fe, r, nflag, f, st, fb, fst, nz, dz2, out, nx, ny, P, R, i, j, corr, status);
+}
+
+// One thread per listed column (warps of listed work only): the side solve
+// above.  The column's T (and its ghost copies) in the new state is
+// overwritten; with sums, the column's own FP64 sum of T dz is recorded for
+// the finalize kernel (the step kernel leaves listed columns out of its T
+// sums).  With nz <= kFixSmemNz the f_k stay in shared memory between the
+// sweeps ([k][thread]); otherwise they overwrite the parked T* in place.
+constexpr int kFixThreads = 128, kFixSmemNz = 64;
+template <bool SM>
+__global__ void __launch_bounds__(kFixThreads, 6) mixed_fixup_kernel(const int *__restrict__ list, long nflag, long n64,
+                                                          const double2 *__restrict__ fac,
+                                                          const float *__restrict__ fe, float *__restrict__ side,
+                                                          const Q4<float> *__restrict__ dz2, float *__restrict__ out,
+                                                          double *__restrict__ corr, int nx, int ny, int nz, int P,
+                                                          int R, unsigned *__restrict__ status) {
+    extern __shared__ float fsh[];
+    const long f = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nflag) return;
+    if (SM)
+        side_column(list, nflag, n64, fac, fe, side, dz2, out, corr, nx, ny, nz, P, R, f, fsh + threadIdx.x,
+                    (size_t)kFixThreads, status);
+    else
+        side_column(list, nflag, n64, fac, fe, side, dz2, out, corr, nx, ny, nz, P, R, f, side + f,
+                    2 * (size_t)nflag, status);
+}
+
 int launch_mixed_fixup(wx_ctx *c, int dst, bool sums, cudaStream_t s) {
-    const int nt = 128;
-    mixed_fixup_kernel<<<(unsigned)((c->n_list + nt - 1) / nt), nt, 0, s>>>(
+    const int nt = kFixThreads;
+    const bool sm = c->nz <= kFixSmemNz;
+    auto kern = sm ? mixed_fixup_kernel<true> : mixed_fixup_kernel<false>;
+    static bool carveout = false;  // six blocks' f_k in shared memory per SM
+    if (!carveout) {
+        WX_CK(cudaFuncSetAttribute(mixed_fixup_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   cudaSharedmemCarveoutMaxShared),
+              "fixup carveout");
+        carveout = true;
+    }
+    kern<<<(unsigned)((c->n_list + nt - 1) / nt), nt, sm ? (size_t)nt * c->nz * sizeof(float) : 0, s>>>(
         c->flag_list, c->n_list, c->n_flag, (const double2 *)c->flag_fac, c->flag_e, c->flag_side,
         (const Q4<float> *)c->tab + REC_F * c->nz, (float *)c->fld[dst], sums ? c->flag_corr : nullptr, c->nx,
         c->ny, c->nz, c->P, c->R, c->d_status);

@@ -89,6 +89,38 @@ template <> struct ColSum2<float> {
         return (va ? (double)s.x + (double)c.x : 0.0) + (vb ? (double)s.y + (double)c.y : 0.0);
     }
 };
+
+// A float pair (s, c) standing for s + c with |c| <= ulp(s)/2: the tile's
+// sums are reduced in these, with error-free TwoSum / Fast2Sum steps written
+// as round-to-nearest intrinsics, so that the reduction takes no FP64
+// instruction (a warp's FP64 add occupies its sub-core's FP64 unit for
+// tens of cycles on this part).
+struct FF {
+    float s, c;
+};
+__device__ __forceinline__ FF ff_norm(float s, float c) {  // Fast2Sum, |s| >= |c|
+    const float r = __fadd_rn(s, c);
+    return FF{r, __fsub_rn(c, __fsub_rn(r, s))};
+}
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+    const float s = __fadd_rn(x.s, y.s), bp = __fsub_rn(s, x.s);
+    const float e = __fadd_rn(__fsub_rn(x.s, __fsub_rn(s, bp)), __fsub_rn(y.s, bp));  // TwoSum error
+    return ff_norm(s, __fadd_rn(__fadd_rn(x.c, y.c), e));
+}
+// the lane's two columns as one pair (invalid columns contribute nothing)
+__device__ __forceinline__ FF ff_lane(const ColSum2<float> &cs, bool va, bool vb) {
+    const FF a = va ? ff_norm(cs.s.x, cs.c.x) : FF{0.f, 0.f};
+    const FF b = vb ? ff_norm(cs.s.y, cs.c.y) : FF{0.f, 0.f};
+    return ff_add(a, b);
+}
+// fixed-tree warp reduction (lane 0 ends with the warp's pair)
+__device__ __forceinline__ FF ff_warp_sum(FF v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = ff_add(v, FF{__shfl_down_sync(0xffffffffu, v.s, o), __shfl_down_sync(0xffffffffu, v.c, o)});
+    return v;
+}
+
 template <> struct ColSum2<double> {
     double2 s = make_double2(0.0, 0.0);
     __device__ __forceinline__ void add(double2 v, double w, double) {
@@ -572,7 +604,29 @@ __global__ void __launch_bounds__(32 * (TY + 1), 1) step_kernel(const __grid_con
         else
             run_pass2(std::integral_constant<int, 2>{});
 
-        if (SUMS) {
+        if constexpr (SUMS && std::is_same<T, float>::value) {
+            // deterministic per-tile reduction in float pairs: the lane's
+            // columns, a warp tree, then a fixed tree over the warps in warp 0
+            __shared__ FF redf[2 * TY];
+            const FF pq = ff_warp_sum(ff_lane(sumQ, va, vb)), pt = ff_warp_sum(ff_lane(sumT, va, vb));
+            if (tx == 0) {
+                redf[2 * wy] = pq;
+                redf[2 * wy + 1] = pt;
+            }
+            consumer_sync(NT);
+            if (wy == 0) {
+                FF q = tx < TY ? redf[2 * tx] : FF{0.f, 0.f}, tt = tx < TY ? redf[2 * tx + 1] : FF{0.f, 0.f};
+                q = ff_warp_sum(q);
+                tt = ff_warp_sum(tt);
+                if (tx == 0) {
+                    if (!isfinite(q.s) || !isfinite(q.c) || !isfinite(tt.s) || !isfinite(tt.c))
+                        atomicOr(a.status, ST_NONFINITE);
+                    a.partials[2 * (size_t)t] = (double)q.s + (double)q.c;
+                    a.partials[2 * (size_t)t + 1] = (double)tt.s + (double)tt.c;
+                }
+            }
+            consumer_sync(NT);
+        } else if constexpr (SUMS) {
             double mT = sumT.total(va, vb), mQ = sumQ.total(va, vb);
             if ((va || vb) && (!isfinite(mT) || !isfinite(mQ))) atomicOr(a.status, ST_NONFINITE);
             // deterministic per-tile reduction: warp tree, then warps in order
@@ -594,8 +648,9 @@ __global__ void __launch_bounds__(32 * (TY + 1), 1) step_kernel(const __grid_con
                 a.partials[2 * (size_t)t + 1] = tt;
             }
             consumer_sync(NT);
-        } else if (!isfinite(chk.x) || !isfinite(chk.y)) {
-            atomicOr(a.status, ST_NONFINITE);  // edge tiles tallied only their valid columns
+        } else {
+            if (!isfinite(chk.x) || !isfinite(chk.y))
+                atomicOr(a.status, ST_NONFINITE);  // edge tiles tallied only their valid columns
         }
     }
     if (!ok && tx == 0) atomicOr(ms.status, ST_TIMEOUT);
@@ -618,8 +673,9 @@ __global__ void __launch_bounds__(256) sums_finalize(const double *__restrict__ 
                                                      double *__restrict__ park, unsigned *__restrict__ ticket,
                                                      double *__restrict__ ring, long long *__restrict__ count,
                                                      int cap) {
-    __shared__ double sq[256], st[256];
+    __shared__ double sq[8], st[8];
     __shared__ bool last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long per = (nblk + gridDim.x - 1) / gridDim.x, perc = (ncorr + gridDim.x - 1) / gridDim.x;
     const long b0 = blockIdx.x * per, b1 = min(nblk, b0 + per);
     const long c0 = blockIdx.x * perc, c1 = min(ncorr, c0 + perc);
@@ -629,29 +685,50 @@ __global__ void __launch_bounds__(256) sums_finalize(const double *__restrict__ 
         t += part[2 * b + 1];
     }
     for (long b = c0 + threadIdx.x; b < c1; b += blockDim.x) t += corr[b];
-    sq[threadIdx.x] = q;
-    st[threadIdx.x] = t;
+    // fixed trees: within each warp, then over the block's eight warps
+    q = warp_sum(q);
+    t = warp_sum(t);
+    if (lane == 0) {
+        sq[warp] = q;
+        st[warp] = t;
+    }
     __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) {
-            sq[threadIdx.x] += sq[threadIdx.x + o];
-            st[threadIdx.x] += st[threadIdx.x + o];
+    if (warp == 0) {
+        q = lane < 8 ? sq[lane] : 0.0;
+        t = lane < 8 ? st[lane] : 0.0;
+        q = warp_sum(q);
+        t = warp_sum(t);
+        if (lane == 0) {
+            park[2 * blockIdx.x] = q;
+            park[2 * blockIdx.x + 1] = t;
+            __threadfence();
+            last = atomicAdd(ticket, 1u) == gridDim.x - 1;
         }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        park[2 * blockIdx.x] = sq[0];
-        park[2 * blockIdx.x + 1] = st[0];
-        __threadfence();
-        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
+    if (!last) return;
+    // the last block: the parked block results in a fixed tree (block b in
+    // lane b % 32 of warp b / 32), then the warps in order
+    __threadfence();
+    q = 0.0;
+    t = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+        q += ((volatile double *)park)[2 * b];
+        t += ((volatile double *)park)[2 * b + 1];
+    }
+    q = warp_sum(q);
+    t = warp_sum(t);
+    __syncthreads();
+    if (lane == 0) {
+        sq[warp] = q;
+        st[warp] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
         double Q = 0.0, Tt = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) {
-            Q += ((volatile double *)park)[2 * b];
-            Tt += ((volatile double *)park)[2 * b + 1];
+        for (int w = 0; w < 8; ++w) {
+            Q += sq[w];
+            Tt += st[w];
         }
         // the ring slot comes from a device counter, so a captured graph
         // replays into the next slots
