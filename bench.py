@@ -416,9 +416,29 @@ def variant_ensemble(steps):
     ms = e0.elapsed_time(e1) / steps
     peak, _ = peaks()
     alg = sum(nx * ny * nz * CELL_BYTES["f32"] + nx * ny * COL_BYTES["f32"] for nx, ny, nz in sizes)
+    # the (member, tile) work list of one launch: tiles per member, the
+    # persistent CTAs walking it and how full their last round is, counted
+    # in tiles and in tile-levels (a tile's cost goes with its depth)
+    cfg = ens.step_config()
+    ty, ctas = cfg["ty"], torch.cuda.get_device_properties(0).multi_processor_count * cfg["ctas_per_sm"]
+    tiles = [-(-nx // 64) * -(-ny // ty) for nx, ny, _ in sizes]
+    levels = [t * nz for t, (_, _, nz) in zip(tiles, sizes)]
+    rounds = -(-sum(tiles) // ctas)
+    work = {"order": "members by depth (nz) descending, then by size", "ctas": ctas,
+            "tiles_per_member": tiles, "nz_per_member": [nz for _, _, nz in sizes], "tiles": sum(tiles),
+            "rounds": rounds, "last_round_fill": (sum(tiles) - (rounds - 1) * ctas) / ctas, "tile_levels": sum(levels)}
+    # utilisation in tile-levels: the work over CTAs x the busiest CTA's share
+    order = sorted(range(len(sizes)), key=lambda m: (-sizes[m][2], -sizes[m][0] * sizes[m][1]))
+    per_cta = [0] * ctas
+    w = 0
+    for m in order:
+        for _ in range(tiles[m]):
+            per_cta[w % ctas] += sizes[m][2]
+            w += 1
+    work["tile_level_utilisation"] = sum(levels) / (ctas * max(per_cta))
     out = {"ms_per_step": ms, "value": cells / (ms * 1e-3), "unit": "cell-steps/s (all members)",
            "steps": steps, "members": len(sizes), "cells": cells, "hbm_frac": alg / (ms * 1e-3) / 1e9 / peak,
-           "graph": True, "tuned_config": ens.step_config(), "tune_ms": tuned_ms,
+           "graph": True, "tuned_config": cfg, "tune_ms": tuned_ms, "work_list": work,
            "gpu_launches_per_step": ens.last_launches() / steps}
     ens.close()
     return out
