@@ -36,16 +36,21 @@ struct Strip {
     int n, src_step, dst_step, pad;
 };
 
+// One cell per thread (blockIdx.x = strip, blockIdx.y * 256 + thread = cell
+// of the strip's n x nplanes), so that every copy's load is in flight at
+// once: the column strips are one element per 32-byte sector and the kernel
+// is latency bound.
 template <typename T>
 __global__ void __launch_bounds__(256) halo_exchange_kernel(const Strip *__restrict__ strips, int nplanes,
                                                             unsigned *__restrict__ status) {
     const Strip s = strips[blockIdx.x];
-    const T *src = static_cast<const T *>(s.src);
-    T *dst = static_cast<T *>(s.dst);
-    const long total = (long)s.n * nplanes;
-    for (long e = (long)blockIdx.y * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.y * blockDim.x) {
-        const long p = e / s.n, i = e - p * s.n;
-        const long so = s.src_off + p * s.src_plane + i * s.src_step, d = s.dst_off + p * s.dst_plane + i * s.dst_step;
+    const T *__restrict__ src = static_cast<const T *>(s.src);
+    T *__restrict__ dst = static_cast<T *>(s.dst);
+    const unsigned total = (unsigned)s.n * (unsigned)nplanes;
+    for (unsigned e = blockIdx.y * blockDim.x + threadIdx.x; e < total; e += gridDim.y * blockDim.x) {
+        const unsigned p = e / (unsigned)s.n, i = e - p * (unsigned)s.n;
+        const long so = s.src_off + (long)p * s.src_plane + (long)i * s.src_step;
+        const long d = s.dst_off + (long)p * s.dst_plane + (long)i * s.dst_step;
         if (WX_IN(so, s.src_n, status) && WX_IN(d, s.dst_n, status)) dst[d] = src[so];
     }
 }
@@ -162,8 +167,10 @@ static int launch_exchange(wx_dom *d, cudaStream_t s) {
     const int nplanes = 2 * d->nz;
     long maxn = 1;
     for (int r = 0; r < R; ++r) maxn = std::max<long>(maxn, std::max(d->blk[r]->nx, d->blk[r]->ny));
+    if (maxn * nplanes >= (1L << 32) - 65536L * 256)
+        return dfail(d, WX_EUNSUPPORTED, "halo exchange: a strip holds 2^32 cells or more");
     const long per = (maxn * nplanes + 255) / 256;
-    dim3 grid((unsigned)(4 * R), (unsigned)std::min<long>(per, 64));
+    dim3 grid((unsigned)(4 * R), (unsigned)std::min<long>(per, 65535));
     const Strip *st = d->d_strips + (size_t)par * 4 * R;
     if (d->blk[0]->t_bytes == 4)
         halo_exchange_kernel<float><<<grid, 256, 0, s>>>(st, nplanes, d->d_status);
