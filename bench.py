@@ -460,7 +460,7 @@ def variant_surrogate(steps, nx=1581, ny=1301, plain_ms=None, train_epochs=32):
     X, Yt = S.rows(net, Ts, qs, km, tend)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    hist = S.train(net, X, Yt, Ts.shape[0], epochs=train_epochs, batch=4096, lr0=3e-3, seed=0) \
+    hist = S.train(net, X, Yt, Ts.shape[0], epochs=train_epochs, batch=4096, lr0=2e-3, seed=0) \
         if train_epochs else [float("nan")]
     torch.cuda.synchronize()
     t2 = time.perf_counter()

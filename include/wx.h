@@ -504,6 +504,15 @@ int wx_convert(const void *src, void *dst, long n, int to_f64,
 int wx_gather_rows(const void *src, long src_rows, long row_bytes,
                    const int *idx, long n, void *dst, void *cuda_stream);
 
+/* The training driver's minibatch order: out[0..n) = a permutation of
+ * 0..n-1 (host memory, n <= 2^31 - 1), Fisher-Yates from the top with the
+ * splitmix64 generator (Steele, Lea and Flood, OOPSLA 2014) seeded with
+ * `seed`; draw r for position i is the high 64 bits of u * (i + 1) (Lemire's
+ * multiply-shift, bias below (i + 1) / 2^64).  The same (n, seed) gives the
+ * same permutation on every host.  Host only: no CUDA call.  WX_EINVAL for
+ * n < 0, n > 2^31 - 1 or a NULL out with n > 0. */
+int wx_permutation(long n, unsigned long long seed, int *out);
+
 /* Attach (m != NULL) or detach (NULL) a trained network to an FP32 context
  * with nz = 58.  With WX_SURROGATE in the flags, each wx_step then runs the
  * dynamics, predicts the column physics with the network and accepts a

@@ -934,6 +934,28 @@ extern "C" int wx_gather_rows(const void *src, long src_rows, long row_bytes, co
                             : mfail(nullptr, WX_ECUDA, std::string("wx_gather_rows: ") + cudaGetErrorString(e));
 }
 
+// The training driver's minibatch order (host only): Fisher-Yates from the
+// top with splitmix64 (Steele, Lea and Flood 2014), each draw in [0, i]
+// taken as the high half of u * (i + 1) (Lemire's multiply-shift).
+extern "C" int wx_permutation(long n, unsigned long long seed, int *out) {
+    if (n < 0 || n > 2147483647L || (n > 0 && !out)) return WX_EINVAL;
+    for (long i = 0; i < n; ++i) out[i] = (int)i;
+    unsigned long long state = seed;
+    auto next = [&]() {
+        unsigned long long z = (state += 0x9e3779b97f4a7c15ull);
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+        return z ^ (z >> 31);
+    };
+    for (long i = n - 1; i > 0; --i) {
+        const long r = (long)(((unsigned __int128)next() * (unsigned long long)(i + 1)) >> 64);
+        const int t = out[i];
+        out[i] = out[r];
+        out[r] = t;
+    }
+    return WX_OK;
+}
+
 extern "C" int wx_mlp_denormalize(wx_mlp *m, const float *Y, long M, float *out, void *stream) {
     if (!m) return mfail(nullptr, WX_EINVAL, "wx_mlp_denormalize: no network");
     if (M < 0 || (M > 0 && (!Y || !out))) return mfail(m, WX_EINVAL, "wx_mlp_denormalize: bad arguments");

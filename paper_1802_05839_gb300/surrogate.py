@@ -7,7 +7,8 @@ normalised rows through wx_mlp_train_step (forward, backward and Adam in the
 library's kernels), cosine-decayed learning rate.  Every transpose, cast,
 row gather and denormalisation runs in the library (wx_read_columns_f32,
 wx_convert, wx_gather_rows, wx_mlp_denormalize); PyTorch only allocates
-device memory and draws the minibatch order (a seeded CPU permutation).
+device memory; the minibatch order is the library's seeded permutation
+(wx_permutation).
 """
 from __future__ import annotations
 
@@ -122,7 +123,6 @@ def train(mlp, X, Yt, n_rows, epochs=4, batch=4096, lr0=1e-3, seed=0, log=None):
     """Adam on shuffled minibatches of the first n_rows rows; returns the
     per-epoch mean loss (device losses read once per epoch)."""
     torch = _torch()
-    g = torch.Generator(device="cpu").manual_seed(seed)  # the minibatch order
     nb = n_rows // batch
     total = epochs * nb
     loss = torch.zeros(max(nb, 1), dtype=torch.float32, device="cuda")
@@ -131,7 +131,8 @@ def train(mlp, X, Yt, n_rows, epochs=4, batch=4096, lr0=1e-3, seed=0, log=None):
     hist = []
     step = 0
     for ep in range(epochs):
-        perm = torch.randperm(n_rows, generator=g).to(torch.int32).cuda()
+        # the epoch's minibatch order from the library's seeded permutation
+        perm = torch.from_numpy(wx.permutation(n_rows, seed * 1000003 + ep)).cuda()
         for b in range(nb):
             idx = perm[b * batch:(b + 1) * batch]
             lr = 0.5 * lr0 * (1.0 + np.cos(np.pi * step / total))

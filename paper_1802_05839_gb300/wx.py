@@ -133,6 +133,7 @@ SIGNATURES = [
     ("wx_mlp_denormalize", ctypes.c_int, [_VP, _VP, ctypes.c_long, _VP, _VP]),
     ("wx_convert", ctypes.c_int, [_VP, _VP, ctypes.c_long, ctypes.c_int, _VP]),
     ("wx_gather_rows", ctypes.c_int, [_VP, ctypes.c_long, ctypes.c_long, _VP, ctypes.c_long, _VP, _VP]),
+    ("wx_permutation", ctypes.c_int, [ctypes.c_long, ctypes.c_ulonglong, _VP]),
     ("wx_destroy", None, [_VP]),
     ("wx_last_error", ctypes.c_char_p, [_VP]),
 ]
@@ -816,6 +817,17 @@ def wx_convert(src, dst, stream=None):
     code = lib().wx_convert(_dptr(src), _dptr(dst), n, int(to64), _stream_ptr(stream))
     if code != 0:
         raise WxError(code, lib().wx_mlp_last_error().decode())
+
+
+def permutation(n, seed):
+    """A seeded permutation of 0..n-1 (numpy int32, host), drawn by the
+    library (wx_permutation: Fisher-Yates with splitmix64)."""
+    n = int(n)
+    out = np.empty(n if 0 <= n < 2 ** 31 else 0, dtype=np.int32)
+    code = lib().wx_permutation(n, int(seed) & (2 ** 64 - 1), out.ctypes.data_as(_VP) if out.size else None)
+    if code != 0:
+        raise WxError(code, "wx_permutation: n must be in [0, 2^31 - 1]")
+    return out
 
 
 def wx_gather_rows(src, idx, dst, stream=None):

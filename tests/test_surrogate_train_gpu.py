@@ -32,7 +32,7 @@ def trained():
     X, Yt = S.rows(m, Ts, qs, km, tend)
     val = S.dataset([101], 256, 256)
     before = S.tendency_error(m, *val)
-    hist = S.train(m, X, Yt, Ts.shape[0], epochs=32, batch=4096, lr0=3e-3, seed=0)
+    hist = S.train(m, X, Yt, Ts.shape[0], epochs=32, batch=4096, lr0=2e-3, seed=0)
     del X, Yt
     yield m, hist, before, val, (Ts, qs, km, tend)
     m.close()
