@@ -72,8 +72,12 @@ __global__ void __launch_bounds__(512) pf_step_kernel(const PfArgs<T> g) {
     const int k0 = blockIdx.z * kPfChunk, k1 = min(k0 + kPfChunk, g.nz);
     if (i >= g.W || j >= g.H) return;
     const long plane = g.sk;
-    const T *col = g.E + j * g.sj + i * g.si;
-    T *out = g.En + j * g.sj + i * g.si;
+    // the two buffers never overlap: without __restrict__ every load would
+    // wait for the previous level's store
+    const T *__restrict__ E = g.E;
+    T *__restrict__ En = g.En;
+    const T *__restrict__ col = E + j * g.sj + i * g.si;
+    T *__restrict__ out = En + j * g.sj + i * g.si;
     const bool ghost_col = (i == 0 || i == g.nx + 1);
     const bool ghost_row = !ghost_col && (j == 0 || j == g.ny + 1);
     auto aff_a = [&](int k) { return k == 0 ? g.a_bot : (k == g.nz - 1 ? g.a_top : g.a_mid); };
@@ -82,13 +86,14 @@ __global__ void __launch_bounds__(512) pf_step_kernel(const PfArgs<T> g) {
     if (ghost_col || ghost_row) {
         // two neighbours on the same level: the row's (or column's) other end
         // and the adjacent interior cell
-        const T *na, *nb;
+        const T *__restrict__ na;
+        const T *__restrict__ nb;
         if (ghost_col) {
-            na = g.E + j * g.sj + (i == 0 ? 1 : g.nx) * g.si;
-            nb = g.E + j * g.sj + (i == 0 ? g.nx + 1 : 0) * g.si;
+            na = E + j * g.sj + (i == 0 ? 1 : g.nx) * g.si;
+            nb = E + j * g.sj + (i == 0 ? g.nx + 1 : 0) * g.si;
         } else {
-            na = g.E + (j == 0 ? 1 : g.ny) * g.sj + i * g.si;
-            nb = g.E + (j == 0 ? g.ny + 1 : 0) * g.sj + i * g.si;
+            na = E + (j == 0 ? 1 : g.ny) * g.sj + i * g.si;
+            nb = E + (j == 0 ? g.ny + 1 : 0) * g.sj + i * g.si;
         }
 #pragma unroll 4
         for (int k = k0; k < k1; ++k) {
