@@ -73,6 +73,31 @@ def test_small_case_ten_steps_per_step(dtype):
     ctx.close()
 
 
+@pytest.mark.parametrize("shape", [(45, 38, 58), (70, 50, 58), (130, 30, 58), (7, 13, 58)])
+def test_tmem_variant_row_ends_over_steps(shape):
+    """The FP32 TMEM variant (twelve-row tiles) over several steps on rows
+    whose length is not a multiple of the 32-byte sector, and on a row
+    shorter than one sector: a ghost column lost or overwritten in step n
+    shows from step n + 1 on, at the row ends, so every cell of three steps
+    is checked (the increments too)."""
+    case = prepared(inputs.paper_grid_case(*shape, seed=5), "f32")
+    ctx = wx.Context(case.nx, case.ny, case.nz, "f32")
+    ctx.set_params(case)
+    ctx.load_fields(case.T, case.q, case.U, case.V)
+    assert ctx.step_config()["ty"] == 12
+    T, q = case.T, case.q
+    for s in range(3):
+        ctx.step(1)
+        ctx.sync()
+        Tg, qg = ctx.read_fields()
+        To, qo = oracle.step(case, T, q, case.U, case.V)
+        assert maxrel(Tg, To) <= TOL["f32"] and maxrel(qg, qo) <= TOL["f32"], (s, maxrel(Tg, To), maxrel(qg, qo))
+        Ts, _ = oracle.dynamics(case, T, q, case.U, case.V)
+        assert_increments(T, Ts, Tg, To, what=f"{shape} step {s}")
+        T, q = Tg, qg
+    ctx.close()
+
+
 @pytest.mark.parametrize("near_singular", [False, True])
 def test_f32_strong_physics_increments(near_singular):
     """FP32 step on a case whose physics increment is ~1 K (a +-5 K level
