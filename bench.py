@@ -19,7 +19,7 @@ CUDA graph, the residual-checked MLP-surrogate step (network trained in this
 run by the library's kernels) against the plain step, and the paper's own
 reduced weather application on its three grids beside the paper's timings.
 
-  python bench.py --only f64|mixed|ensemble|surrogate|reduced_app|ablation|rk3 [--nx --ny]   one variant
+  python bench.py --only f64|mixed|ensemble|surrogate|reduced_app|ablation|rk3|decomposed [--nx --ny]   one variant
 """
 from __future__ import annotations
 
