@@ -224,6 +224,7 @@ struct wx_ctx {
     double *flag_corr = nullptr; // [n_flag] energy correction of the FP64 solve (sums)
     long n_flag = 0;             // columns solved in FP64 (first in the list)
     long n_list = 0;             // all listed columns (kappa_mult != 1)
+    bool fixup_carveout = false; // the side kernel's shared-memory carveout is set on this device
 
     // WX_SURROGATE: the attached network and this grid's activation buffers
     struct wx_mlp *sur = nullptr;

@@ -238,12 +238,11 @@ int launch_mixed_fixup(wx_ctx *c, int dst, bool sums, cudaStream_t s) {
     const int nt = kFixThreads;
     const bool sm = c->nz <= kFixSmemNz;
     auto kern = sm ? mixed_fixup_kernel<true> : mixed_fixup_kernel<false>;
-    static bool carveout = false;  // six blocks' f_k in shared memory per SM
-    if (!carveout) {
+    if (sm && !c->fixup_carveout) {  // six blocks' f_k in shared memory per SM (once per context)
         WX_CK(cudaFuncSetAttribute(mixed_fixup_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                    cudaSharedmemCarveoutMaxShared),
               "fixup carveout");
-        carveout = true;
+        c->fixup_carveout = true;
     }
     kern<<<(unsigned)((c->n_list + nt - 1) / nt), nt, sm ? (size_t)nt * c->nz * sizeof(float) : 0, s>>>(
         c->flag_list, c->n_list, c->n_flag, (const double2 *)c->flag_fac, c->flag_e, c->flag_side,
