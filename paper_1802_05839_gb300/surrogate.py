@@ -59,8 +59,9 @@ def case_columns(case, adv_steps, out=None):
         state_columns(ctx, nx, ny, nz, (Ts, qs))
     finally:
         ctx.close()
-    if km is not None:
-        km.copy_(torch.from_numpy(np.ascontiguousarray(case.kappa_mult, np.float32).reshape(-1)))
+    if km is not None:  # kappa_mult = 1 where the case has none
+        kmh = np.ones(n, np.float32) if case.kappa_mult is None else case.kappa_mult
+        km.copy_(torch.from_numpy(np.ascontiguousarray(kmh, np.float32).reshape(-1)))
     # Targets from the FP64 column kernel: T** - T* is ~1e-4 K, a few FP32
     # ulps of T ~ 280 K, so FP32 targets would be mostly rounding noise.
     f64 = lambda a: None if a is None else torch.empty(a.shape, dtype=torch.float64, device="cuda")
