@@ -93,6 +93,45 @@ def test_ensemble_sums_under_graph_replay():
     ens.close()
 
 
+def test_near_singular_members_with_sums_under_graph_replay():
+    """FP32 members with near-singular kappa_mult columns (the listing
+    variant of the batch, then each member's side solve) and FP64 sums,
+    replayed from a graph: each member equals its own context bit for bit,
+    sums included, and its sums equal the FP64 sums of its state (1e-12).
+    (Ensembles take WX_F32 or WX_F64 members.)"""
+    dtype = "f32"
+    sizes = [(70, 50, 58), (45, 33, 58), (33, 71, 40)]
+    cases = []
+    for m, (nx, ny, nz) in enumerate(sizes):
+        c = inputs.round_to_f32(inputs.paper_grid_case(nx, ny, nz, seed=40 + m, near_singular=True))
+        cases.append(c)
+    flags = wx.WX_ADVECTION | wx.WX_PHYSICS | wx.WX_SUMS
+    ens = wx.Ensemble([(c.nx, c.ny, c.nz) for c in cases], dtype)
+    for mem, c in zip(ens.members, cases):
+        mem.set_params(c, flags=flags)
+        mem.load_fields(c.T, c.q, c.U, c.V)
+    ens.step(3, graph=True)
+    ens.step(2, graph=True)
+    ens.sync()
+    for mem, c in zip(ens.members, cases):
+        Tg, qg = mem.read_fields()
+        mg, eg = mem.sums()
+        ctx = wx.Context(c.nx, c.ny, c.nz, dtype)
+        ctx.set_params(c, flags=flags)
+        ctx.load_fields(c.T, c.q, c.U, c.V)
+        ctx.step(5)
+        ctx.sync()
+        Ts, qs = ctx.read_fields()
+        ms, es = ctx.sums()
+        ctx.close()
+        assert np.array_equal(Tg, Ts) and np.array_equal(qg, qs)
+        assert np.array_equal(mg, ms) and np.array_equal(eg, es)
+        w = c.h ** 2 * c.dz[:, None, None]
+        assert abs(eg[-1] - np.sum(Tg * w)) / abs(eg[-1]) <= 1e-12
+        assert abs(mg[-1] - np.sum(qg * w)) / abs(mg[-1]) <= 1e-12
+    ens.close()
+
+
 def test_ensemble_rejects_mismatched_members():
     cases = members(SIZES[:2])
     ens = wx.Ensemble([(c.nx, c.ny, c.nz) for c in cases], "f32")
