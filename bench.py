@@ -424,11 +424,11 @@ def variant_ensemble(steps):
     tiles = [-(-nx // 64) * -(-ny // ty) for nx, ny, _ in sizes]
     levels = [t * nz for t, (_, _, nz) in zip(tiles, sizes)]
     rounds = -(-sum(tiles) // ctas)
-    work = {"order": "members by depth (nz) descending, then by size", "ctas": ctas,
+    work = {"order": "members by size (cells) descending", "ctas": ctas,
             "tiles_per_member": tiles, "nz_per_member": [nz for _, _, nz in sizes], "tiles": sum(tiles),
             "rounds": rounds, "last_round_fill": (sum(tiles) - (rounds - 1) * ctas) / ctas, "tile_levels": sum(levels)}
     # utilisation in tile-levels: the work over CTAs x the busiest CTA's share
-    order = sorted(range(len(sizes)), key=lambda m: (-sizes[m][2], -sizes[m][0] * sizes[m][1]))
+    order = sorted(range(len(sizes)), key=lambda m: -sizes[m][0] * sizes[m][1] * sizes[m][2])
     per_cta = [0] * ctas
     w = 0
     for m in order:
